@@ -1,0 +1,412 @@
+"""Benchmark of the sub-1-spp sampling + reconstruction hot path on GB300.
+
+One step = one frame of the plain method at 1920x1080 (8-frame synthetic
+sequence, 0.25 spp, 3-level pyramid, 54/29/25 seeded logits, bilinear
+reprojection along affine motion of at most 8 px with 5% disoccluded pixels,
+tone map tau + sRGB), through the C ABI:
+    spp_alloc_sample_map -> spp_render_synthetic -> spp_splat_samples
+    -> spp_reconstruct_level (levels 2, 1, 0; level 0 with the temporal term
+       over the previous step's output, and the tone map)
+Inputs of all 8 frames are resident in HBM before the timed region (value);
+the end-to-end figure (e2e) copies each frame's inputs from pinned host memory
+and reads the tone-mapped frame back inside the timed region.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (the paper ships no code to compare against).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (W, H, frames, budget, levels)
+    "1080p": (1920, 1080, 8, 0.25, 3),
+    "4k": (3840, 2160, 4, 0.25, 3),
+}
+METRIC = "Mpix/s per frame of alloc+splat+reconstruct (plain method)"
+UNIT = "Mpix/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="1080p")
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="bounded CPU work for the oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# inputs
+# --------------------------------------------------------------------------
+def make_inputs(W, H, L, frames):
+    import spp_inputs as inp
+    return [inp.frame_inputs(W, H, L, frame=t, temporal=True) for t in range(frames)]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def level0_algorithmic_bytes(W, H, mask: np.ndarray) -> int:
+    """Compulsory bytes of one full-resolution reconstruction launch: 29
+    spatial logits everywhere, 25 temporal logits where the pixel is not
+    disoccluded, L^0 (12 B), L-hat^1 (12 B per coarse pixel), previous HDR
+    (12 B), motion (8 B), mask (1 B), HDR + sRGB outputs (24 B)."""
+    N = W * H
+    unmasked = int(N - int(mask.astype(bool).sum()))
+    coarse = (W // 2) * (H // 2)
+    return N * (29 * 4 + 12 + 12 + 8 + 1 + 24) + unmasked * 25 * 4 + coarse * 12
+
+
+# --------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# --------------------------------------------------------------------------
+def oracle_frame_seconds(W, H, L, B, x, prev):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.frame(x["d"], x["clean"], [a.astype(np.float64) for a in x["logits"]], W, H, L, B,
+                 prev=prev, mv=x["mv"], mask=x["mask"], frame_index=1)
+    return time.perf_counter() - t0
+
+
+def cpu_sample(W, H, L, B, budget_s):
+    """Runs the oracle on band crops of the workload's frame (full width,
+    H/8 rows, same per-pixel work) until budget_s of CPU time is spent."""
+    import spp_inputs as inp
+    Hs = max(H // 8 // (1 << (L - 1)) * (1 << (L - 1)), 1 << (L - 1))
+    x = inp.frame_inputs(W, Hs, L, frame=1, temporal=True)
+    prev = np.random.default_rng(1).random((3, Hs, W))
+    spent, pix = 0.0, 0
+    while spent < budget_s:
+        spent += oracle_frame_seconds(W, Hs, L, B, x, prev)
+        pix += W * Hs
+    return pix / spent / 1e6, f"oracle frames of {W}x{Hs} (full-width band of the {W}x{H} " \
+        f"workload), {pix // (W * Hs)} runs, {spent:.1f} s, 1 thread"
+
+
+def run_reference(args, rank, world):
+    W, H, F, B, L = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    import spp_inputs as inp
+    Hs = max(H // 8 // (1 << (L - 1)) * (1 << (L - 1)), 1 << (L - 1))
+    x = inp.frame_inputs(W, Hs, L, frame=1, temporal=True)
+    prev = np.random.default_rng(1).random((3, Hs, W))
+    for _ in range(args.warmup):
+        oracle_frame_seconds(W, Hs, L, B, x, prev)
+    t = [oracle_frame_seconds(W, Hs, L, B, x, prev) for _ in range(args.steps)]
+    total = sum(t)
+    value = W * Hs * args.steps / total / 1e6
+    sample = (f"each step one oracle frame of a {W}x{Hs} full-width band of the {W}x{H} "
+              f"workload (same per-pixel work), FP64, 1 thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args.workload),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(name):
+    W, H, F, B, L = WORKLOADS[name]
+    return {"workload": f"plain method {W}x{H}, {F}-frame sequence, {B} spp, {L}-level pyramid, "
+                        f"54/29/25 seeded logits, bilinear reprojection (|mv| <= 8 px, 5% "
+                        f"disoccluded), tone map tau + sRGB",
+            "W": W, "H": H, "frames": F, "spp": B, "levels": L,
+            "l2": "inputs larger than L2 (about 0.8 GB read per frame vs 129 MB L2)"}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2602_08642_gb300 as spp
+    from paper_2602_08642_gb300 import _binding as Bnd
+
+    W, H, F, B, L = WORKLOADS[args.workload]
+    N = W * H
+    dev = torch.device("cuda", local)
+    host_inputs = make_inputs(W, H, L, F)
+    stream = torch.cuda.current_stream()
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    frames = []
+    for x in host_inputs:
+        frames.append(dict(d=to_dev(x["d"]), clean=to_dev(x["clean"]),
+                           logits=[to_dev(a) for a in x["logits"]], mv=to_dev(x["mv"]),
+                           mask=to_dev(x["mask"])))
+    fr = spp.Frame(W, H, L, max_budget=B, device=dev)
+    tm = spp.make_tonemap()
+    hats = [None] + [torch.empty((3, H >> l, W >> l), device=dev) for l in range(1, L)]
+    state = {"prev": None, "parity": 0}
+    ev_l0 = []
+
+    def step(k, timed_l0=False, inp=None):
+        t = k % F
+        x = inp if inp is not None else frames[t]
+        params = spp.make_params(B, frame=t + rank * 1000)
+        fr.alloc(x["d"], params)
+        fr.render(x["clean"], 0xC0FFEE + rank, t)
+        fr.splat()
+        for l in range(L - 1, 0, -1):
+            C = 25 if l == L - 1 else 29
+            Bnd.check(spp.spp_reconstruct_level(
+                fr.layers[l], x["logits"][l], C, hats[l + 1] if l + 1 < L else None, None, None,
+                None, W >> l, H >> l, None, hats[l], None), "level")
+        out = fr.hdr[state["parity"]]
+        prev = state["prev"]
+        if prev is None:  # first frame of the run: no previous output yet
+            prev_t, mv_t, mask_t = None, None, None
+        else:
+            prev_t, mv_t, mask_t = prev, x["mv"], x["mask"]
+        if timed_l0:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        Bnd.check(spp.spp_reconstruct_level(fr.layers[0], x["logits"][0], 54, hats[1], prev_t,
+                                            mv_t, mask_t, W, H, tm, out, fr.ldr), "level 0")
+        if timed_l0:
+            e1.record(stream)
+            ev_l0.append((e0, e1))
+        state["prev"] = out
+        state["parity"] ^= 1
+        return out
+
+    fr.clear_status()
+    for k in range(max(args.warmup, 3)):
+        step(k)
+    torch.cuda.synchronize()
+    fr.check_status()
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = spp.spp_launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k, timed_l0=True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = spp.spp_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    fr.check_status()
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = N * args.steps * world / (ms_max / 1e3) / 1e6
+
+    l0_ms = [a.elapsed_time(b) for a, b in ev_l0]
+    l0_avg = sum(l0_ms) / len(l0_ms)
+    masks = [x["mask"] for x in host_inputs]
+    l0_bytes = sum(level0_algorithmic_bytes(W, H, masks[(args.warmup + k) % F])
+                   for k in range(args.steps)) / args.steps
+    peaks, peak_kind = measured_peaks()
+    achieved = l0_bytes / (l0_avg / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "recon_kernel<UP,TEMP,TONE> (level 0)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                "traffic": None, "algorithmic_bytes_per_launch": l0_bytes,
+                "avg_launch_ms": l0_avg,
+                "share_of_step": l0_avg * args.steps / ms}
+
+    # end to end: host inputs -> device -> frame -> tone-mapped frame on host
+    e2e = run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, world, dist)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        import oracle
+        oracle.build()
+        v, sample = cpu_sample(W, H, L, B, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(args.workload),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches,
+            "samples_per_frame": int(fr.sample_count()),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, world, dist):
+    import torch
+    pinned = []
+    for x in host_inputs:
+        pinned.append(dict(d=torch.from_numpy(x["d"]).pin_memory(),
+                           clean=torch.from_numpy(x["clean"]).pin_memory(),
+                           logits=[torch.from_numpy(a).pin_memory() for a in x["logits"]],
+                           mv=torch.from_numpy(x["mv"]).pin_memory(),
+                           mask=torch.from_numpy(x["mask"]).pin_memory()))
+    staging = dict(d=torch.empty_like(pinned[0]["d"], device=dev),
+                   clean=torch.empty_like(pinned[0]["clean"], device=dev),
+                   logits=[torch.empty_like(a, device=dev) for a in pinned[0]["logits"]],
+                   mv=torch.empty_like(pinned[0]["mv"], device=dev),
+                   mask=torch.empty_like(pinned[0]["mask"], device=dev))
+    out_host = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in
+              [pinned[0]["d"], pinned[0]["clean"], pinned[0]["mv"], pinned[0]["mask"],
+               *pinned[0]["logits"]])
+    d2h = out_host.numel() * out_host.element_size()
+
+    def e2e_step(k):
+        x = pinned[k % F]
+        staging["d"].copy_(x["d"], non_blocking=True)
+        staging["clean"].copy_(x["clean"], non_blocking=True)
+        for a, b in zip(staging["logits"], x["logits"]):
+            a.copy_(b, non_blocking=True)
+        staging["mv"].copy_(x["mv"], non_blocking=True)
+        staging["mask"].copy_(x["mask"], non_blocking=True)
+        step(k, inp=staging)
+        out_host.copy_(fr.ldr, non_blocking=True)
+
+    for k in range(2):
+        e2e_step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.e2e_steps):
+        e2e_step(2 + k)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    return {"value": W * H * args.e2e_steps * world / (ms / 1e3) / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": ms / args.e2e_steps, "steps": args.e2e_steps}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * spp.h -- C ABI of the GB300 (sm_103a) library for sub-1-spp adaptive
+ * sampling and gather-pyramid reconstruction, after "Forget Superresolution,
+ * Sample Adaptively (when Path Tracing)" (arXiv 2602.08642).
+ *
+ * Conventions shared by every entry point
+ *   - Images are planar FP32 [C][H][W], row-major, x fastest.  Level l of the
+ *     pyramid is (W >> l) x (H >> l); W and H must be divisible by 2^(L-1).
+ *   - Every data pointer is a DEVICE pointer owned by the caller, 16-byte
+ *     aligned (SPP_ERR_ALIGN otherwise).  Arrays of pointers (layers, logits)
+ *     are HOST arrays of device pointers.  The library allocates nothing:
+ *     scratch space is a caller-provided workspace whose size the
+ *     *_workspace_bytes queries return.
+ *   - Every call is asynchronous on the given cudaStream_t and returns an int:
+ *     SPP_OK, or a negative SPP_ERR_* for errors found on the host (no work is
+ *     enqueued then).  Errors found by the kernels (bad density values, too
+ *     small sample capacity, a look-back wait that gave up) are written to a
+ *     caller-provided device int32 status word, first error wins; read it with
+ *     spp_get_status and reset it with spp_clear_status.
+ *   - Calls are thread-compatible: concurrent calls must use distinct
+ *     workspaces and outputs.
+ */
+#ifndef SPP_H
+#define SPP_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define SPP_OK 0
+#define SPP_ERR_ARG (-1)       /* bad argument: null pointer, size out of range */
+#define SPP_ERR_ALIGN (-2)     /* a pointer is not 16-byte aligned */
+#define SPP_ERR_SHAPE (-3)     /* W or H not divisible by 2^(L-1), or L out of [2,5] */
+#define SPP_ERR_WORKSPACE (-4) /* workspace too small */
+#define SPP_ERR_CAPACITY (-5)  /* more samples than the sample buffers hold */
+#define SPP_ERR_TIMEOUT (-6)   /* a bounded device-side wait gave up */
+#define SPP_ERR_INPUT (-7)     /* density has NaN, inf, negative values, or sums to 0 */
+#define SPP_ERR_CUDA (-8)      /* a CUDA runtime call failed */
+
+/* Holdout weighting of the extra sample. */
+#define SPP_HOLDOUT_RAMP 0 /* relaxed ramp of Eq. relaxed_holdout with h of Eq. h_factor */
+#define SPP_HOLDOUT_HARD 1 /* hard step of Eq. holdout (the lambda -> inf limit), weight 1 */
+
+/* spp_params.flags */
+#define SPP_FLAG_EXACT_FP64 1u /* evaluate every pixel on the FP64 path (no FP32 filter) */
+/* Test of the bounded waits: scan tile 1 never publishes its prefix, so the
+ * look-back waits of the later tiles run out; the call completes with
+ * SPP_ERR_TIMEOUT in the status word and meaningless offsets. */
+#define SPP_FLAG_TEST_STALL_TILE1 (1u << 31)
+
+/* Sampling parameters (Sec. 3, Sec. 4.2-4.3). */
+typedef struct spp_params {
+    double budget;           /* B: mean samples per pixel of the frame, > 0 */
+    double uniform_fraction; /* phi: part of the budget spread uniformly; the paper uses 1/8 */
+    double lambda;           /* ramp temperature, >= 1; the paper uses 10 */
+    uint64_t seed;           /* seed of the per-pixel uniforms u_i */
+    uint32_t frame;          /* frame index t (selects the uniform stream) */
+    int32_t holdout_mode;    /* SPP_HOLDOUT_RAMP or SPP_HOLDOUT_HARD */
+    uint32_t flags;          /* SPP_FLAG_* */
+    uint32_t reserved;       /* must be 0 */
+} spp_params;
+
+/* Tone-map parameters (Sec. 5): contrast alpha, saturation beta, exposure k,
+ * shadow s in (0,1), highlight h in (0,1).  Defaults 1, 1, 0, 0.5, 0.5. */
+typedef struct spp_tonemap {
+    float alpha;
+    float beta;
+    float exposure;
+    float shadow;
+    float highlight;
+} spp_tonemap;
+
+/* ------------------------------------------------------------ utilities */
+/* Message for an SPP_* code; never NULL. */
+const char *spp_strerror(int code);
+
+/* ABI version of this header (increases on incompatible change). */
+int spp_abi_version(void);
+
+/* Number of kernels this library has launched in this process (host-side
+ * counter, incremented at every launch). */
+uint64_t spp_launch_count(void);
+
+/* Copies the device status word to the host (synchronises the stream) and
+ * returns it (SPP_OK or an SPP_ERR_* code); SPP_ERR_CUDA if the copy fails. */
+int spp_get_status(const int32_t *status, cudaStream_t stream);
+
+/* Resets the device status word to SPP_OK (asynchronous). */
+int spp_clear_status(int32_t *status, cudaStream_t stream);
+
+/* ---------------------------------------------------- a1-a3: allocation */
+/* Workspace bytes spp_alloc_sample_map needs for a W x H frame. */
+size_t spp_alloc_workspace_bytes(int W, int H);
+
+/*
+ * Turns a sampler density into an integer sample-count map and a sample list
+ * (Sec. 3: 1/8 of the budget uniform, 7/8 by the spatial softmax of d;
+ * Sec. 4.2: stochastic rounding; Sec. 4.3, Eq. relaxed_holdout and h_factor:
+ * the relaxed holdout weight).
+ *
+ *   d            [H][W] FP32 sampler output, >= 0 (already exponentiated, so
+ *                d_i / sum d is the softmax).  NaN, inf, negative values or an
+ *                all-zero map set SPP_ERR_INPUT in *status; the outputs are
+ *                then zero counts, s = 1, weights 1.
+ *   p            sampling parameters (host pointer).
+ *   counts       [H][W] int32 n_i, or NULL to skip.
+ *   offsets      [H*W + 1] int32 exclusive scan of n; offsets[H*W] = T.  The
+ *                samples of pixel i are slots offsets[i] .. offsets[i+1]-1,
+ *                its extra (holdout) sample, if any, is the last of them.
+ *   sample_pixel [capacity] int32 pixel index of every slot < min(T, capacity).
+ *   capacity     number of slots sample_pixel (and the renderer's sample
+ *                buffer) hold.  T > capacity sets SPP_ERR_CAPACITY.
+ *   s_out        [H][W] FP32 density s_i = B phi + (1-phi) B N d_i / sum d.
+ *   holdout_w    [H][W] FP32 weight of pixel i's last slot: the ramp weight
+ *                H_i / S_i,last when the extra sample is taken, else 1.
+ *   total        device int64 T (number of samples).
+ *   status       device int32 status word.
+ *   ws, ws_bytes workspace of at least spp_alloc_workspace_bytes(W, H).
+ *
+ * The count map is bit-exact to the FP64 definition: sum d is computed
+ * exactly and rounded once to FP64, and s_i, floor(s_i), p_i and the test
+ * u_i > 1 - p_i are decided as FP64 round-to-nearest operations (an FP32
+ * filter settles the pixels whose decision is not close; the rest run in
+ * FP64).  u_i = (bits >> 16) 2^-48 with bits the SplitMix64 mix of
+ * key + (i+1) gamma, key = mix(seed + (frame+1) gamma).
+ * Requires B * N + N < 2^31.
+ */
+int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p,
+                         int32_t *counts, int32_t *offsets, int32_t *sample_pixel,
+                         int64_t capacity, float *s_out, float *holdout_w, int64_t *total,
+                         int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---------------------------------------------- a4: renderer stand-in */
+/*
+ * Stand-in for the path tracer, which the paper runs in Falcor (Sec. 3, Sec.
+ * 6.3): sample k of pixel i is clean_i * exp(0.8 Z - 0.32), Z ~ N(0,1) by
+ * Box-Muller from two SplitMix64 counters of (seed, frame, i, k).
+ *
+ *   clean        [3][H][W] FP32 clean image.
+ *   offsets, sample_pixel, total   the sample list of spp_alloc_sample_map.
+ *   capacity     slots in rgb; slots >= min(T, capacity) are not written.
+ *   rgb          [capacity][4] FP32 (r, g, b, 0) per slot.
+ */
+int spp_render_synthetic(const float *clean, const int32_t *offsets, const int32_t *sample_pixel,
+                         const int64_t *total, int64_t capacity, int W, int H, uint64_t seed,
+                         uint32_t frame, float *rgb, cudaStream_t stream);
+
+/* --------------------------------------------- a5: splat and pyramid */
+/*
+ * Normalised splat of Eq. stoch_rnoisy, L0_i = (sum_{k<floor s_i} S_ik + H_i)/s_i,
+ * and the average-pool pyramid of Eq. app-pyramid, L^l = 4^-l sum over the
+ * 2^l x 2^l block.  Each pixel gathers its own slots (the sample list is
+ * ordered by pixel), so no atomics are used and the result is deterministic.
+ *
+ *   offsets      [H*W + 1] from spp_alloc_sample_map.
+ *   rgb          [capacity][4] samples (spp_render_synthetic layout).
+ *   s, holdout_w [H][W] from spp_alloc_sample_map.
+ *   capacity     slots in rgb; reads never go past it.
+ *   layers       host array of L device pointers, layers[l] = [3][H>>l][W>>l].
+ */
+int spp_splat_samples(const int32_t *offsets, const float *rgb, const float *s,
+                      const float *holdout_w, int64_t capacity, int W, int H, int L,
+                      float *const *layers, cudaStream_t stream);
+
+/* ---------------------------------------- a6-a9: reconstruction, tau */
+/* Workspace bytes of spp_reconstruct_frame (the denoised levels 1..L-1). */
+size_t spp_reconstruct_workspace_bytes(int W, int H, int L);
+
+/*
+ * One level of the coarse-to-fine reconstruction (Appendix A):
+ * Eq. app-recon-coarse when coarse == NULL, Eq. app-recon-mid otherwise, and
+ * Eq. app-recon-full when prev_hdr != NULL.  The joint softmax (Eq.
+ * app-softmax-mid, app-softmax-full) spans the 25 denoise logits, the 4
+ * upsampling logits when coarse != NULL, and the 25 temporal logits when
+ * prev_hdr != NULL and mask is 0 at the pixel.
+ *
+ *   noisy     [3][Hl][Wl] noisy level L^l.
+ *   logits    [C][Hl][Wl]: channels 0..24 denoise tap (i,j) at (j+2)*5+(i+2);
+ *             25..28 upsampling tap (i,j) at 25+2j+i; 29..53 temporal taps.
+ *             C >= 25, >= 29 with coarse, == 54 with prev_hdr.
+ *   coarse    [3][Hl/2][Wl/2] denoised L-hat^{l+1}, or NULL at the coarsest level.
+ *   prev_hdr  [3][Hl][Wl] previous HDR output, or NULL (no temporal term).
+ *   mv        [2][Hl][Wl] motion in pixels, current -> previous (needed with prev_hdr).
+ *   mask      [Hl][Wl] uint8, nonzero = disoccluded (drops the temporal
+ *             logits), or NULL.
+ *   tm        tone map for out_ldr, or NULL for the defaults.
+ *   out       [3][Hl][Wl] reconstructed HDR level.
+ *   out_ldr   [3][Hl][Wl] sRGB(tau(...)) of out (Sec. 5), or NULL.
+ * Borders clamp to the edge; the upsampling taps read floor((x+i)/2),
+ * floor((y+j)/2) of the coarser level as printed in Eq. app-upsample.
+ */
+int spp_reconstruct_level(const float *noisy, const float *logits, int C, const float *coarse,
+                          const float *prev_hdr, const float *mv, const uint8_t *mask, int Wl,
+                          int Hl, const spp_tonemap *tm, float *out, float *out_ldr,
+                          cudaStream_t stream);
+
+/*
+ * The whole reconstruction: levels L-1 .. 1 into the workspace, then level 0
+ * with the temporal term and the tone map (Appendix A; Sec. 5).
+ *   layers   host array of L pointers to the noisy pyramid (spp_splat_samples).
+ *   logits   host array of L pointers: logits[L-1] has 25 channels, logits[l]
+ *            for 0 < l < L-1 has 29, logits[0] has C0 (29, or 54 with temporal).
+ *   C0       channels of logits[0]: 29 or 54.  prev_hdr != NULL needs 54.
+ *   L        pyramid levels, 2..5.
+ *   out_hdr  [3][H][W]; out_ldr [3][H][W] or NULL.
+ */
+int spp_reconstruct_frame(const float *const *layers, const float *const *logits, int C0,
+                          const float *prev_hdr, const float *mv, const uint8_t *mask, int W,
+                          int H, int L, const spp_tonemap *tm, float *out_hdr, float *out_ldr,
+                          void *ws, size_t ws_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPP_H */

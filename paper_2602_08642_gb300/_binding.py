@@ -1,0 +1,204 @@
+"""Thin ctypes binding of the C ABI in ``include/spp.h``.
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in ``_build/libspp.so``.  Tensors are passed by device pointer; the
+binding checks that they live on a CUDA device, are contiguous and have the
+expected dtype, because a host pointer handed to a kernel would fault.  There
+is no fallback: importing this module fails loudly when the library has not
+been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build_lib
+
+if not os.path.exists(build_lib.LIB):
+    raise ImportError(
+        f"CUDA library {build_lib.LIB} is missing; build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (nvcc, sm_103a)")
+
+lib = ctypes.CDLL(build_lib.LIB)
+
+SPP_OK = 0
+SPP_ERR_ARG = -1
+SPP_ERR_ALIGN = -2
+SPP_ERR_SHAPE = -3
+SPP_ERR_WORKSPACE = -4
+SPP_ERR_CAPACITY = -5
+SPP_ERR_TIMEOUT = -6
+SPP_ERR_INPUT = -7
+SPP_ERR_CUDA = -8
+
+SPP_HOLDOUT_RAMP = 0
+SPP_HOLDOUT_HARD = 1
+SPP_FLAG_EXACT_FP64 = 1
+SPP_FLAG_TEST_STALL_TILE1 = 1 << 31
+
+
+class spp_params(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_double), ("uniform_fraction", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("frame", ctypes.c_uint32), ("holdout_mode", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class spp_tonemap(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("exposure", ctypes.c_float), ("shadow", ctypes.c_float),
+                ("highlight", ctypes.c_float)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_U64 = ctypes.c_uint64
+_U32 = ctypes.c_uint32
+_SZ = ctypes.c_size_t
+
+_SIGS = {
+    "spp_strerror": (ctypes.c_char_p, [_I]),
+    "spp_abi_version": (_I, []),
+    "spp_launch_count": (_U64, []),
+    "spp_get_status": (_I, [_P, _P]),
+    "spp_clear_status": (_I, [_P, _P]),
+    "spp_alloc_workspace_bytes": (_SZ, [_I, _I]),
+    "spp_alloc_sample_map": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _P, _P, _I64, _P,
+                                  _P, _P, _P, _P, _SZ, _P]),
+    "spp_render_synthetic": (_I, [_P, _P, _P, _P, _I64, _I, _I, _U64, _U32, _P, _P]),
+    "spp_splat_samples": (_I, [_P, _P, _P, _P, _I64, _I, _I, _I, _P, _P]),
+    "spp_reconstruct_workspace_bytes": (_SZ, [_I, _I, _I]),
+    "spp_reconstruct_level": (_I, [_P, _P, _I, _P, _P, _P, _P, _I, _I,
+                                   ctypes.POINTER(spp_tonemap), _P, _P, _P]),
+    "spp_reconstruct_frame": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _I,
+                                   ctypes.POINTER(spp_tonemap), _P, _P, _P, _SZ, _P]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class SppError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {spp_strerror(code)} ({code})")
+
+
+def check(code: int, where: str = "spp") -> int:
+    if code != SPP_OK:
+        raise SppError(code, where)
+    return code
+
+
+def _dev(t: torch.Tensor | None, dtype: torch.dtype | None = None):
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr_array(ts, dtype):
+    arr = (ctypes.c_void_p * len(ts))(*[_dev(t, dtype).value for t in ts])
+    return arr
+
+
+def spp_strerror(code: int) -> str:
+    return lib.spp_strerror(code).decode()
+
+
+def spp_abi_version() -> int:
+    return lib.spp_abi_version()
+
+
+def spp_launch_count() -> int:
+    return int(lib.spp_launch_count())
+
+
+def spp_get_status(status: torch.Tensor, stream=None) -> int:
+    return lib.spp_get_status(_dev(status, torch.int32), _stream(stream))
+
+
+def spp_clear_status(status: torch.Tensor, stream=None) -> int:
+    return lib.spp_clear_status(_dev(status, torch.int32), _stream(stream))
+
+
+def spp_alloc_workspace_bytes(W: int, H: int) -> int:
+    return int(lib.spp_alloc_workspace_bytes(W, H))
+
+
+def make_params(budget: float, *, uniform_fraction: float = 0.125, lam: float = 10.0,
+                seed: int = 0x5EED, frame: int = 0, hard: bool = False,
+                exact_fp64: bool = False) -> spp_params:
+    return spp_params(budget, uniform_fraction, lam, seed & 0xFFFFFFFFFFFFFFFF, frame,
+                      SPP_HOLDOUT_HARD if hard else SPP_HOLDOUT_RAMP,
+                      SPP_FLAG_EXACT_FP64 if exact_fp64 else 0, 0)
+
+
+def make_tonemap(alpha=1.0, beta=1.0, exposure=0.0, shadow=0.5, highlight=0.5) -> spp_tonemap:
+    return spp_tonemap(alpha, beta, exposure, shadow, highlight)
+
+
+def spp_alloc_sample_map(d, W, H, params: spp_params, counts, offsets, sample_pixel, capacity,
+                         s_out, holdout_w, total, status, ws, stream=None) -> int:
+    return lib.spp_alloc_sample_map(
+        _dev(d, torch.float32), W, H, ctypes.byref(params), _dev(counts, torch.int32),
+        _dev(offsets, torch.int32), _dev(sample_pixel, torch.int32), int(capacity),
+        _dev(s_out, torch.float32), _dev(holdout_w, torch.float32), _dev(total, torch.int64),
+        _dev(status, torch.int32), _dev(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def spp_render_synthetic(clean, offsets, sample_pixel, total, capacity, W, H, seed, frame, rgb,
+                         stream=None) -> int:
+    return lib.spp_render_synthetic(
+        _dev(clean, torch.float32), _dev(offsets, torch.int32), _dev(sample_pixel, torch.int32),
+        _dev(total, torch.int64), int(capacity), W, H, seed & 0xFFFFFFFFFFFFFFFF, frame,
+        _dev(rgb, torch.float32), _stream(stream))
+
+
+def spp_splat_samples(offsets, rgb, s, holdout_w, capacity, W, H, L, layers, stream=None) -> int:
+    arr = _ptr_array(layers, torch.float32)
+    return lib.spp_splat_samples(
+        _dev(offsets, torch.int32), _dev(rgb, torch.float32), _dev(s, torch.float32),
+        _dev(holdout_w, torch.float32), int(capacity), W, H, L, ctypes.cast(arr, _P),
+        _stream(stream))
+
+
+def spp_reconstruct_workspace_bytes(W: int, H: int, L: int) -> int:
+    return int(lib.spp_reconstruct_workspace_bytes(W, H, L))
+
+
+def spp_reconstruct_level(noisy, logits, C, coarse, prev_hdr, mv, mask, Wl, Hl, tm, out, out_ldr,
+                          stream=None) -> int:
+    return lib.spp_reconstruct_level(
+        _dev(noisy, torch.float32), _dev(logits, torch.float32), C, _dev(coarse, torch.float32),
+        _dev(prev_hdr, torch.float32), _dev(mv, torch.float32), _dev(mask, torch.uint8), Wl, Hl,
+        ctypes.byref(tm) if tm is not None else None, _dev(out, torch.float32),
+        _dev(out_ldr, torch.float32), _stream(stream))
+
+
+def spp_reconstruct_frame(layers, logits, C0, prev_hdr, mv, mask, W, H, L, tm, out_hdr, out_ldr,
+                          ws, stream=None) -> int:
+    la = _ptr_array(layers, torch.float32)
+    lo = _ptr_array(logits, torch.float32)
+    return lib.spp_reconstruct_frame(
+        ctypes.cast(la, _P), ctypes.cast(lo, _P), C0, _dev(prev_hdr, torch.float32),
+        _dev(mv, torch.float32), _dev(mask, torch.uint8), W, H, L,
+        ctypes.byref(tm) if tm is not None else None, _dev(out_hdr, torch.float32),
+        _dev(out_ldr, torch.float32), _dev(ws) if ws is not None else None,
+        (ws.numel() * ws.element_size()) if ws is not None else 0, _stream(stream))

@@ -1,0 +1,563 @@
+// a1-a3: budget normalisation, stochastic rounding with the relaxed holdout
+// ramp, and the sample list (Sec. 3, Sec. 4.2-4.3 of arXiv 2602.08642).
+//
+// Two kernels per frame, after one memset of the workspace header:
+//   budget_sum_kernel   exact sum of the FP32 density in integer limbs; the
+//                       last block rounds it once to FP64 and derives the
+//                       budget coefficients a = phi B, c = (1-phi) B N / S.
+//   assign_scan_kernel  per pixel: s_i = a + c d_i, n_i, holdout weight; a
+//                       single-pass decoupled look-back scan of n_i gives the
+//                       offsets; each pixel writes its slots of the sample list.
+//
+// Bit-exactness of the count map.  The decisions floor(s_i) and
+// u_i > 1 - p_i are those of FP64 round-to-nearest arithmetic.  FP64 is slow
+// on this part, so every pixel first evaluates s_i in float-float (error below
+// 2^-45 s_i) and decides in FP32 when the decision is further than a safe
+// margin from its threshold; only the few pixels within the margin (about
+// 2e-6 of them) run the FP64 sequence.
+#include "spp_internal.cuh"
+
+namespace spp {
+namespace {
+
+constexpr int kSumThreads = 256;
+constexpr int kWindows = 8;      // 32-bit windows of the 2^-149-scaled integer value
+constexpr int kLimbs = 9;        // per-thread limb accumulators (32-bit weights)
+constexpr int kWords = 11;       // carry-propagated 32-bit words of the total
+constexpr int kFlushEvery = 256; // elements per window before it is split into limbs
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kTile = kScanThreads * kScanItems;
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr int kSpinLimit = 1 << 20;
+
+struct AllocHeader {
+    unsigned long long limbs[kLimbs];  // exact sum, limb j has weight 2^(32 j - 149)
+    unsigned int blocks_done;          // ticket of the budget sum's last block
+    unsigned int tile_counter;         // dynamic tile index of the scan
+    int bad_input;
+    int valid;                         // 1 when the coefficients below are usable
+    double S, a, c, lam, h;
+    float a_hi, a_lo, c_hi, c_lo, lam_f, h_f;
+    int fast_ok;
+};
+constexpr size_t kHeaderBytes = 256;
+static_assert(sizeof(AllocHeader) <= kHeaderBytes, "alloc header too large");
+
+struct BudgetArgs {
+    double budget, phi, lambda;
+    int hard;
+    int force_exact;
+};
+
+// ---------------------------------------------------------------- K1
+__device__ __forceinline__ void accum_value(float x, unsigned long long (&win)[kWindows],
+                                            bool &bad) {
+    const uint32_t bits = __float_as_uint(x);
+    const uint32_t mag = bits & 0x7fffffffu;
+    if (mag >= 0x7f800000u || (bits != mag && mag != 0u)) {  // inf, NaN, negative
+        bad = true;
+        return;
+    }
+    const uint32_t e = mag >> 23;
+    const uint32_t m = (mag & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const uint32_t pos = e ? e - 1u : 0u;  // x = m 2^(pos - 149)
+    const unsigned long long val = static_cast<unsigned long long>(m) << (pos & 31u);
+    const uint32_t w = pos >> 5;
+#pragma unroll
+    for (int j = 0; j < kWindows; ++j) win[j] += (w == static_cast<uint32_t>(j)) ? val : 0ull;
+}
+
+__device__ __forceinline__ void flush_windows(unsigned long long (&win)[kWindows],
+                                              unsigned long long (&lim)[kLimbs]) {
+#pragma unroll
+    for (int j = 0; j < kWindows; ++j) {
+        lim[j] += win[j] & 0xffffffffull;
+        lim[j + 1] += win[j] >> 32;
+        win[j] = 0ull;
+    }
+}
+
+__device__ __forceinline__ int word_bit(const uint32_t *w, int b) {
+    return b < 0 ? 0 : static_cast<int>((w[b >> 5] >> (b & 31)) & 1u);
+}
+
+// Correctly rounded FP64 value of the exact total (single thread).
+__device__ double round_limbs(const unsigned long long *limbs) {
+    uint32_t w[kWords];
+    unsigned long long carry = 0ull;
+    for (int j = 0; j < kLimbs; ++j) {
+        const unsigned long long v = limbs[j] + carry;
+        w[j] = static_cast<uint32_t>(v & 0xffffffffull);
+        carry = v >> 32;
+    }
+    w[kLimbs] = static_cast<uint32_t>(carry & 0xffffffffull);
+    w[kLimbs + 1] = static_cast<uint32_t>(carry >> 32);
+    int top = -1;
+    for (int j = kWords - 1; j >= 0; --j)
+        if (w[j]) { top = j; break; }
+    if (top < 0) return 0.0;
+    const int P = 32 * top + 31 - __clz(w[top]);  // highest set bit
+    if (P <= 52) {
+        const unsigned long long x =
+            static_cast<unsigned long long>(w[0]) | (static_cast<unsigned long long>(w[1]) << 32);
+        return __dmul_rn(__ull2double_rn(x), 0x1p-149);  // exact
+    }
+    unsigned long long mant = 0ull;
+    for (int b = P; b >= P - 52; --b) mant = (mant << 1) | static_cast<unsigned long long>(word_bit(w, b));
+    const int rbit = word_bit(w, P - 53);
+    int sticky = 0;
+    for (int b = P - 54; b >= 0 && !sticky; --b) sticky |= word_bit(w, b);
+    int exp2 = P - 149;  // value = mant 2^(exp2 - 52)
+    if (rbit && (sticky || (mant & 1ull))) {
+        ++mant;
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            ++exp2;
+        }
+    }
+    const unsigned long long bits = (static_cast<unsigned long long>(exp2 + 1023) << 52) |
+                                    (mant & ((1ull << 52) - 1ull));
+    return __longlong_as_double(static_cast<long long>(bits));
+}
+
+__device__ void finalize_budget(AllocHeader *hdr, long long N, const BudgetArgs &args,
+                                int32_t *status) {
+    unsigned long long limbs[kLimbs];
+    for (int j = 0; j < kLimbs; ++j) limbs[j] = atomicAdd(&hdr->limbs[j], 0ull);
+    const int bad = atomicAdd(&hdr->bad_input, 0);
+    const double S = round_limbs(limbs);
+    hdr->S = S;
+    if (bad || !(S > 0.0)) {
+        set_status(status, SPP_ERR_INPUT);
+        hdr->valid = 0;
+        return;
+    }
+    // The FP64 round-to-nearest sequence of Sec. 3 (no contraction).
+    const double a = __dmul_rn(args.phi, args.budget);
+    const double k = __dmul_rn(__dsub_rn(1.0, args.phi), args.budget);
+    const double num = __dmul_rn(k, static_cast<double>(N));
+    const double c = __ddiv_rn(num, S);
+    const double two_lam = __dmul_rn(2.0, args.lambda);
+    const double h = __ddiv_rn(two_lam, __dsub_rn(two_lam, 1.0));
+    hdr->a = a;
+    hdr->c = c;
+    hdr->lam = args.lambda;
+    hdr->h = h;
+    const float c_hi = __double2float_rn(c);
+    const float a_hi = __double2float_rn(a);
+    hdr->c_hi = c_hi;
+    hdr->c_lo = __double2float_rn(__dsub_rn(c, static_cast<double>(c_hi)));
+    hdr->a_hi = a_hi;
+    hdr->a_lo = __double2float_rn(__dsub_rn(a, static_cast<double>(a_hi)));
+    hdr->lam_f = __double2float_rn(args.lambda);
+    hdr->h_f = __double2float_rn(h);
+    const bool c_ok = c >= 0x1p-60 && c <= 0x1p60;
+    const bool a_ok = a == 0.0 || (a >= 0x1p-60 && a <= 0x1p60);
+    hdr->fast_ok = (c_ok && a_ok && !args.force_exact) ? 1 : 0;
+    __threadfence();
+    hdr->valid = 1;
+}
+
+__global__ void __launch_bounds__(kSumThreads)
+budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, BudgetArgs args,
+                  int32_t *status) {
+    unsigned long long win[kWindows];
+    unsigned long long lim[kLimbs];
+#pragma unroll
+    for (int j = 0; j < kWindows; ++j) win[j] = 0ull;
+#pragma unroll
+    for (int j = 0; j < kLimbs; ++j) lim[j] = 0ull;
+    bool bad = false;
+    int cnt = 0;
+    const long long nthreads = static_cast<long long>(gridDim.x) * blockDim.x;
+    const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const long long n4 = N >> 2;
+    const float4 *d4 = reinterpret_cast<const float4 *>(d);
+    for (long long q = gtid; q < n4; q += nthreads) {
+        const float4 v = __ldg(d4 + q);
+        accum_value(v.x, win, bad);
+        accum_value(v.y, win, bad);
+        accum_value(v.z, win, bad);
+        accum_value(v.w, win, bad);
+        cnt += 4;
+        if (cnt >= kFlushEvery) {
+            flush_windows(win, lim);
+            cnt = 0;
+        }
+    }
+    for (long long i = (n4 << 2) + gtid; i < N; i += nthreads) accum_value(d[i], win, bad);
+    flush_windows(win, lim);
+
+    __shared__ unsigned long long s_part[kSumThreads / 32][kLimbs];
+    __shared__ int s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < kLimbs; ++j) {
+        unsigned long long v = lim[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) s_part[warp][j] = v;
+    }
+    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+    if (threadIdx.x < kLimbs) {
+        unsigned long long v = 0ull;
+        for (int w = 0; w < kSumThreads / 32; ++w) v += s_part[w][threadIdx.x];
+        if (v) atomicAdd(&hdr->limbs[threadIdx.x], v);
+    }
+    if (threadIdx.x == 0 && any_bad) atomicOr(&hdr->bad_input, 1);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(&hdr->blocks_done, 1u);
+        s_last = (t == gridDim.x - 1u) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        finalize_budget(hdr, N, args, status);
+    }
+}
+
+// ---------------------------------------------------------------- K2
+struct Coef {
+    double a, c, lam, h;
+    float a_hi, a_lo, c_hi, c_lo, lam_f, h_f;
+    int hard, fast;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// FP64 sequence, operation for operation the definition of Sec. 3 and 4.2-4.3.
+__device__ __noinline__ void assign_exact(float d, uint64_t bits, const Coef &k, int &n, float &w,
+                                          float &s) {
+    const double u = __dmul_rn(__ull2double_rn(bits >> 16), 0x1p-48);
+    const double m = __dmul_rn(k.c, static_cast<double>(d));
+    const double sd = __dadd_rn(k.a, m);
+    const double f = floor(sd);
+    const double p = __dsub_rn(sd, f);
+    const double t = __dsub_rn(1.0, p);
+    const bool extra = (p > 0.0) && (u > t);
+    double wd = 1.0;
+    if (extra && !k.hard) {
+        const double q = __ddiv_rn(k.lam, p);
+        const double v = __dsub_rn(__dadd_rn(u, p), 1.0);
+        double r = __dmul_rn(q, v);
+        r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+        wd = __dmul_rn(k.h, r);
+    }
+    n = static_cast<int>(f) + (extra ? 1 : 0);
+    w = __double2float_rn(wd);
+    s = __double2float_rn(sd);
+}
+
+// Float-float filter.  Returns false when a decision is within the margin of
+// its threshold (the caller then runs assign_exact).
+__device__ __forceinline__ bool assign_fast(float d, uint64_t bits, const Coef &k, int &n,
+                                            float &w, float &s) {
+    // s = a + c d in float-float
+    const float ph = __fmul_rn(k.c_hi, d);
+    float pl = __fmaf_rn(k.c_hi, d, -ph);
+    pl = __fmaf_rn(k.c_lo, d, pl);
+    float s1, e1;
+    two_sum(k.a_hi, ph, s1, e1);
+    const float e = __fadd_rn(e1, __fadd_rn(k.a_lo, pl));
+    const float sh = __fadd_rn(s1, e);
+    const float sl = __fsub_rn(e, __fsub_rn(sh, s1));
+    if (!(sh < 4194304.0f)) return false;
+    const float E = __fmaf_rn(sh, 0x1p-40f, 0x1p-90f);  // bound on |s_ff - s_fp64|
+    float f = floorf(sh);
+    if (sh == f && sl < 0.0f) f = __fsub_rn(f, 1.0f);
+    const float p1 = __fsub_rn(sh, f);  // exact
+    const float plow = __fadd_rn(p1, sl);  // p, distance to floor
+    float hh, he;
+    two_sum(1.0f, -p1, hh, he);
+    const float hl = __fsub_rn(he, sl);  // 1 - p = hh + hl
+    if (plow < 2.0f * E || __fadd_rn(hh, hl) < 2.0f * E) return false;
+    const float uh = __fmul_rn(static_cast<float>(static_cast<uint32_t>(bits >> 40)), 0x1p-24f);
+    const float ul = __fmul_rn(static_cast<float>(static_cast<uint32_t>((bits >> 16) & 0xffffffull)),
+                               0x1p-48f);
+    float vh, ve;
+    two_sum(uh, -hh, vh, ve);
+    const float v = __fadd_rn(vh, __fadd_rn(ve, __fsub_rn(ul, hl)));  // u + p - 1
+    const float thr = fmaxf(0x1p-20f, 4.0f * E);
+    if (fabsf(v) < thr) return false;
+    const bool extra = v > 0.0f;
+    float wf = 1.0f;
+    if (extra && !k.hard) {
+        float r = __fmul_rn(__fdiv_rn(k.lam_f, plow), v);
+        r = fminf(fmaxf(r, 0.0f), 1.0f);
+        wf = __fmul_rn(k.h_f, r);
+    }
+    n = static_cast<int>(f) + (extra ? 1 : 0);
+    w = wf;
+    s = sh;
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long ld_state(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+__device__ __forceinline__ void st_state(unsigned long long *p, unsigned long long v) {
+    atomicExch(p, v);
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *hdr_c,
+                   AllocHeader *hdr, unsigned long long *tile_state, uint64_t key, int hard,
+                   int stall_tile1,
+                   int32_t *__restrict__ counts, int32_t *__restrict__ offsets,
+                   int32_t *__restrict__ sample_pixel, long long capacity, float *__restrict__ s_out,
+                   float *__restrict__ w_out, long long *total, int32_t *status, int num_tiles) {
+    __shared__ int s_tile;
+    __shared__ int s_warp_excl[kScanThreads / 32];
+    __shared__ int s_warp_tot[kScanThreads / 32];
+    __shared__ int s_prefix;
+    if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->tile_counter, 1u));
+    __syncthreads();
+    const int tile = s_tile;
+    const long long base = static_cast<long long>(tile) * kTile +
+                           static_cast<long long>(threadIdx.x) * kScanItems;
+
+    Coef k;
+    const int valid = hdr_c->valid;
+    k.a = hdr_c->a;
+    k.c = hdr_c->c;
+    k.lam = hdr_c->lam;
+    k.h = hdr_c->h;
+    k.a_hi = hdr_c->a_hi;
+    k.a_lo = hdr_c->a_lo;
+    k.c_hi = hdr_c->c_hi;
+    k.c_lo = hdr_c->c_lo;
+    k.lam_f = hdr_c->lam_f;
+    k.h_f = hdr_c->h_f;
+    k.hard = hard;
+    k.fast = hdr_c->fast_ok;
+
+    float dv[kScanItems];
+    const bool full = base + kScanItems <= N;
+    if (full) {
+        const float4 v0 = __ldcs(reinterpret_cast<const float4 *>(d + base));
+        const float4 v1 = __ldcs(reinterpret_cast<const float4 *>(d + base) + 1);
+        dv[0] = v0.x; dv[1] = v0.y; dv[2] = v0.z; dv[3] = v0.w;
+        dv[4] = v1.x; dv[5] = v1.y; dv[6] = v1.z; dv[7] = v1.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) dv[q] = (base + q < N) ? d[base + q] : 0.0f;
+    }
+    int n[kScanItems];
+    float wv[kScanItems], sv[kScanItems];
+    int tsum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const long long i = base + q;
+        n[q] = 0;
+        wv[q] = 1.0f;
+        sv[q] = 1.0f;
+        if (i < N && valid) {
+            const uint64_t bits = stream_bits(key, static_cast<uint64_t>(i));
+            bool done = false;
+            if (k.fast) done = assign_fast(dv[q], bits, k, n[q], wv[q], sv[q]);
+            if (!done) assign_exact(dv[q], bits, k, n[q], wv[q], sv[q]);
+        }
+        tsum += n[q];
+    }
+
+    // block-wide exclusive scan of the per-thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = tsum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int wt = lane < kScanThreads / 32 ? s_warp_tot[lane] : 0;
+        int wincl = wt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wincl, off);
+            if (lane >= off) wincl += y;
+        }
+        if (lane < kScanThreads / 32) s_warp_excl[lane] = wincl - wt;
+        const int agg = __shfl_sync(0xffffffffu, wincl, kScanThreads / 32 - 1);
+        // decoupled look-back over the predecessors, 32 at a time
+        long long excl = 0;
+        if (stall_tile1 && tile == 1) {
+            // test of the bounded waits: publish nothing
+        } else if (tile == 0) {
+            if (lane == 0) st_state(&tile_state[0], kFlagInc | static_cast<unsigned int>(agg));
+        } else {
+            if (lane == 0) st_state(&tile_state[tile], kFlagAgg | static_cast<unsigned int>(agg));
+            int j = tile - 1;
+            while (true) {
+                const int idx = j - lane;
+                unsigned long long st = kFlagInc;
+                if (idx >= 0) {
+                    st = ld_state(&tile_state[idx]);
+                    int spins = 0;
+                    while ((st >> 62) == 0ull) {
+                        if (++spins > kSpinLimit) {
+                            set_status(status, SPP_ERR_TIMEOUT);
+                            st = kFlagInc;
+                            break;
+                        }
+                        __nanosleep(64);
+                        st = ld_state(&tile_state[idx]);
+                    }
+                }
+                const unsigned inc = __ballot_sync(0xffffffffu, (st >> 62) == 2ull);
+                int val = static_cast<int>(st & 0xffffffffull);
+                if (inc) {
+                    const int first = __ffs(inc) - 1;
+                    if (lane > first) val = 0;
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) val += __shfl_down_sync(0xffffffffu, val, off);
+                excl += __shfl_sync(0xffffffffu, val, 0);
+                if (inc) break;
+                j -= 32;
+            }
+            if (lane == 0)
+                st_state(&tile_state[tile],
+                         kFlagInc | static_cast<unsigned int>(excl + static_cast<long long>(agg)));
+        }
+        if (lane == 0) s_prefix = static_cast<int>(excl);
+    }
+    __syncthreads();
+
+    int run = s_prefix + s_warp_excl[warp] + (incl - tsum);
+    int off[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        off[q] = run;
+        run += n[q];
+    }
+    if (full) {
+        int4 *o4 = reinterpret_cast<int4 *>(offsets + base);
+        o4[0] = make_int4(off[0], off[1], off[2], off[3]);
+        o4[1] = make_int4(off[4], off[5], off[6], off[7]);
+        float4 *s4 = reinterpret_cast<float4 *>(s_out + base);
+        s4[0] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        s4[1] = make_float4(sv[4], sv[5], sv[6], sv[7]);
+        float4 *w4 = reinterpret_cast<float4 *>(w_out + base);
+        w4[0] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        w4[1] = make_float4(wv[4], wv[5], wv[6], wv[7]);
+        if (counts) {
+            int4 *c4 = reinterpret_cast<int4 *>(counts + base);
+            c4[0] = make_int4(n[0], n[1], n[2], n[3]);
+            c4[1] = make_int4(n[4], n[5], n[6], n[7]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            if (base + q < N) {
+                offsets[base + q] = off[q];
+                s_out[base + q] = sv[q];
+                w_out[base + q] = wv[q];
+                if (counts) counts[base + q] = n[q];
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        for (int r = 0; r < n[q]; ++r) {
+            const long long t = static_cast<long long>(off[q]) + r;
+            if (t < capacity) sample_pixel[t] = static_cast<int32_t>(base + q);
+        }
+    }
+    // the owner of the last pixel closes the scan
+    if (base <= N - 1 && N - 1 < base + kScanItems) {
+        offsets[N] = run;
+        *total = run;
+        if (static_cast<long long>(run) > capacity) set_status(status, SPP_ERR_CAPACITY);
+    }
+    (void)num_tiles;
+}
+
+}  // namespace
+
+size_t alloc_tiles(long long N) { return static_cast<size_t>((N + kTile - 1) / kTile); }
+
+}  // namespace spp
+
+extern "C" {
+
+size_t spp_alloc_workspace_bytes(int W, int H) {
+    if (W < 0 || H < 0) return 0;
+    const long long N = static_cast<long long>(W) * H;
+    return spp::kHeaderBytes + spp::alloc_tiles(N) * sizeof(unsigned long long);
+}
+
+int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int32_t *counts,
+                         int32_t *offsets, int32_t *sample_pixel, int64_t capacity, float *s_out,
+                         float *holdout_w, int64_t *total, int32_t *status, void *ws,
+                         size_t ws_bytes, cudaStream_t stream) {
+    using namespace spp;
+    if (!p || W < 0 || H < 0 || capacity < 0) return SPP_ERR_ARG;
+    if (static_cast<long long>(W) * H == 0) {  // empty frame: T = 0, offsets[0] = 0
+        if (!offsets || !total) return SPP_ERR_ARG;
+        if (!aligned16(offsets) || !aligned16(total)) return SPP_ERR_ALIGN;
+        if (cudaMemsetAsync(offsets, 0, sizeof(int32_t), stream) != cudaSuccess) return SPP_ERR_CUDA;
+        if (cudaMemsetAsync(total, 0, sizeof(int64_t), stream) != cudaSuccess) return SPP_ERR_CUDA;
+        return SPP_OK;
+    }
+    if (!d || !offsets || !s_out || !holdout_w || !total || !status || !ws) return SPP_ERR_ARG;
+    if (capacity > 0 && !sample_pixel) return SPP_ERR_ARG;
+    if (!(p->budget > 0.0) || !(p->budget < 1e30)) return SPP_ERR_ARG;
+    if (!(p->uniform_fraction >= 0.0) || !(p->uniform_fraction <= 1.0)) return SPP_ERR_ARG;
+    if (p->holdout_mode != SPP_HOLDOUT_RAMP && p->holdout_mode != SPP_HOLDOUT_HARD)
+        return SPP_ERR_ARG;
+    if (p->holdout_mode == SPP_HOLDOUT_RAMP && !(p->lambda >= 1.0 && p->lambda < 1e30))
+        return SPP_ERR_ARG;
+    if (p->reserved != 0 || (p->flags & ~(SPP_FLAG_EXACT_FP64 | SPP_FLAG_TEST_STALL_TILE1)) != 0)
+        return SPP_ERR_ARG;
+    const long long N = static_cast<long long>(W) * H;
+    if (N >= (1ll << 31) - 1) return SPP_ERR_ARG;
+    if (p->budget * static_cast<double>(N) + static_cast<double>(N) >= 2147483647.0)
+        return SPP_ERR_ARG;
+    if (!aligned16(d) || !aligned16(offsets) || !aligned16(s_out) || !aligned16(holdout_w) ||
+        (counts && !aligned16(counts)) || !aligned16(ws) || !aligned16(total))
+        return SPP_ERR_ALIGN;
+    const size_t need = spp_alloc_workspace_bytes(W, H);
+    if (ws_bytes < need) return SPP_ERR_WORKSPACE;
+
+    if (cudaMemsetAsync(ws, 0, need, stream) != cudaSuccess) return SPP_ERR_CUDA;
+    auto *hdr = static_cast<AllocHeader *>(ws);
+    auto *tiles = reinterpret_cast<unsigned long long *>(static_cast<char *>(ws) + kHeaderBytes);
+
+    BudgetArgs args;
+    args.budget = p->budget;
+    args.phi = p->uniform_fraction;
+    args.lambda = p->holdout_mode == SPP_HOLDOUT_RAMP ? p->lambda : 1.0;
+    args.hard = p->holdout_mode == SPP_HOLDOUT_HARD;
+    args.force_exact = (p->flags & SPP_FLAG_EXACT_FP64) ? 1 : 0;
+
+    const long long per_block = static_cast<long long>(kSumThreads) * 32;
+    long long grid = (N + per_block - 1) / per_block;
+    const long long max_grid = static_cast<long long>(sm_count()) * 4;
+    if (grid > max_grid) grid = max_grid;
+    if (grid < 1) grid = 1;
+    budget_sum_kernel<<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(d, N, hdr, args,
+                                                                             status);
+    const int num_tiles = static_cast<int>(alloc_tiles(N));
+    assign_scan_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
+        d, N, hdr, hdr, tiles, stream_key(p->seed, p->frame), args.hard,
+        (p->flags & SPP_FLAG_TEST_STALL_TILE1) ? 1 : 0, counts, offsets,
+        sample_pixel, capacity, s_out, holdout_w, reinterpret_cast<long long *>(total), status,
+        num_tiles);
+    count_launch(2);
+    return launch_status();
+}
+
+}  // extern "C"

@@ -1,5 +1,8 @@
 """Seeded synthetic inputs shaped like the paper's workloads.
 
+A module of its own: the CUDA path and the FP64 oracle both read their inputs
+from here, and it imports neither of them.
+
 This module holds none of the method's arithmetic: it only draws the inputs
 (sampler density, clean procedural scene, G-buffer, kernel logits, motion
 vectors, disocclusion masks) that both the CUDA path and the FP64 oracle

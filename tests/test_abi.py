@@ -1,0 +1,114 @@
+"""The C-ABI library loads and exports every entry point of include/spp.h.
+
+CPU only: nothing here launches a kernel.  The argument checks below return
+before any CUDA call, so they run without a GPU.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_08642_gb300 import build_lib
+    build_lib.build()
+    return ctypes.CDLL(build_lib.LIB)
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for name in ("spp_alloc_sample_map", "spp_render_synthetic", "spp_splat_samples",
+                 "spp_reconstruct_frame", "spp_reconstruct_level", "spp_get_status"):
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    import paper_2602_08642_gb300 as spp
+    assert spp.spp_abi_version() == 1
+    for code in range(0, -9, -1):
+        assert spp.spp_strerror(code) and spp.spp_strerror(code) != "unknown status code"
+    assert spp.spp_strerror(-99) == "unknown status code"
+
+
+def test_workspace_queries():
+    import paper_2602_08642_gb300 as spp
+    assert spp.spp_alloc_workspace_bytes(1920, 1080) == 256 + 8 * ((1920 * 1080 + 2047) // 2048)
+    assert spp.spp_alloc_workspace_bytes(-1, 4) == 0
+    b = spp.spp_reconstruct_workspace_bytes(1920, 1080, 3)
+    assert b >= 3 * 4 * (960 * 540 + 480 * 270)
+    assert spp.spp_reconstruct_workspace_bytes(64, 64, 1) == 0
+    assert spp.spp_reconstruct_workspace_bytes(64, 64, 6) == 0
+
+
+def _fake(addr):
+    return ctypes.c_void_p(addr)
+
+
+def test_host_argument_errors(lib):
+    """Host-side validation returns before any CUDA call."""
+    import paper_2602_08642_gb300._binding as B
+    p = B.make_params(0.25)
+    a = _fake(0x10000)
+    mis = _fake(0x10004)
+    n = None
+    f = B.lib.spp_alloc_sample_map
+    # null params / negative size
+    assert f(a, 4, 4, None, a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
+    assert f(a, -1, 4, ctypes.byref(p), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
+    # misaligned density
+    assert f(mis, 4, 4, ctypes.byref(p), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ALIGN
+    # workspace too small
+    assert f(a, 64, 64, ctypes.byref(p), a, a, a, 16, a, a, a, a, a, 8, n) == B.SPP_ERR_WORKSPACE
+    # bad budget, lambda, mode, reserved
+    for bad in (B.make_params(0.0), B.make_params(-1.0), B.make_params(0.25, lam=0.5)):
+        assert f(a, 4, 4, ctypes.byref(bad), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
+    q = B.make_params(0.25)
+    q.reserved = 1
+    assert f(a, 4, 4, ctypes.byref(q), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
+    # budget * N beyond int32 sample indices
+    big = B.make_params(2000.0)
+    assert f(a, 4096, 4096, ctypes.byref(big), a, a, a, 16, a, a, a, a, a, 1 << 30, n) == \
+        B.SPP_ERR_ARG
+    # splat: shape not divisible by 2^(L-1), L out of range
+    arr = (ctypes.c_void_p * 5)(0x10000, 0x10000, 0x10000, 0x10000, 0x10000)
+    g = B.lib.spp_splat_samples
+    assert g(a, a, a, a, 16, 30, 16, 3, ctypes.cast(arr, ctypes.c_void_p), n) == B.SPP_ERR_SHAPE
+    assert g(a, a, a, a, 16, 32, 16, 6, ctypes.cast(arr, ctypes.c_void_p), n) == B.SPP_ERR_SHAPE
+    # reconstruction: temporal needs 54 channels and a coarser level
+    r = B.lib.spp_reconstruct_level
+    assert r(a, a, 29, a, a, a, None, 32, 32, None, a, None, n) == B.SPP_ERR_ARG
+    assert r(a, a, 54, None, a, a, None, 32, 32, None, a, None, n) == B.SPP_ERR_ARG
+    assert r(a, mis, 25, None, None, None, None, 32, 32, None, a, None, n) == B.SPP_ERR_ALIGN
+    tm = B.make_tonemap(shadow=1.5)
+    assert r(a, a, 25, None, None, None, None, 32, 32, ctypes.byref(tm), a, a, n) == B.SPP_ERR_ARG
+    fr = B.lib.spp_reconstruct_frame
+    assert fr(ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 29, a, a,
+              None, 32, 32, 3, None, a, a, a, 1 << 20, n) == B.SPP_ERR_ARG  # prev needs C0=54
+    assert fr(ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 54, None,
+              None, None, 36, 32, 4, None, a, a, a, 1 << 20, n) == B.SPP_ERR_SHAPE
+    assert fr(ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 54, None,
+              None, None, 64, 64, 3, None, a, a, a, 16, n) == B.SPP_ERR_WORKSPACE
+
+
+def test_binding_rejects_host_tensors():
+    import torch
+    import paper_2602_08642_gb300 as spp
+    fr_args = [torch.zeros(4)] * 3
+    with pytest.raises(ValueError):
+        spp.binding._dev(fr_args[0])
