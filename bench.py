@@ -43,11 +43,11 @@ UNIT = "Mpix/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="1080p")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bounded CPU work for the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -65,7 +65,7 @@ def dist_env():
 # clocks during the timed region
 # --------------------------------------------------------------------------
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -89,7 +89,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, name: str):
+        setattr(self, name, time.time())
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -103,16 +106,21 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0 = getattr(self, "t_start", 0.0)
+        t1 = getattr(self, "t_end", float("inf"))
+        window = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.15]
+        if not window:  # region shorter than the sampling period: nearest samples after it
+            window = [ln for (t, ln) in self.lines if t >= t0][:2]
+        for ln in window:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
+            if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[0]))
-                smax.append(float(parts[1]))
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
+            for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
@@ -290,11 +298,13 @@ def run_ours(args, rank, world, local):
     launches0 = spp.spp_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark("t_start")
     t0.record(stream)
     for k in range(args.steps):
         step(args.warmup + k, timed_l0=True)
     t1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark("t_end")
     launches = spp.spp_launch_count() - launches0
     if world > 1:
         dist.barrier()
@@ -350,11 +360,10 @@ def run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, worl
     import torch
     pinned = []
     for x in host_inputs:
-        pinned.append(dict(d=torch.from_numpy(x["d"]).pin_memory(),
-                           clean=torch.from_numpy(x["clean"]).pin_memory(),
-                           logits=[torch.from_numpy(a).pin_memory() for a in x["logits"]],
-                           mv=torch.from_numpy(x["mv"]).pin_memory(),
-                           mask=torch.from_numpy(x["mask"]).pin_memory()))
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        pinned.append(dict(d=pin(x["d"]), clean=pin(x["clean"]),
+                           logits=[pin(a) for a in x["logits"]], mv=pin(x["mv"]),
+                           mask=pin(x["mask"])))
     staging = dict(d=torch.empty_like(pinned[0]["d"], device=dev),
                    clean=torch.empty_like(pinned[0]["clean"], device=dev),
                    logits=[torch.empty_like(a, device=dev) for a in pinned[0]["logits"]],

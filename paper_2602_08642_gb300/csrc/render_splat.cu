@@ -25,10 +25,19 @@ render_kernel(const float *__restrict__ clean, const int32_t *__restrict__ offse
         const uint64_t hp = stream_bits(key, static_cast<uint64_t>(i));
         const uint64_t b1 = mix64(hp + (2ull * k + 1ull) * kGamma);
         const uint64_t b2 = mix64(hp + (2ull * k + 2ull) * kGamma);
-        const float u1 = __fmaf_rn(static_cast<float>(static_cast<uint32_t>(b1 >> 40)), 0x1p-24f,
-                                   0x1p-25f);
+        // ln u1 with u1 = (m + 1/2) 2^-24 taken exactly: below 1/2 u1 itself is
+        // exact in FP32; above it 1 - u1 = (2(2^24 - m) - 1) 2^-25 is, and
+        // log1p keeps the steep sqrt(-2 ln u1) near u1 = 1 accurate.
+        const uint32_t m1 = static_cast<uint32_t>(b1 >> 40);
+        float lnu;
+        if (m1 < (1u << 23)) {
+            lnu = logf(static_cast<float>(2u * m1 + 1u) * 0x1p-25f);
+        } else {
+            const uint32_t q = (1u << 24) - m1;
+            lnu = log1pf(-static_cast<float>(2u * q - 1u) * 0x1p-25f);
+        }
         const float u2 = static_cast<float>(static_cast<uint32_t>(b2 >> 40)) * 0x1p-24f;
-        const float z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+        const float z = sqrtf(-2.0f * lnu) * cospif(2.0f * u2);
         const float g = expf(__fmaf_rn(0.8f, z, -0.32f));
         rgb[t] = make_float4(clean[i] * g, clean[N + i] * g, clean[2 * N + i] * g, 0.0f);
     }

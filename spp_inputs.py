@@ -80,7 +80,7 @@ def scene(W: int, H: int, seed: int = 3, frame: int = 0):
             amp = r.uniform(0.15, 0.35)
             acc += np.float32(amp) * np.sin(2 * np.pi * (fx * u + fy * v) + ph).astype(np.float32)
         illum[c] = acc
-    clean = np.clip(2.2 * albedo * illum, 0.0, 4.0).astype(np.float32)
+    clean = np.ascontiguousarray(np.clip(2.2 * albedo * illum, 0.0, 4.0), dtype=np.float32)
     # height field for normals: smooth bumps
     hgt = np.zeros((H, W), np.float32)
     for _ in range(3):
@@ -92,8 +92,9 @@ def scene(W: int, H: int, seed: int = 3, frame: int = 0):
     nrm /= np.linalg.norm(nrm, axis=0, keepdims=True)
     depth = depth_tab[label] + 0.3 * hgt + 0.002 * (xs + ys)
     depth = np.clip(depth, 1.0, 100.0).astype(np.float32)
-    gbuf = dict(albedo=albedo.astype(np.float32), normal=nrm.astype(np.float32),
-                depth=depth[None].astype(np.float32))
+    gbuf = dict(albedo=np.ascontiguousarray(albedo, dtype=np.float32),
+                normal=np.ascontiguousarray(nrm, dtype=np.float32),
+                depth=np.ascontiguousarray(depth[None], dtype=np.float32))
     return clean, gbuf
 
 

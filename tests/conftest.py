@@ -17,3 +17,14 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+def build_spp_lib():
+    """Builds libspp.so (if stale) without importing the package, whose import
+    needs the library."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_2602_08642_gb300", "build_lib.py")
+    spec = importlib.util.spec_from_file_location("spp_build_lib", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()

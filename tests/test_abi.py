@@ -15,9 +15,8 @@ HEADER = os.path.join(ROOT, "include", "spp.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2602_08642_gb300 import build_lib
-    build_lib.build()
-    return ctypes.CDLL(build_lib.LIB)
+    from conftest import build_spp_lib
+    return ctypes.CDLL(build_spp_lib())
 
 
 def declared_symbols():

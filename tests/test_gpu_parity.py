@@ -26,8 +26,8 @@ LDR_ATOL = 1e-6
 
 @pytest.fixture(scope="module")
 def spp():
-    from paper_2602_08642_gb300 import build_lib
-    build_lib.build()
+    from conftest import build_spp_lib
+    build_spp_lib()
     import paper_2602_08642_gb300 as spp
     torch.cuda.set_device(0)
     return spp
