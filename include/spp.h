@@ -135,6 +135,31 @@ int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p,
                          int64_t capacity, float *s_out, float *holdout_w, int64_t *total,
                          int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
 
+/*
+ * Allocation-free variant of spp_alloc_sample_map.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * while they run, such as an engine or plug-in host that owns the GPU memory
+ * budget and forbids allocation inside its frame loop (cudaMalloc can
+ * synchronise the device and take unbounded time).
+ *
+ * Same arguments and results as spp_alloc_sample_map, without the workspace:
+ * the scratch lives in a library-owned static device array of 131,328 bytes,
+ * which every GPU that loads the library keeps until the process exits.
+ *   - Frames are limited to W*H <= 33,554,432 pixels (2^25); larger frames
+ *     return SPP_ERR_WORKSPACE and enqueue nothing.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and each call clears the part it uses
+ *     before use.  Calls that overlap on the GPU (for example on two streams
+ *     at once) race on it: issue them on one stream, one after the other.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+int spp_alloc_sample_map_static(const float *d, int W, int H, const spp_params *p,
+                                int32_t *counts, int32_t *offsets, int32_t *sample_pixel,
+                                int64_t capacity, float *s_out, float *holdout_w, int64_t *total,
+                                int32_t *status, cudaStream_t stream);
+
 /* ---------------------------------------------- a4: renderer stand-in */
 /*
  * Stand-in for the path tracer, which the paper runs in Falcor (Sec. 3, Sec.

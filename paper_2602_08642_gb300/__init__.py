@@ -10,6 +10,7 @@ fallback.
 from . import _binding as binding  # noqa: F401  (raises ImportError if libspp.so is missing)
 from ._binding import (  # noqa: F401
     SppError, check, make_params, make_tonemap, spp_abi_version, spp_alloc_sample_map,
+    spp_alloc_sample_map_static,
     spp_alloc_workspace_bytes, spp_clear_status, spp_get_status, spp_launch_count,
     spp_reconstruct_frame, spp_reconstruct_level, spp_reconstruct_workspace_bytes,
     spp_render_synthetic, spp_splat_samples, spp_strerror)

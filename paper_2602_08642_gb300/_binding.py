@@ -68,6 +68,8 @@ _SIGS = {
     "spp_alloc_workspace_bytes": (_SZ, [_I, _I]),
     "spp_alloc_sample_map": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _P, _P, _I64, _P,
                                   _P, _P, _P, _P, _SZ, _P]),
+    "spp_alloc_sample_map_static": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _P, _P,
+                                         _I64, _P, _P, _P, _P, _P]),
     "spp_render_synthetic": (_I, [_P, _P, _P, _P, _I64, _I, _I, _U64, _U32, _P, _P]),
     "spp_splat_samples": (_I, [_P, _P, _P, _P, _I64, _I, _I, _I, _P, _P]),
     "spp_reconstruct_workspace_bytes": (_SZ, [_I, _I, _I]),
@@ -161,6 +163,15 @@ def spp_alloc_sample_map(d, W, H, params: spp_params, counts, offsets, sample_pi
         _dev(offsets, torch.int32), _dev(sample_pixel, torch.int32), int(capacity),
         _dev(s_out, torch.float32), _dev(holdout_w, torch.float32), _dev(total, torch.int64),
         _dev(status, torch.int32), _dev(ws), ws.numel() * ws.element_size(), _stream(stream))
+
+
+def spp_alloc_sample_map_static(d, W, H, params: spp_params, counts, offsets, sample_pixel,
+                                capacity, s_out, holdout_w, total, status, stream=None) -> int:
+    return lib.spp_alloc_sample_map_static(
+        _dev(d, torch.float32), W, H, ctypes.byref(params), _dev(counts, torch.int32),
+        _dev(offsets, torch.int32), _dev(sample_pixel, torch.int32), int(capacity),
+        _dev(s_out, torch.float32), _dev(holdout_w, torch.float32), _dev(total, torch.int64),
+        _dev(status, torch.int32), _stream(stream))
 
 
 def spp_render_synthetic(clean, offsets, sample_pixel, total, capacity, W, H, seed, frame, rgb,

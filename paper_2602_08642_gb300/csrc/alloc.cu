@@ -15,6 +15,8 @@
 // 2^-45 s_i) and decides in FP32 when the decision is further than a safe
 // margin from its threshold; only the few pixels within the margin (about
 // 2e-6 of them) run the FP64 sequence.
+#include <mutex>
+
 #include "spp_internal.cuh"
 
 namespace spp {
@@ -561,3 +563,70 @@ int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of spp_alloc_sample_map.
+//
+// Some callers cannot allocate device memory while they run: an engine or
+// plug-in host that owns the GPU's memory budget and forbids allocation inside
+// its frame loop (cudaMalloc can synchronise the device and its latency is
+// unbounded).  This entry point therefore keeps its scratch (the budget-sum
+// header and the scan's tile states) in a library-owned array in device memory
+// instead of a caller workspace.  The array has a fixed size, so frames are
+// limited to kStaticMaxPixels pixels; every GPU that loads the library keeps
+// it resident until the process exits.
+// ---------------------------------------------------------------------------
+namespace spp {
+namespace {
+constexpr long long kStaticMaxPixels = 1ll << 25;  // 33,554,432 pixels (8K UHD fits)
+constexpr size_t kStaticScratchBytes =
+    kHeaderBytes + static_cast<size_t>((kStaticMaxPixels + kTile - 1) / kTile) *
+                       sizeof(unsigned long long);  // 131,328 bytes
+}  // namespace
+}  // namespace spp
+
+static __device__ __align__(256) unsigned char spp_static_scratch[spp::kStaticScratchBytes];
+
+namespace spp {
+namespace {
+// The host-side name spp_static_scratch is only a stand-in for the array; its
+// device address is looked up once per device, with that device current.
+void *static_scratch_address(int *rc) {
+    static std::mutex mu;
+    constexpr int kMaxDevices = 64;
+    static void *addr[kMaxDevices] = {nullptr};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        *rc = SPP_ERR_CUDA;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, spp_static_scratch) != cudaSuccess || !p) {
+            *rc = SPP_ERR_CUDA;
+            return nullptr;
+        }
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+}  // namespace
+}  // namespace spp
+
+extern "C" int spp_alloc_sample_map_static(const float *d, int W, int H, const spp_params *p,
+                                           int32_t *counts, int32_t *offsets,
+                                           int32_t *sample_pixel, int64_t capacity, float *s_out,
+                                           float *holdout_w, int64_t *total, int32_t *status,
+                                           cudaStream_t stream) {
+    using namespace spp;
+    if (W < 0 || H < 0) return SPP_ERR_ARG;
+    if (static_cast<long long>(W) * H > kStaticMaxPixels) return SPP_ERR_WORKSPACE;
+    int rc = SPP_OK;
+    void *ws = static_scratch_address(&rc);
+    if (!ws) return rc;
+    // the regular entry point clears the header and tile states it uses before
+    // its kernels run, so leftovers of the previous call do not matter
+    return spp_alloc_sample_map(d, W, H, p, counts, offsets, sample_pixel, capacity, s_out,
+                                holdout_w, total, status, ws, kStaticScratchBytes, stream);
+}
