@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bounded CPU work for the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="distinct input frames resident on the device (default: the workload's)")
     return ap.parse_args()
 
 
@@ -147,12 +149,12 @@ def measured_peaks():
 def level0_algorithmic_bytes(W, H, mask: np.ndarray) -> int:
     """Compulsory bytes of one full-resolution reconstruction launch: 29
     spatial logits everywhere, 25 temporal logits where the pixel is not
-    disoccluded, L^0 (12 B), L-hat^1 (12 B per coarse pixel), previous HDR
-    (12 B), motion (8 B), mask (1 B), HDR + sRGB outputs (24 B)."""
+    disoccluded, L^0 (12 B), the warped previous output W_t L_{t-1} (12 B),
+    L-hat^1 (12 B per coarse pixel), mask (1 B), HDR + sRGB outputs (24 B)."""
     N = W * H
     unmasked = int(N - int(mask.astype(bool).sum()))
     coarse = (W // 2) * (H // 2)
-    return N * (29 * 4 + 12 + 12 + 8 + 1 + 24) + unmasked * 25 * 4 + coarse * 12
+    return N * (29 * 4 + 12 + 12 + 1 + 24) + unmasked * 25 * 4 + coarse * 12
 
 
 # --------------------------------------------------------------------------
@@ -233,6 +235,8 @@ def run_ours(args, rank, world, local):
     from paper_2602_08642_gb300 import _binding as Bnd
 
     W, H, F, B, L = WORKLOADS[args.workload]
+    if args.frames > 0:
+        F = args.frames
     N = W * H
     dev = torch.device("cuda", local)
     host_inputs = make_inputs(W, H, L, F)
@@ -249,6 +253,7 @@ def run_ours(args, rank, world, local):
     fr = spp.Frame(W, H, L, max_budget=B, device=dev)
     tm = spp.make_tonemap()
     hats = [None] + [torch.empty((3, H >> l, W >> l), device=dev) for l in range(1, L)]
+    warped = torch.empty((3, H, W), device=dev)
     state = {"prev": None, "parity": 0}
     ev_l0 = []
 
@@ -263,19 +268,19 @@ def run_ours(args, rank, world, local):
             C = 25 if l == L - 1 else 29
             Bnd.check(spp.spp_reconstruct_level(
                 fr.layers[l], x["logits"][l], C, hats[l + 1] if l + 1 < L else None, None, None,
-                None, W >> l, H >> l, None, hats[l], None), "level")
+                W >> l, H >> l, None, hats[l], None, status=fr.status), "level")
         out = fr.hdr[state["parity"]]
         prev = state["prev"]
-        if prev is None:  # first frame of the run: no previous output yet
-            prev_t, mv_t, mask_t = None, None, None
-        else:
-            prev_t, mv_t, mask_t = prev, x["mv"], x["mask"]
+        if prev is not None:  # the first frame of the run has no previous output
+            Bnd.check(spp.spp_warp_previous(prev, x["mv"], W, H, warped), "warp")
         if timed_l0:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        Bnd.check(spp.spp_reconstruct_level(fr.layers[0], x["logits"][0], 54, hats[1], prev_t,
-                                            mv_t, mask_t, W, H, tm, out, fr.ldr), "level 0")
+        Bnd.check(spp.spp_reconstruct_level(fr.layers[0], x["logits"][0], 54, hats[1],
+                                            warped if prev is not None else None,
+                                            x["mask"] if prev is not None else None, W, H, tm, out,
+                                            fr.ldr, status=fr.status), "level 0")
         if timed_l0:
             e1.record(stream)
             ev_l0.append((e0, e1))
@@ -324,7 +329,7 @@ def run_ours(args, rank, world, local):
                    for k in range(args.steps)) / args.steps
     peaks, peak_kind = measured_peaks()
     achieved = l0_bytes / (l0_avg / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "recon_kernel<UP,TEMP,TONE> (level 0)",
+    roofline = {"bound": "hbm", "kernel": "recon_tma_kernel<54,UP,TEMP,TONE,3> (level 0)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
                 "traffic": None, "algorithmic_bytes_per_launch": l0_bytes,

@@ -193,35 +193,52 @@ int spp_splat_samples(const int32_t *offsets, const float *rgb, const float *s,
                       float *const *layers, cudaStream_t stream);
 
 /* ---------------------------------------- a6-a9: reconstruction, tau */
-/* Workspace bytes of spp_reconstruct_frame (the denoised levels 1..L-1). */
+/* Workspace bytes of spp_reconstruct_frame (the denoised levels 1..L-1 and
+ * the warped previous frame). */
 size_t spp_reconstruct_workspace_bytes(int W, int H, int L);
+
+/*
+ * W_t L_{t-1}: the previous HDR output warped along the motion vectors
+ * (App. A, Eq. app-recon-full; Sec. 6.1).  warped(x, y) is the bilinear sample
+ * of prev_hdr at (x + mv_x, y + mv_y), pixel centres at integer coordinates,
+ * the position clamped to [0, W-1] x [0, H-1].
+ *   prev_hdr [3][H][W]; mv [2][H][W] in pixels, current -> previous;
+ *   warped   [3][H][W] output.
+ */
+int spp_warp_previous(const float *prev_hdr, const float *mv, int W, int H, float *warped,
+                      cudaStream_t stream);
 
 /*
  * One level of the coarse-to-fine reconstruction (Appendix A):
  * Eq. app-recon-coarse when coarse == NULL, Eq. app-recon-mid otherwise, and
- * Eq. app-recon-full when prev_hdr != NULL.  The joint softmax (Eq.
+ * Eq. app-recon-full when warped_prev != NULL.  The joint softmax (Eq.
  * app-softmax-mid, app-softmax-full) spans the 25 denoise logits, the 4
  * upsampling logits when coarse != NULL, and the 25 temporal logits when
- * prev_hdr != NULL and mask is 0 at the pixel.
+ * warped_prev != NULL and mask is 0 at the pixel.
  *
  *   noisy     [3][Hl][Wl] noisy level L^l.
  *   logits    [C][Hl][Wl]: channels 0..24 denoise tap (i,j) at (j+2)*5+(i+2);
  *             25..28 upsampling tap (i,j) at 25+2j+i; 29..53 temporal taps.
  *             C >= 25, >= 29 with coarse, == 54 with prev_hdr.
  *   coarse    [3][Hl/2][Wl/2] denoised L-hat^{l+1}, or NULL at the coarsest level.
- *   prev_hdr  [3][Hl][Wl] previous HDR output, or NULL (no temporal term).
- *   mv        [2][Hl][Wl] motion in pixels, current -> previous (needed with prev_hdr).
+ *   warped_prev [3][Hl][Wl] W_t L_{t-1} from spp_warp_previous, or NULL (no
+ *             temporal term).
  *   mask      [Hl][Wl] uint8, nonzero = disoccluded (drops the temporal
  *             logits), or NULL.
  *   tm        tone map for out_ldr, or NULL for the defaults.
  *   out       [3][Hl][Wl] reconstructed HDR level.
  *   out_ldr   [3][Hl][Wl] sRGB(tau(...)) of out (Sec. 5), or NULL.
+ *   status    device int32 status word, or NULL; a bounded wait of the
+ *             pipelined kernel that gave up records SPP_ERR_TIMEOUT there.
  * Borders clamp to the edge; the upsampling taps read floor((x+i)/2),
  * floor((y+j)/2) of the coarser level as printed in Eq. app-upsample.
+ * Levels whose width is a multiple of 4 run a persistent kernel fed by bulk
+ * tensor copies (TMA) through a multi-stage shared-memory pipeline; other
+ * widths run a direct kernel.  Both compute the same values.
  */
 int spp_reconstruct_level(const float *noisy, const float *logits, int C, const float *coarse,
-                          const float *prev_hdr, const float *mv, const uint8_t *mask, int Wl,
-                          int Hl, const spp_tonemap *tm, float *out, float *out_ldr,
+                          const float *warped_prev, const uint8_t *mask, int Wl, int Hl,
+                          const spp_tonemap *tm, float *out, float *out_ldr, int32_t *status,
                           cudaStream_t stream);
 
 /*
@@ -231,13 +248,16 @@ int spp_reconstruct_level(const float *noisy, const float *logits, int C, const 
  *   logits   host array of L pointers: logits[L-1] has 25 channels, logits[l]
  *            for 0 < l < L-1 has 29, logits[0] has C0 (29, or 54 with temporal).
  *   C0       channels of logits[0]: 29 or 54.  prev_hdr != NULL needs 54.
+ *   prev_hdr [3][H][W] previous HDR output or NULL; mv [2][H][W] with it.
+ *            The frame call warps it (spp_warp_previous) into the workspace.
  *   L        pyramid levels, 2..5.
  *   out_hdr  [3][H][W]; out_ldr [3][H][W] or NULL.
+ *   status   device int32 status word, or NULL (see spp_reconstruct_level).
  */
 int spp_reconstruct_frame(const float *const *layers, const float *const *logits, int C0,
                           const float *prev_hdr, const float *mv, const uint8_t *mask, int W,
                           int H, int L, const spp_tonemap *tm, float *out_hdr, float *out_ldr,
-                          void *ws, size_t ws_bytes, cudaStream_t stream);
+                          void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

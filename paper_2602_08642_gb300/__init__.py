@@ -13,5 +13,6 @@ from ._binding import (  # noqa: F401
     spp_alloc_sample_map_static,
     spp_alloc_workspace_bytes, spp_clear_status, spp_get_status, spp_launch_count,
     spp_reconstruct_frame, spp_reconstruct_level, spp_reconstruct_workspace_bytes,
+    spp_warp_previous,
     spp_render_synthetic, spp_splat_samples, spp_strerror)
 from .pipeline import Frame, default_capacity, logit_channels  # noqa: F401

@@ -73,10 +73,11 @@ _SIGS = {
     "spp_render_synthetic": (_I, [_P, _P, _P, _P, _I64, _I, _I, _U64, _U32, _P, _P]),
     "spp_splat_samples": (_I, [_P, _P, _P, _P, _I64, _I, _I, _I, _P, _P]),
     "spp_reconstruct_workspace_bytes": (_SZ, [_I, _I, _I]),
-    "spp_reconstruct_level": (_I, [_P, _P, _I, _P, _P, _P, _P, _I, _I,
-                                   ctypes.POINTER(spp_tonemap), _P, _P, _P]),
+    "spp_warp_previous": (_I, [_P, _P, _I, _I, _P, _P]),
+    "spp_reconstruct_level": (_I, [_P, _P, _I, _P, _P, _P, _I, _I,
+                                   ctypes.POINTER(spp_tonemap), _P, _P, _P, _P]),
     "spp_reconstruct_frame": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _I,
-                                   ctypes.POINTER(spp_tonemap), _P, _P, _P, _SZ, _P]),
+                                   ctypes.POINTER(spp_tonemap), _P, _P, _P, _SZ, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -194,17 +195,22 @@ def spp_reconstruct_workspace_bytes(W: int, H: int, L: int) -> int:
     return int(lib.spp_reconstruct_workspace_bytes(W, H, L))
 
 
-def spp_reconstruct_level(noisy, logits, C, coarse, prev_hdr, mv, mask, Wl, Hl, tm, out, out_ldr,
-                          stream=None) -> int:
+def spp_warp_previous(prev_hdr, mv, W, H, warped, stream=None) -> int:
+    return lib.spp_warp_previous(_dev(prev_hdr, torch.float32), _dev(mv, torch.float32), W, H,
+                                 _dev(warped, torch.float32), _stream(stream))
+
+
+def spp_reconstruct_level(noisy, logits, C, coarse, warped_prev, mask, Wl, Hl, tm, out, out_ldr,
+                          status=None, stream=None) -> int:
     return lib.spp_reconstruct_level(
         _dev(noisy, torch.float32), _dev(logits, torch.float32), C, _dev(coarse, torch.float32),
-        _dev(prev_hdr, torch.float32), _dev(mv, torch.float32), _dev(mask, torch.uint8), Wl, Hl,
+        _dev(warped_prev, torch.float32), _dev(mask, torch.uint8), Wl, Hl,
         ctypes.byref(tm) if tm is not None else None, _dev(out, torch.float32),
-        _dev(out_ldr, torch.float32), _stream(stream))
+        _dev(out_ldr, torch.float32), _dev(status, torch.int32), _stream(stream))
 
 
 def spp_reconstruct_frame(layers, logits, C0, prev_hdr, mv, mask, W, H, L, tm, out_hdr, out_ldr,
-                          ws, stream=None) -> int:
+                          ws, status=None, stream=None) -> int:
     la = _ptr_array(layers, torch.float32)
     lo = _ptr_array(logits, torch.float32)
     return lib.spp_reconstruct_frame(
@@ -212,4 +218,5 @@ def spp_reconstruct_frame(layers, logits, C0, prev_hdr, mv, mask, W, H, L, tm, o
         _dev(mv, torch.float32), _dev(mask, torch.uint8), W, H, L,
         ctypes.byref(tm) if tm is not None else None, _dev(out_hdr, torch.float32),
         _dev(out_ldr, torch.float32), _dev(ws) if ws is not None else None,
-        (ws.numel() * ws.element_size()) if ws is not None else 0, _stream(stream))
+        (ws.numel() * ws.element_size()) if ws is not None else 0, _dev(status, torch.int32),
+        _stream(stream))

@@ -23,10 +23,8 @@ namespace spp {
 namespace {
 
 constexpr int kSumThreads = 256;
-constexpr int kWindows = 8;      // 32-bit windows of the 2^-149-scaled integer value
-constexpr int kLimbs = 9;        // per-thread limb accumulators (32-bit weights)
-constexpr int kWords = 11;       // carry-propagated 32-bit words of the total
-constexpr int kFlushEvery = 256; // elements per window before it is split into limbs
+constexpr int kLimbs = 11;       // per-thread limb accumulators (32-bit weights)
+constexpr int kWords = 13;       // carry-propagated 32-bit words of the total
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -56,7 +54,35 @@ struct BudgetArgs {
 };
 
 // ---------------------------------------------------------------- K1
-__device__ __forceinline__ void accum_value(float x, unsigned long long (&win)[kWindows],
+// Every finite FP32 x >= 0 is m 2^(pos - 149) with an integer m < 2^24 and
+// pos in [0, 253].  A thread keeps a 128-bit integer sum of m 2^(pos - 32 b)
+// for the elements whose 32-bit window pos >> 5 is b or b + 1 (one add with
+// carry per element); an element outside that span first moves the sum into
+// the thread's 32-bit limbs (limb j weighs 2^(32 j - 149)) and re-bases.
+struct ExactAcc {
+    unsigned long long lo, hi;
+    int b;
+};
+
+__device__ __forceinline__ void acc_flush(ExactAcc &A, unsigned long long (&lim)[kLimbs]) {
+    if (A.b >= 0) {
+        const unsigned long long c0 = A.lo & 0xffffffffull, c1 = A.lo >> 32;
+        const unsigned long long c2 = A.hi & 0xffffffffull, c3 = A.hi >> 32;
+#pragma unroll
+        for (int j = 0; j < kLimbs; ++j) {
+            unsigned long long v = 0ull;
+            v += (j == A.b) ? c0 : 0ull;
+            v += (j == A.b + 1) ? c1 : 0ull;
+            v += (j == A.b + 2) ? c2 : 0ull;
+            v += (j == A.b + 3) ? c3 : 0ull;
+            lim[j] += v;
+        }
+    }
+    A.lo = 0ull;
+    A.hi = 0ull;
+}
+
+__device__ __forceinline__ void accum_value(float x, ExactAcc &A, unsigned long long (&lim)[kLimbs],
                                             bool &bad) {
     const uint32_t bits = __float_as_uint(x);
     const uint32_t mag = bits & 0x7fffffffu;
@@ -65,32 +91,27 @@ __device__ __forceinline__ void accum_value(float x, unsigned long long (&win)[k
         return;
     }
     const uint32_t e = mag >> 23;
-    const uint32_t m = (mag & 0x7fffffu) | (e ? 0x800000u : 0u);
-    const uint32_t pos = e ? e - 1u : 0u;  // x = m 2^(pos - 149)
-    const unsigned long long val = static_cast<unsigned long long>(m) << (pos & 31u);
-    const uint32_t w = pos >> 5;
-#pragma unroll
-    for (int j = 0; j < kWindows; ++j) win[j] += (w == static_cast<uint32_t>(j)) ? val : 0ull;
-}
-
-__device__ __forceinline__ void flush_windows(unsigned long long (&win)[kWindows],
-                                              unsigned long long (&lim)[kLimbs]) {
-#pragma unroll
-    for (int j = 0; j < kWindows; ++j) {
-        lim[j] += win[j] & 0xffffffffull;
-        lim[j + 1] += win[j] >> 32;
-        win[j] = 0ull;
+    const unsigned long long m = (mag & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int pos = e ? static_cast<int>(e) - 1 : 0;  // x = m 2^(pos - 149)
+    const int w = pos >> 5;
+    if (w < A.b || w > A.b + 1) {  // rare for data spanning < 2^32 in range
+        acc_flush(A, lim);
+        A.b = w > 0 ? w - 1 : 0;
     }
+    const int sh = pos - 32 * A.b;  // 0 .. 63
+    const unsigned long long vlo = m << sh;
+    const unsigned long long vhi = sh > 40 ? (m >> (64 - sh)) : 0ull;
+    A.lo += vlo;
+    A.hi += vhi + (A.lo < vlo ? 1ull : 0ull);
 }
 
-__device__ __forceinline__ int word_bit(const uint32_t *w, int b) {
-    return b < 0 ? 0 : static_cast<int>((w[b >> 5] >> (b & 31)) & 1u);
-}
-
-// Correctly rounded FP64 value of the exact total (single thread).
+// Correctly rounded FP64 value of the exact total (single thread): carry the
+// limbs into 32-bit words, take the 64 bits below the leading one, round to
+// nearest even with the remaining bits as sticky.
 __device__ double round_limbs(const unsigned long long *limbs) {
     uint32_t w[kWords];
     unsigned long long carry = 0ull;
+#pragma unroll
     for (int j = 0; j < kLimbs; ++j) {
         const unsigned long long v = limbs[j] + carry;
         w[j] = static_cast<uint32_t>(v & 0xffffffffull);
@@ -98,21 +119,35 @@ __device__ double round_limbs(const unsigned long long *limbs) {
     }
     w[kLimbs] = static_cast<uint32_t>(carry & 0xffffffffull);
     w[kLimbs + 1] = static_cast<uint32_t>(carry >> 32);
-    int top = -1;
-    for (int j = kWords - 1; j >= 0; --j)
-        if (w[j]) { top = j; break; }
-    if (top < 0) return 0.0;
-    const int P = 32 * top + 31 - __clz(w[top]);  // highest set bit
-    if (P <= 52) {
+    int t = -1;
+#pragma unroll
+    for (int j = 0; j < kWords; ++j)
+        if (w[j]) t = j;
+    if (t < 0) return 0.0;
+    if (t <= 1) {  // below 2^64 units of 2^-149: convert in two exact steps
         const unsigned long long x =
             static_cast<unsigned long long>(w[0]) | (static_cast<unsigned long long>(w[1]) << 32);
-        return __dmul_rn(__ull2double_rn(x), 0x1p-149);  // exact
+        if ((x >> 53) == 0ull) return __dmul_rn(__ull2double_rn(x), 0x1p-149);
     }
-    unsigned long long mant = 0ull;
-    for (int b = P; b >= P - 52; --b) mant = (mant << 1) | static_cast<unsigned long long>(word_bit(w, b));
-    const int rbit = word_bit(w, P - 53);
-    int sticky = 0;
-    for (int b = P - 54; b >= 0 && !sticky; --b) sticky |= word_bit(w, b);
+    uint32_t w1 = 0u, w2 = 0u, below = 0u;
+#pragma unroll
+    for (int j = 0; j < kWords; ++j) {
+        if (j == t - 1) w1 = w[j];
+        if (j == t - 2) w2 = w[j];
+        if (j < t - 2) below |= w[j];
+    }
+    const int lz = __clz(w[t]);
+    unsigned long long a = (static_cast<unsigned long long>(w[t]) << 32) | w1;
+    uint32_t b = w2;
+    if (lz > 0) {
+        a = (a << lz) | static_cast<unsigned long long>(b >> (32 - lz));
+        b = b << lz;
+    }
+    // a holds the leading 64 bits (bit 63 set); value = a 2^(P - 63 - 149)
+    const int P = 32 * t + 31 - lz;
+    unsigned long long mant = a >> 11;
+    const unsigned long long rbit = (a >> 10) & 1ull;
+    const bool sticky = (a & 0x3ffull) != 0ull || b != 0u || below != 0u;
     int exp2 = P - 149;  // value = mant 2^(exp2 - 52)
     if (rbit && (sticky || (mant & 1ull))) {
         ++mant;
@@ -126,11 +161,8 @@ __device__ double round_limbs(const unsigned long long *limbs) {
     return __longlong_as_double(static_cast<long long>(bits));
 }
 
-__device__ void finalize_budget(AllocHeader *hdr, long long N, const BudgetArgs &args,
-                                int32_t *status) {
-    unsigned long long limbs[kLimbs];
-    for (int j = 0; j < kLimbs; ++j) limbs[j] = atomicAdd(&hdr->limbs[j], 0ull);
-    const int bad = atomicAdd(&hdr->bad_input, 0);
+__device__ void finalize_budget(AllocHeader *hdr, const unsigned long long *limbs, int bad,
+                                long long N, const BudgetArgs &args, int32_t *status) {
     const double S = round_limbs(limbs);
     hdr->S = S;
     if (bad || !(S > 0.0)) {
@@ -167,32 +199,65 @@ __device__ void finalize_budget(AllocHeader *hdr, long long N, const BudgetArgs 
 __global__ void __launch_bounds__(kSumThreads)
 budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, BudgetArgs args,
                   int32_t *status) {
-    unsigned long long win[kWindows];
     unsigned long long lim[kLimbs];
 #pragma unroll
-    for (int j = 0; j < kWindows; ++j) win[j] = 0ull;
-#pragma unroll
     for (int j = 0; j < kLimbs; ++j) lim[j] = 0ull;
+    ExactAcc A;
+    A.lo = 0ull;
+    A.hi = 0ull;
+    A.b = -100;
     bool bad = false;
-    int cnt = 0;
     const long long nthreads = static_cast<long long>(gridDim.x) * blockDim.x;
     const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const long long n4 = N >> 2;
     const float4 *d4 = reinterpret_cast<const float4 *>(d);
-    for (long long q = gtid; q < n4; q += nthreads) {
-        const float4 v = __ldg(d4 + q);
-        accum_value(v.x, win, bad);
-        accum_value(v.y, win, bad);
-        accum_value(v.z, win, bad);
-        accum_value(v.w, win, bad);
-        cnt += 4;
-        if (cnt >= kFlushEvery) {
-            flush_windows(win, lim);
-            cnt = 0;
+    // eight independent vector loads in flight per thread and iteration; a
+    // warp whose 256 values all lie in the accumulators' span (the common
+    // case) takes the short path, decided by a warp vote so that the re-basing
+    // code stays out of it
+    for (long long q0 = gtid; q0 < n4; q0 += 8 * nthreads) {
+        float4 v4[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const long long q = q0 + r * nthreads;
+            v4[r] = q < n4 ? __ldg(d4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float *v = reinterpret_cast<const float *>(v4);
+        int wmin = 1 << 20, wmax = -(1 << 20);
+        bool ok = true;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const uint32_t bits = __float_as_uint(v[r]);
+            const uint32_t mag = bits & 0x7fffffffu;
+            ok &= mag < 0x7f800000u && bits == mag;  // finite, not negative
+            if (mag != 0u) {
+                const uint32_t e = mag >> 23;
+                const int w = (e ? static_cast<int>(e) - 1 : 0) >> 5;
+                wmin = min(wmin, w);
+                wmax = max(wmax, w);
+            }
+        }
+        ok &= wmin >= A.b && wmax <= A.b + 1;
+        if (__all_sync(__activemask(), ok)) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t mag = __float_as_uint(v[r]);
+                const uint32_t e = mag >> 23;
+                const unsigned long long m = (mag & 0x7fffffu) | (e ? 0x800000u : 0u);
+                const int sh = (e ? static_cast<int>(e) - 1 : 0) - 32 * A.b;
+                const unsigned long long vlo = m << (sh & 63);
+                const unsigned long long vhi = sh > 40 ? (m >> (64 - sh)) : 0ull;
+                const bool nz = mag != 0u;
+                A.lo += nz ? vlo : 0ull;
+                A.hi += (nz ? vhi : 0ull) + (A.lo < (nz ? vlo : 0ull) ? 1ull : 0ull);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) accum_value(v[r], A, lim, bad);
         }
     }
-    for (long long i = (n4 << 2) + gtid; i < N; i += nthreads) accum_value(d[i], win, bad);
-    flush_windows(win, lim);
+    for (long long i = (n4 << 2) + gtid; i < N; i += nthreads) accum_value(d[i], A, lim, bad);
+    acc_flush(A, lim);
 
     __shared__ unsigned long long s_part[kSumThreads / 32][kLimbs];
     __shared__ int s_last;
@@ -218,9 +283,16 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
         s_last = (t == gridDim.x - 1u) ? 1 : 0;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last) {
+        // the last block gathers the limbs in parallel, then one thread rounds
+        __shared__ unsigned long long s_limbs[kLimbs];
+        __shared__ int s_bad;
         __threadfence();
-        finalize_budget(hdr, N, args, status);
+        if (threadIdx.x < kLimbs)
+            s_limbs[threadIdx.x] = *reinterpret_cast<volatile unsigned long long *>(&hdr->limbs[threadIdx.x]);
+        if (threadIdx.x == kLimbs) s_bad = *reinterpret_cast<volatile int *>(&hdr->bad_input);
+        __syncthreads();
+        if (threadIdx.x == 0) finalize_budget(hdr, s_limbs, s_bad, N, args, status);
     }
 }
 
@@ -237,27 +309,35 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+struct PixelOut {
+    int n;
+    float w, s;
+};
+
 // FP64 sequence, operation for operation the definition of Sec. 3 and 4.2-4.3.
-__device__ __noinline__ void assign_exact(float d, uint64_t bits, const Coef &k, int &n, float &w,
-                                          float &s) {
+// Returned by value so that the caller's per-item arrays stay in registers.
+__device__ __noinline__ PixelOut assign_exact(float d, uint64_t bits, double ka, double kc,
+                                              double klam, double kh, int hard) {
     const double u = __dmul_rn(__ull2double_rn(bits >> 16), 0x1p-48);
-    const double m = __dmul_rn(k.c, static_cast<double>(d));
-    const double sd = __dadd_rn(k.a, m);
+    const double m = __dmul_rn(kc, static_cast<double>(d));
+    const double sd = __dadd_rn(ka, m);
     const double f = floor(sd);
     const double p = __dsub_rn(sd, f);
     const double t = __dsub_rn(1.0, p);
     const bool extra = (p > 0.0) && (u > t);
     double wd = 1.0;
-    if (extra && !k.hard) {
-        const double q = __ddiv_rn(k.lam, p);
+    if (extra && !hard) {
+        const double q = __ddiv_rn(klam, p);
         const double v = __dsub_rn(__dadd_rn(u, p), 1.0);
         double r = __dmul_rn(q, v);
         r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
-        wd = __dmul_rn(k.h, r);
+        wd = __dmul_rn(kh, r);
     }
-    n = static_cast<int>(f) + (extra ? 1 : 0);
-    w = __double2float_rn(wd);
-    s = __double2float_rn(sd);
+    PixelOut r;
+    r.n = static_cast<int>(f) + (extra ? 1 : 0);
+    r.w = __double2float_rn(wd);
+    r.s = __double2float_rn(sd);
+    return r;
 }
 
 // Float-float filter.  Returns false when a decision is within the margin of
@@ -294,7 +374,7 @@ __device__ __forceinline__ bool assign_fast(float d, uint64_t bits, const Coef &
     const bool extra = v > 0.0f;
     float wf = 1.0f;
     if (extra && !k.hard) {
-        float r = __fmul_rn(__fdiv_rn(k.lam_f, plow), v);
+        float r = __fmul_rn(__fdividef(k.lam_f, plow), v);  // 2-ulp quotient suffices for w
         r = fminf(fmaxf(r, 0.0f), 1.0f);
         wf = __fmul_rn(k.h_f, r);
     }
@@ -312,7 +392,7 @@ __device__ __forceinline__ void st_state(unsigned long long *p, unsigned long lo
     atomicExch(p, v);
 }
 
-__global__ void __launch_bounds__(kScanThreads)
+__global__ void __launch_bounds__(kScanThreads, 4)
 assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *hdr_c,
                    AllocHeader *hdr, unsigned long long *tile_state, uint64_t key, int hard,
                    int stall_tile1,
@@ -366,9 +446,19 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
         sv[q] = 1.0f;
         if (i < N && valid) {
             const uint64_t bits = stream_bits(key, static_cast<uint64_t>(i));
+            int nq = 0;
+            float wq = 1.0f, sq = 1.0f;
             bool done = false;
-            if (k.fast) done = assign_fast(dv[q], bits, k, n[q], wv[q], sv[q]);
-            if (!done) assign_exact(dv[q], bits, k, n[q], wv[q], sv[q]);
+            if (k.fast) done = assign_fast(dv[q], bits, k, nq, wq, sq);
+            if (!done) {
+                const PixelOut r = assign_exact(dv[q], bits, k.a, k.c, k.lam, k.h, k.hard);
+                nq = r.n;
+                wq = r.w;
+                sq = r.s;
+            }
+            n[q] = nq;
+            wv[q] = wq;
+            sv[q] = sq;
         }
         tsum += n[q];
     }
@@ -383,6 +473,9 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
     }
     if (lane == 31) s_warp_tot[warp] = incl;
     __syncthreads();
+    __shared__ int s_agg;
+    __shared__ int s_first[kScanThreads / 32];
+    __shared__ int s_part[kScanThreads / 32];
     if (warp == 0) {
         const int wt = lane < kScanThreads / 32 ? s_warp_tot[lane] : 0;
         int wincl = wt;
@@ -393,49 +486,58 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
         }
         if (lane < kScanThreads / 32) s_warp_excl[lane] = wincl - wt;
         const int agg = __shfl_sync(0xffffffffu, wincl, kScanThreads / 32 - 1);
-        // decoupled look-back over the predecessors, 32 at a time
-        long long excl = 0;
-        if (stall_tile1 && tile == 1) {
-            // test of the bounded waits: publish nothing
-        } else if (tile == 0) {
-            if (lane == 0) st_state(&tile_state[0], kFlagInc | static_cast<unsigned int>(agg));
-        } else {
-            if (lane == 0) st_state(&tile_state[tile], kFlagAgg | static_cast<unsigned int>(agg));
-            int j = tile - 1;
-            while (true) {
-                const int idx = j - lane;
-                unsigned long long st = kFlagInc;
-                if (idx >= 0) {
-                    st = ld_state(&tile_state[idx]);
-                    int spins = 0;
-                    while ((st >> 62) == 0ull) {
-                        if (++spins > kSpinLimit) {
-                            set_status(status, SPP_ERR_TIMEOUT);
-                            st = kFlagInc;
-                            break;
-                        }
-                        __nanosleep(64);
-                        st = ld_state(&tile_state[idx]);
-                    }
-                }
-                const unsigned inc = __ballot_sync(0xffffffffu, (st >> 62) == 2ull);
-                int val = static_cast<int>(st & 0xffffffffull);
-                if (inc) {
-                    const int first = __ffs(inc) - 1;
-                    if (lane > first) val = 0;
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) val += __shfl_down_sync(0xffffffffu, val, off);
-                excl += __shfl_sync(0xffffffffu, val, 0);
-                if (inc) break;
-                j -= 32;
-            }
-            if (lane == 0)
-                st_state(&tile_state[tile],
-                         kFlagInc | static_cast<unsigned int>(excl + static_cast<long long>(agg)));
+        if (lane == 0) {
+            s_agg = agg;
+            if (!(stall_tile1 && tile == 1))  // the test of the bounded waits publishes nothing
+                st_state(&tile_state[tile], (tile == 0 ? kFlagInc : kFlagAgg) |
+                                                static_cast<unsigned int>(agg));
         }
-        if (lane == 0) s_prefix = static_cast<int>(excl);
     }
+    __syncthreads();
+    // decoupled look-back with the whole block: each round reads the states of
+    // the 256 nearest predecessors not yet accounted for and stops at the
+    // nearest one that already holds an inclusive prefix
+    long long excl = 0;
+    if (tile > 0) {
+        int j = tile - 1;
+        while (true) {
+            const int idx = j - static_cast<int>(threadIdx.x);
+            unsigned long long st = kFlagInc;  // before tile 0: an empty inclusive prefix
+            if (idx >= 0) {
+                st = ld_state(&tile_state[idx]);
+                int spins = 0;
+                while ((st >> 62) == 0ull) {
+                    if (++spins > kSpinLimit) {
+                        set_status(status, SPP_ERR_TIMEOUT);
+                        st = kFlagInc;
+                        break;
+                    }
+                    __nanosleep(64);
+                    st = ld_state(&tile_state[idx]);
+                }
+            }
+            const unsigned inc = __ballot_sync(0xffffffffu, (st >> 62) == 2ull);
+            if (lane == 0) s_first[warp] = inc ? warp * 32 + __ffs(inc) - 1 : 0x7fffffff;
+            __syncthreads();
+            int first = 0x7fffffff;
+#pragma unroll
+            for (int w = 0; w < kScanThreads / 32; ++w) first = min(first, s_first[w]);
+            int val = static_cast<int>(threadIdx.x) <= first ? static_cast<int>(st & 0xffffffffull) : 0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) val += __shfl_down_sync(0xffffffffu, val, off);
+            if (lane == 0) s_part[warp] = val;
+            __syncthreads();
+#pragma unroll
+            for (int w = 0; w < kScanThreads / 32; ++w) excl += s_part[w];
+            __syncthreads();  // s_first / s_part are reused by the next round
+            if (first != 0x7fffffff) break;
+            j -= kScanThreads;
+        }
+        if (threadIdx.x == 0 && !(stall_tile1 && tile == 1))
+            st_state(&tile_state[tile],
+                     kFlagInc | static_cast<unsigned int>(excl + static_cast<long long>(s_agg)));
+    }
+    if (threadIdx.x == 0) s_prefix = static_cast<int>(excl);
     __syncthreads();
 
     int run = s_prefix + s_warp_excl[warp] + (incl - tsum);
@@ -547,7 +649,7 @@ int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int3
 
     const long long per_block = static_cast<long long>(kSumThreads) * 32;
     long long grid = (N + per_block - 1) / per_block;
-    const long long max_grid = static_cast<long long>(sm_count()) * 4;
+    const long long max_grid = static_cast<long long>(sm_count()) * 8;
     if (grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
     budget_sum_kernel<<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(d, N, hdr, args,

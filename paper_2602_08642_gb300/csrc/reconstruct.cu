@@ -2,14 +2,16 @@
 // the temporal term over the bilinearly reprojected previous output and the
 // filmic tone map + sRGB epilogue (Sec. 5).
 //
-// One kernel per pyramid level.  A block owns a 32 x 8 pixel tile: it stages
-// the noisy level's tile plus a 2-pixel halo in shared memory and, at full
-// resolution, the warped previous frame W_t L_{t-1} on the same halo (each
-// halo pixel warped with its own motion vector), so that the 5 x 5 gathers
-// read shared memory.  The per-pixel logits (the dominant HBM stream: 54
-// planes at full resolution) are read once, coalesced along x, and the joint
-// softmax is evaluated in registers.
-#include "spp_internal.cuh"
+// One launch per pyramid level.  Levels whose row pitch is a multiple of 16
+// bytes run the TMA-pipelined persistent kernel (reconstruct_tma.cu); the
+// others run the direct kernel below.  In the direct kernel a block owns a
+// 32 x 8 pixel tile: it stages the noisy level's tile plus a 2-pixel halo in
+// shared memory and, at full resolution, the warped previous frame
+// W_t L_{t-1} on the same halo (each halo pixel warped with its own motion
+// vector), so that the 5 x 5 gathers read shared memory.  The per-pixel
+// logits are read once, coalesced along x, and the joint softmax is evaluated
+// in registers.
+#include "recon_common.cuh"
 
 namespace spp {
 namespace {
@@ -19,33 +21,13 @@ constexpr int kTY = 8;
 constexpr int kHalo = 2;
 constexpr int kHX = kTX + 2 * kHalo;
 constexpr int kHY = kTY + 2 * kHalo;
-constexpr float kLog2e = 1.4426950408889634f;
-
-struct ToneArgs {
-    float alpha, beta, k, s, h;
-};
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-
-// tau of Sec. 5: exponential toe below s-1, linear middle, exponential shoulder
-// above 1-h.
-__device__ __forceinline__ float tau_curve(float x, float s, float h) {
-    if (x < s - 1.0f) return 0.5f * s * __expf((x + 1.0f - s) / s);
-    if (x < 1.0f - h) return 0.5f * (1.0f + x);
-    return 1.0f - 0.5f * h * __expf(-(x + h - 1.0f) / h);
-}
-
-// IEC 61966-2-1 sRGB encoding.
-__device__ __forceinline__ float srgb(float v) {
-    return v <= 0.0031308f ? 12.92f * v : 1.055f * __powf(v, 1.0f / 2.4f) - 0.055f;
-}
 
 template <bool UP, bool TEMP, bool TONE>
 __global__ void __launch_bounds__(kTX *kTY, 2)
 recon_kernel(const float *__restrict__ noisy, const float *__restrict__ logits,
-             const float *__restrict__ coarse, const float *__restrict__ prev,
-             const float *__restrict__ mv, const uint8_t *__restrict__ mask, int Wl, int Hl,
-             float *__restrict__ out, float *__restrict__ out_ldr, ToneArgs tm) {
+             const float *__restrict__ coarse, const float *__restrict__ warped,
+             const uint8_t *__restrict__ mask, int Wl, int Hl, float *__restrict__ out,
+             float *__restrict__ out_ldr, ToneArgs tm) {
     static_assert(!TEMP || UP, "the temporal term lives at full resolution, below a coarser level");
     constexpr int kSpatial = 25 + (UP ? 4 : 0);
     constexpr int kNK = kSpatial + (TEMP ? 25 : 0);
@@ -79,7 +61,7 @@ recon_kernel(const float *__restrict__ noisy, const float *__restrict__ logits,
     }
 
     // stage the noisy tile (+ halo) and, at full resolution, the warped
-    // previous frame on the same halo
+    // previous frame on the same halo, clamped to the edge
     for (int idx = tid; idx < kHX * kHY; idx += kTX * kTY) {
         const int hx = idx % kHX, hy = idx / kHX;
         const int gx = clampi(bx0 + hx - kHalo, 0, Wl - 1);
@@ -89,27 +71,9 @@ recon_kernel(const float *__restrict__ noisy, const float *__restrict__ logits,
         sN[1][hy][hx] = __ldg(noisy + Nl + g);
         sN[2][hy][hx] = __ldg(noisy + 2 * Nl + g);
         if (TEMP) {
-            // W_t: bilinear at (gx + mv_x, gy + mv_y), pixel centres at
-            // integers, position clamped to the frame.  The fraction is taken
-            // from the motion vector itself so that it is exact.
-            const float mx = __ldg(mv + g), my = __ldg(mv + Nl + g);
-            float ix = fminf(fmaxf(floorf(mx), -1048576.0f), 1048576.0f);
-            float iy = fminf(fmaxf(floorf(my), -1048576.0f), 1048576.0f);
-            float fx = mx - floorf(mx), fy = my - floorf(my);
-            int X0 = gx + static_cast<int>(ix), Y0 = gy + static_cast<int>(iy);
-            if (X0 < 0) { X0 = 0; fx = 0.0f; } else if (X0 >= Wl - 1) { X0 = Wl - 1; fx = 0.0f; }
-            if (Y0 < 0) { Y0 = 0; fy = 0.0f; } else if (Y0 >= Hl - 1) { Y0 = Hl - 1; fy = 0.0f; }
-            const int X1 = X0 + 1 < Wl ? X0 + 1 : Wl - 1;
-            const int Y1 = Y0 + 1 < Hl ? Y0 + 1 : Hl - 1;
-            const long long r0 = static_cast<long long>(Y0) * Wl, r1 = static_cast<long long>(Y1) * Wl;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float *P = prev + c * Nl;
-                const float p00 = __ldg(P + r0 + X0), p10 = __ldg(P + r0 + X1);
-                const float p01 = __ldg(P + r1 + X0), p11 = __ldg(P + r1 + X1);
-                sW[c][hy][hx] = (1.0f - fy) * ((1.0f - fx) * p00 + fx * p10) +
-                                fy * ((1.0f - fx) * p01 + fx * p11);
-            }
+            sW[0][hy][hx] = __ldg(warped + g);
+            sW[1][hy][hx] = __ldg(warped + Nl + g);
+            sW[2][hy][hx] = __ldg(warped + 2 * Nl + g);
         }
     }
     __syncthreads();
@@ -173,31 +137,25 @@ recon_kernel(const float *__restrict__ noisy, const float *__restrict__ logits,
     __stcs(out + Nl + op, o1);
     __stcs(out + 2 * Nl + op, o2);
     if (TONE) {
-        // Sec. 5: x_c = alpha (mean + beta (ln L_c - mean) + k), then tau, sRGB
-        const float l0 = __logf(fmaxf(o0, 0x1p-24f));
-        const float l1 = __logf(fmaxf(o1, 0x1p-24f));
-        const float l2 = __logf(fmaxf(o2, 0x1p-24f));
-        const float mean = (l0 + l1 + l2) * (1.0f / 3.0f);
-        const float x0v = tm.alpha * (mean + tm.beta * (l0 - mean) + tm.k);
-        const float x1v = tm.alpha * (mean + tm.beta * (l1 - mean) + tm.k);
-        const float x2v = tm.alpha * (mean + tm.beta * (l2 - mean) + tm.k);
-        __stcs(out_ldr + op, srgb(tau_curve(x0v, tm.s, tm.h)));
-        __stcs(out_ldr + Nl + op, srgb(tau_curve(x1v, tm.s, tm.h)));
-        __stcs(out_ldr + 2 * Nl + op, srgb(tau_curve(x2v, tm.s, tm.h)));
+        float r, g, b;
+        tone_map(o0, o1, o2, tm, r, g, b);
+        __stcs(out_ldr + op, r);
+        __stcs(out_ldr + Nl + op, g);
+        __stcs(out_ldr + 2 * Nl + op, b);
     }
 }
 
 template <bool UP, bool TEMP>
 void launch_level(bool tone, dim3 grid, dim3 block, cudaStream_t st, const float *noisy,
-                  const float *logits, const float *coarse, const float *prev, const float *mv,
+                  const float *logits, const float *coarse, const float *warped,
                   const uint8_t *mask, int Wl, int Hl, float *out, float *out_ldr,
                   const ToneArgs &tm) {
     if (tone)
-        recon_kernel<UP, TEMP, true><<<grid, block, 0, st>>>(noisy, logits, coarse, prev, mv, mask,
+        recon_kernel<UP, TEMP, true><<<grid, block, 0, st>>>(noisy, logits, coarse, warped, mask,
                                                              Wl, Hl, out, out_ldr, tm);
     else
-        recon_kernel<UP, TEMP, false><<<grid, block, 0, st>>>(noisy, logits, coarse, prev, mv,
-                                                              mask, Wl, Hl, out, out_ldr, tm);
+        recon_kernel<UP, TEMP, false><<<grid, block, 0, st>>>(noisy, logits, coarse, warped, mask,
+                                                              Wl, Hl, out, out_ldr, tm);
 }
 
 ToneArgs tone_args(const spp_tonemap *tm) {
@@ -224,34 +182,51 @@ size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
 
 extern "C" {
 
+int spp_warp_previous(const float *prev_hdr, const float *mv, int W, int H, float *warped,
+                      cudaStream_t stream) {
+    using namespace spp;
+    if (W < 0 || H < 0 || !prev_hdr || !mv || !warped) return SPP_ERR_ARG;
+    if (!aligned16(prev_hdr) || !aligned16(mv) || !aligned16(warped)) return SPP_ERR_ALIGN;
+    if (static_cast<long long>(W) * H == 0) return SPP_OK;
+    launch_warp_prev(prev_hdr, mv, W, H, warped, stream);
+    count_launch();
+    return launch_status();
+}
+
 int spp_reconstruct_level(const float *noisy, const float *logits, int C, const float *coarse,
-                          const float *prev_hdr, const float *mv, const uint8_t *mask, int Wl,
-                          int Hl, const spp_tonemap *tm, float *out, float *out_ldr,
+                          const float *warped_prev, const uint8_t *mask, int Wl, int Hl,
+                          const spp_tonemap *tm, float *out, float *out_ldr, int32_t *status,
                           cudaStream_t stream) {
     using namespace spp;
     if (Wl < 0 || Hl < 0 || !noisy || !logits || !out) return SPP_ERR_ARG;
-    if (prev_hdr && (!coarse || !mv)) return SPP_ERR_ARG;
+    if (warped_prev && !coarse) return SPP_ERR_ARG;
     const int need = 25 + (coarse ? 4 : 0);
-    if (C < need || (prev_hdr && C < 54)) return SPP_ERR_ARG;
+    if (C < need || (warped_prev && C < 54)) return SPP_ERR_ARG;
     if (coarse && ((Wl & 1) || (Hl & 1))) return SPP_ERR_SHAPE;
     if (!aligned16(noisy) || !aligned16(logits) || !aligned16(out) ||
-        (coarse && !aligned16(coarse)) || (prev_hdr && !aligned16(prev_hdr)) ||
-        (mv && !aligned16(mv)) || (mask && !aligned16(mask)) || (out_ldr && !aligned16(out_ldr)))
+        (coarse && !aligned16(coarse)) || (warped_prev && !aligned16(warped_prev)) ||
+        (mask && !aligned16(mask)) || (out_ldr && !aligned16(out_ldr)) ||
+        (status && !aligned16(status)))
         return SPP_ERR_ALIGN;
     const ToneArgs ta = tone_args(tm);
     if (out_ldr && !tone_ok(ta)) return SPP_ERR_ARG;
     if (static_cast<long long>(Wl) * Hl == 0) return SPP_OK;
+    const int C_used = warped_prev ? 54 : (coarse ? 29 : 25);
+    int rc = SPP_OK;
+    if (launch_recon_tma(noisy, logits, C, C_used, coarse, warped_prev, mask, Wl, Hl, out, out_ldr,
+                         ta, status, stream, &rc))
+        return rc;
     dim3 block(kTX, kTY);
     dim3 grid((Wl + kTX - 1) / kTX, (Hl + kTY - 1) / kTY);
     const bool tone = out_ldr != nullptr;
     if (!coarse)
-        launch_level<false, false>(tone, grid, block, stream, noisy, logits, coarse, prev_hdr, mv,
+        launch_level<false, false>(tone, grid, block, stream, noisy, logits, coarse, warped_prev,
                                    mask, Wl, Hl, out, out_ldr, ta);
-    else if (!prev_hdr)
-        launch_level<true, false>(tone, grid, block, stream, noisy, logits, coarse, prev_hdr, mv,
+    else if (!warped_prev)
+        launch_level<true, false>(tone, grid, block, stream, noisy, logits, coarse, warped_prev,
                                   mask, Wl, Hl, out, out_ldr, ta);
     else
-        launch_level<true, true>(tone, grid, block, stream, noisy, logits, coarse, prev_hdr, mv,
+        launch_level<true, true>(tone, grid, block, stream, noisy, logits, coarse, warped_prev,
                                  mask, Wl, Hl, out, out_ldr, ta);
     count_launch();
     return launch_status();
@@ -259,7 +234,8 @@ int spp_reconstruct_level(const float *noisy, const float *logits, int C, const 
 
 size_t spp_reconstruct_workspace_bytes(int W, int H, int L) {
     if (W < 0 || H < 0 || L < 2 || L > 5) return 0;
-    size_t total = 0;
+    size_t total = spp::align256(3 * sizeof(float) * static_cast<size_t>(W) *
+                                 static_cast<size_t>(H));  // W_t L_{t-1}
     for (int l = 1; l < L; ++l)
         total += spp::align256(3 * sizeof(float) * static_cast<size_t>(W >> l) *
                                static_cast<size_t>(H >> l));
@@ -269,7 +245,7 @@ size_t spp_reconstruct_workspace_bytes(int W, int H, int L) {
 int spp_reconstruct_frame(const float *const *layers, const float *const *logits, int C0,
                           const float *prev_hdr, const float *mv, const uint8_t *mask, int W,
                           int H, int L, const spp_tonemap *tm, float *out_hdr, float *out_ldr,
-                          void *ws, size_t ws_bytes, cudaStream_t stream) {
+                          void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream) {
     using namespace spp;
     if (!layers || !logits || !out_hdr || W < 0 || H < 0) return SPP_ERR_ARG;
     if (L < 2 || L > 5) return SPP_ERR_SHAPE;
@@ -282,7 +258,8 @@ int spp_reconstruct_frame(const float *const *layers, const float *const *logits
     if (ws_bytes < need || (need && !ws)) return SPP_ERR_WORKSPACE;
     if (ws && !aligned16(ws)) return SPP_ERR_ALIGN;
     float *hat[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    size_t off = 0;
+    float *warped = static_cast<float *>(ws);
+    size_t off = align256(3 * sizeof(float) * static_cast<size_t>(W) * static_cast<size_t>(H));
     for (int l = 1; l < L; ++l) {
         hat[l] = reinterpret_cast<float *>(static_cast<char *>(ws) + off);
         off += align256(3 * sizeof(float) * static_cast<size_t>(W >> l) * static_cast<size_t>(H >> l));
@@ -290,12 +267,18 @@ int spp_reconstruct_frame(const float *const *layers, const float *const *logits
     for (int l = L - 1; l >= 1; --l) {
         const int C = (l == L - 1) ? 25 : 29;
         const int rc = spp_reconstruct_level(layers[l], logits[l], C, l == L - 1 ? nullptr : hat[l + 1],
-                                             nullptr, nullptr, nullptr, W >> l, H >> l, nullptr,
-                                             hat[l], nullptr, stream);
+                                             nullptr, nullptr, W >> l, H >> l, nullptr, hat[l],
+                                             nullptr, status, stream);
         if (rc != SPP_OK) return rc;
     }
-    return spp_reconstruct_level(layers[0], logits[0], C0, hat[1], prev_hdr, prev_hdr ? mv : nullptr,
-                                 prev_hdr ? mask : nullptr, W, H, tm, out_hdr, out_ldr, stream);
+    if (prev_hdr) {
+        if (!mv) return SPP_ERR_ARG;
+        const int rc = spp_warp_previous(prev_hdr, mv, W, H, warped, stream);
+        if (rc != SPP_OK) return rc;
+    }
+    return spp_reconstruct_level(layers[0], logits[0], C0, hat[1], prev_hdr ? warped : nullptr,
+                                 prev_hdr ? mask : nullptr, W, H, tm, out_hdr, out_ldr, status,
+                                 stream);
 }
 
 }  // extern "C"

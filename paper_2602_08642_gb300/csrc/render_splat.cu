@@ -64,38 +64,65 @@ splat_kernel(const int32_t *__restrict__ offsets, const float4 *__restrict__ rgb
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * kSplatTX, y0 = blockIdx.y * kSplatH;
     const long long N = static_cast<long long>(W) * H;
+    // all independent per-pixel loads of both rows first, then the samples
+    long long beg[kSplatRows], end[kSplatRows];
+    float wl[kSplatRows], si[kSplatRows];
+    bool in[kSplatRows];
+#pragma unroll
+    for (int r = 0; r < kSplatRows; ++r) {
+        const int x = x0 + tx, y = y0 + ty + kSplatTY * r;
+        in[r] = x < W && y < H;
+        beg[r] = 0;
+        end[r] = 0;
+        wl[r] = 1.0f;
+        si[r] = 1.0f;
+        if (in[r]) {
+            const long long i = static_cast<long long>(y) * W + x;
+            beg[r] = __ldg(offsets + i);
+            end[r] = __ldg(offsets + i + 1);
+            wl[r] = __ldg(hw + i);
+            si[r] = __ldg(s + i);
+        }
+    }
+    float4 first[kSplatRows], last[kSplatRows];
+#pragma unroll
+    for (int r = 0; r < kSplatRows; ++r) {
+        if (beg[r] < 0) beg[r] = 0;
+        if (end[r] > capacity) end[r] = capacity;
+        first[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        last[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (end[r] > beg[r]) {
+            last[r] = __ldcs(rgb + end[r] - 1);                       // the holdout slot
+            if (end[r] - beg[r] >= 2) first[r] = __ldcs(rgb + beg[r]);  // the first regular slot
+        }
+    }
 #pragma unroll
     for (int r = 0; r < kSplatRows; ++r) {
         const int ly = ty + kSplatTY * r;
-        const int x = x0 + tx, y = y0 + ly;
         float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-        if (x < W && y < H) {
-            const long long i = static_cast<long long>(y) * W + x;
-            long long beg = offsets[i];
-            long long end = offsets[i + 1];
-            if (beg < 0) beg = 0;
-            if (end > capacity) end = capacity;
-            if (end > beg) {
-                for (long long t = beg; t < end - 1; ++t) {
+        if (in[r]) {
+            const long long i = static_cast<long long>(y0 + ly) * W + x0 + tx;
+            if (end[r] > beg[r]) {
+                a0 = first[r].x;
+                a1 = first[r].y;
+                a2 = first[r].z;
+                for (long long t = beg[r] + 1; t < end[r] - 1; ++t) {  // slots beyond two
                     const float4 v = __ldcs(rgb + t);
                     a0 += v.x;
                     a1 += v.y;
                     a2 += v.z;
                 }
-                const float wl = hw[i];
-                const float4 v = __ldcs(rgb + end - 1);
-                a0 = __fmaf_rn(wl, v.x, a0);
-                a1 = __fmaf_rn(wl, v.y, a1);
-                a2 = __fmaf_rn(wl, v.z, a2);
-                const float si = s[i];
-                a0 = __fdiv_rn(a0, si);
-                a1 = __fdiv_rn(a1, si);
-                a2 = __fdiv_rn(a2, si);
+                a0 = __fmaf_rn(wl[r], last[r].x, a0);
+                a1 = __fmaf_rn(wl[r], last[r].y, a1);
+                a2 = __fmaf_rn(wl[r], last[r].z, a2);
+                a0 = __fdiv_rn(a0, si[r]);
+                a1 = __fdiv_rn(a1, si[r]);
+                a2 = __fdiv_rn(a2, si[r]);
             }
             float *L0 = layers.p[0];
-            L0[i] = a0;
-            L0[N + i] = a1;
-            L0[2 * N + i] = a2;
+            __stcs(L0 + i, a0);
+            __stcs(L0 + N + i, a1);
+            __stcs(L0 + 2 * N + i, a2);
         }
         buf[0][0][ly][tx] = a0;
         buf[0][1][ly][tx] = a1;
@@ -103,7 +130,9 @@ splat_kernel(const int32_t *__restrict__ offsets, const float4 *__restrict__ rgb
     }
     __syncthreads();
     const int tid = ty * kSplatTX + tx;
-    for (int l = 1; l < L; ++l) {
+#pragma unroll
+    for (int l = 1; l < kMaxLevels; ++l) {
+        if (l >= L) break;
         const int src = (l - 1) & 1, dst = l & 1;
         const int bw = kSplatTX >> l, bh = kSplatH >> l;
         const int Wl = W >> l, Hl = H >> l;

@@ -81,7 +81,7 @@ class Frame:
         C0 = logits[0].shape[0]
         B.check(B.spp_reconstruct_frame(self.layers, logits, C0, prev, mv, mask, self.W, self.H,
                                         self.L, tm if tm is not None else B.make_tonemap(), out,
-                                        self.ldr, self.recon_ws, stream),
+                                        self.ldr, self.recon_ws, self.status, stream),
                 "spp_reconstruct_frame")
         self.parity ^= 1
         return out

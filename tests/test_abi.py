@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings_and_version():
     import paper_2602_08642_gb300 as spp
-    assert spp.spp_abi_version() == 1
+    assert spp.spp_abi_version() == 3
     for code in range(0, -9, -1):
         assert spp.spp_strerror(code) and spp.spp_strerror(code) != "unknown status code"
     assert spp.spp_strerror(-99) == "unknown status code"
@@ -50,7 +50,7 @@ def test_workspace_queries():
     assert spp.spp_alloc_workspace_bytes(1920, 1080) == 256 + 8 * ((1920 * 1080 + 2047) // 2048)
     assert spp.spp_alloc_workspace_bytes(-1, 4) == 0
     b = spp.spp_reconstruct_workspace_bytes(1920, 1080, 3)
-    assert b >= 3 * 4 * (960 * 540 + 480 * 270)
+    assert b >= 3 * 4 * (1920 * 1080 + 960 * 540 + 480 * 270)
     assert spp.spp_reconstruct_workspace_bytes(64, 64, 1) == 0
     assert spp.spp_reconstruct_workspace_bytes(64, 64, 6) == 0
 
@@ -91,18 +91,21 @@ def test_host_argument_errors(lib):
     assert g(a, a, a, a, 16, 32, 16, 6, ctypes.cast(arr, ctypes.c_void_p), n) == B.SPP_ERR_SHAPE
     # reconstruction: temporal needs 54 channels and a coarser level
     r = B.lib.spp_reconstruct_level
-    assert r(a, a, 29, a, a, a, None, 32, 32, None, a, None, n) == B.SPP_ERR_ARG
-    assert r(a, a, 54, None, a, a, None, 32, 32, None, a, None, n) == B.SPP_ERR_ARG
-    assert r(a, mis, 25, None, None, None, None, 32, 32, None, a, None, n) == B.SPP_ERR_ALIGN
+    assert r(a, a, 29, a, a, None, 32, 32, None, a, None, None, n) == B.SPP_ERR_ARG
+    assert r(a, a, 54, None, a, None, 32, 32, None, a, None, None, n) == B.SPP_ERR_ARG
+    assert r(a, mis, 25, None, None, None, 32, 32, None, a, None, None, n) == B.SPP_ERR_ALIGN
     tm = B.make_tonemap(shadow=1.5)
-    assert r(a, a, 25, None, None, None, None, 32, 32, ctypes.byref(tm), a, a, n) == B.SPP_ERR_ARG
+    assert r(a, a, 25, None, None, None, 32, 32, ctypes.byref(tm), a, a, None, n) == B.SPP_ERR_ARG
+    w = B.lib.spp_warp_previous
+    assert w(None, a, 32, 32, a, n) == B.SPP_ERR_ARG
+    assert w(a, mis, 32, 32, a, n) == B.SPP_ERR_ALIGN
     fr = B.lib.spp_reconstruct_frame
     assert fr(ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 29, a, a,
-              None, 32, 32, 3, None, a, a, a, 1 << 20, n) == B.SPP_ERR_ARG  # prev needs C0=54
+              None, 32, 32, 3, None, a, a, a, 1 << 20, None, n) == B.SPP_ERR_ARG  # C0=54 needed
     assert fr(ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 54, None,
-              None, None, 36, 32, 4, None, a, a, a, 1 << 20, n) == B.SPP_ERR_SHAPE
+              None, None, 36, 32, 4, None, a, a, a, 1 << 20, None, n) == B.SPP_ERR_SHAPE
     assert fr(ctypes.cast(arr, ctypes.c_void_p), ctypes.cast(arr, ctypes.c_void_p), 54, None,
-              None, None, 64, 64, 3, None, a, a, a, 16, n) == B.SPP_ERR_WORKSPACE
+              None, None, 64, 64, 3, None, a, a, a, 16, None, n) == B.SPP_ERR_WORKSPACE
 
 
 def test_binding_rejects_host_tensors():

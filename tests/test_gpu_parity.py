@@ -293,6 +293,21 @@ def test_reconstruct_frame_parity(spp, W, H, L, temporal):
     assert_rel(host(fr.ldr), ldr_ref, atol=LDR_ATOL, what="ldr")
 
 
+@pytest.mark.parametrize("W,H", [(1920, 1080), (37, 23)])
+def test_warp_previous_parity(spp, W, H):
+    """W_t L_{t-1}: bilinear reprojection along the motion vectors, including
+    positions clamped at every border and exactly zero motion."""
+    rng = np.random.default_rng(61)
+    prev = (rng.random((3, H, W)) * 3).astype(np.float32)
+    mv = ((rng.random((2, H, W)) - 0.5) * 24).astype(np.float32)
+    mv[:, : H // 4] = 0.0
+    out = torch.empty((3, H, W), device="cuda")
+    spp.check(spp.spp_warp_previous(dev(prev), dev(mv), W, H, out))
+    ref = oracle.warp(prev.astype(np.float64), mv)
+    assert_rel(host(out), ref, what="warp")
+    assert np.array_equal(host(out)[:, : H // 4], prev[:, : H // 4])
+
+
 def test_reconstruct_level_intermediate_parity(spp):
     W, H = 160, 90
     rng = np.random.default_rng(41)
@@ -300,8 +315,8 @@ def test_reconstruct_level_intermediate_parity(spp):
     coarse = (rng.random((3, H // 2, W // 2)) * 2).astype(np.float32)
     lg = rng.standard_normal((29, H, W)).astype(np.float32) * 3
     out = torch.empty((3, H, W), device="cuda")
-    spp.check(spp.spp_reconstruct_level(dev(noisy), dev(lg), 29, dev(coarse), None, None, None, W,
-                                        H, None, out, None))
+    spp.check(spp.spp_reconstruct_level(dev(noisy), dev(lg), 29, dev(coarse), None, None, W, H,
+                                        None, out, None))
     ref = oracle.reconstruct_level(noisy, lg, coarse=coarse)
     assert_rel(host(out), ref, what="mid level")
 
