@@ -237,6 +237,8 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
                 wmax = max(wmax, w);
             }
         }
+        // an empty accumulator re-bases for free onto this chunk's windows
+        if (A.lo == 0ull && A.hi == 0ull && wmax >= 0) A.b = wmax > 0 ? wmax - 1 : 0;
         ok &= wmin >= A.b && wmax <= A.b + 1;
         if (__all_sync(__activemask(), ok)) {
 #pragma unroll
