@@ -81,6 +81,15 @@ def _load():
             "orc_tau": (_D, [_D, _D, _D]),
             "orc_srgb_encode": (_D, [_D]),
             "orc_tonemap": (None, [_P, _I64, _D, _D, _D, _D, _D, _P]),
+            "orc_reconstruct_level_backward": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _P, _P, _P,
+                                                    _P, _P]),
+            "orc_warp_backward": (None, [_P, _I, _I, _P, _P]),
+            "orc_tonemap_backward": (None, [_P, _I64, _D, _D, _D, _D, _D, _P, _P]),
+            "orc_l1_loss": (_D, [_P, _P, _I64, _P]),
+            "orc_pyramid_backward": (None, [_P, _I, _I, _I, _P]),
+            "orc_splat_backward": (None, [_P, _P, _P, _P, _I64, _D, _I, _U64, _U32, _P, _P, _P]),
+            "orc_density_backward": (None, [_P, _I64, _D, _D, _P, _P]),
+            "orc_density_forward": (None, [_P, _I64, _D, _D, _P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -294,3 +303,92 @@ def frame(d, clean, logits, W, H, L, B, *, prev=None, mv=None, mask=None, lam=10
     hdr, hats = reconstruct(layers, logits, prev=prev, mv=mv, mask=mask)
     ldr = tonemap(hdr, *tm)
     return dict(alloc=a, rgb=rgb, layers=layers, hats=hats, hdr=hdr, ldr=ldr)
+
+
+# --------------------------------------------------------------------------
+# a11: backward (analytic gradients, each pinned by finite differences)
+# --------------------------------------------------------------------------
+def reconstruct_level_backward(noisy, logits, g, coarse=None, warped=None, mask=None):
+    """(grad_logits, grad_noisy, grad_coarse, grad_warped) of loss = sum g * out."""
+    noisy = _c(noisy, np.float64)
+    logits = _c(logits, np.float64)
+    g = _c(g, np.float64)
+    _, Hl, Wl = noisy.shape
+    C = logits.shape[0]
+    coarse = None if coarse is None else _c(coarse, np.float64)
+    warped = None if warped is None else _c(warped, np.float64)
+    mask = None if mask is None else _c(mask, np.uint8)
+    gl = np.empty_like(logits)
+    gn = np.zeros_like(noisy)
+    gc = None if coarse is None else np.zeros_like(coarse)
+    gw = None if warped is None else np.zeros_like(warped)
+    rc = _load().orc_reconstruct_level_backward(_ptr(noisy), _ptr(logits), C, _ptr(coarse),
+                                                _ptr(warped), _ptr(mask), Wl, Hl, _ptr(g),
+                                                _ptr(gl), _ptr(gn), _ptr(gc), _ptr(gw))
+    if rc != OK:
+        raise ValueError(f"orc_reconstruct_level_backward rc={rc}")
+    return gl, gn, gc, gw
+
+
+def warp_backward(mv, g) -> np.ndarray:
+    mv = _c(mv, np.float32)
+    g = _c(g, np.float64)
+    _, H, W = g.shape
+    out = np.zeros_like(g)
+    _load().orc_warp_backward(_ptr(mv), W, H, _ptr(g), _ptr(out))
+    return out
+
+
+def tonemap_backward(hdr, grad_ldr, alpha=1.0, beta=1.0, k=0.0, s=0.5, h=0.5) -> np.ndarray:
+    hdr = _c(hdr, np.float64)
+    grad_ldr = _c(grad_ldr, np.float64)
+    out = np.zeros_like(hdr)
+    _load().orc_tonemap_backward(_ptr(hdr), hdr.size // 3, alpha, beta, k, s, h, _ptr(grad_ldr),
+                                 _ptr(out))
+    return out
+
+
+def l1_loss(ldr, ref):
+    """(mean |ldr - ref|, its gradient with respect to ldr)."""
+    ldr = _c(ldr, np.float64)
+    ref = _c(ref, np.float64)
+    grad = np.empty_like(ldr)
+    v = _load().orc_l1_loss(_ptr(ldr), _ptr(ref), ldr.size, _ptr(grad))
+    return float(v), grad
+
+
+def pyramid_backward(grad_layers, W, H) -> np.ndarray:
+    L = len(grad_layers)
+    gls = [_c(a, np.float64) for a in grad_layers]
+    out = gls[0].copy()
+    ptrs = (ctypes.c_void_p * L)(*[a.ctypes.data for a in gls])
+    _load().orc_pyramid_backward(ctypes.cast(ptrs, ctypes.c_void_p), W, H, L, _ptr(out))
+    return out
+
+
+def splat_backward(a: "Alloc", rgb, L0, grad_L0, lam=10.0, hard=False, seed=0x5EED,
+                   frame=0) -> np.ndarray:
+    rgb = _c(rgb, np.float64).reshape(-1, 3)
+    L0 = _c(L0, np.float64)
+    grad_L0 = _c(grad_L0, np.float64)
+    N = a.s.size
+    out = np.empty(N, np.float64)
+    _load().orc_splat_backward(_ptr(_c(a.offsets, np.int64)), _ptr(rgb), _ptr(_c(a.s, np.float64)),
+                               _ptr(_c(a.extra, np.int32)), N, lam, int(hard),
+                               seed & 0xFFFFFFFFFFFFFFFF, frame, _ptr(L0), _ptr(grad_L0), _ptr(out))
+    return out
+
+
+def density_forward(z, B, phi=0.125) -> np.ndarray:
+    z = _c(z, np.float64).ravel()
+    out = np.empty_like(z)
+    _load().orc_density_forward(_ptr(z), z.size, B, phi, _ptr(out))
+    return out
+
+
+def density_backward(z, grad_s, B, phi=0.125) -> np.ndarray:
+    z = _c(z, np.float64).ravel()
+    grad_s = _c(grad_s, np.float64).ravel()
+    out = np.empty_like(z)
+    _load().orc_density_backward(_ptr(z), z.size, B, phi, _ptr(grad_s), _ptr(out))
+    return out

@@ -461,3 +461,246 @@ void orc_tonemap(const double *hdr, int64_t N, double alpha, double beta, double
         }
     }
 }
+
+/* ======================================================================== */
+/* Backward pass (a11).  Each function is the analytic gradient of the      */
+/* forward function above it, written out by the chain rule; the pins check */
+/* every one against central finite differences of the forward in FP64.    */
+/* ======================================================================== */
+
+/* Reconstruction level (App. A): given g = dLoss/d out ([3][Hl][Wl]),
+ *   out_c = sum_k w_k v_kc, w = softmax(z over the active kernels)
+ *   dLoss/dz_k = w_k (q_k - sum_j w_j q_j), q_k = sum_c g_c v_kc
+ *   dLoss/dv_kc = w_k g_c, scattered to the tap's source pixel.
+ * grad_logits is overwritten ([C][Hl][Wl], zero for inactive channels);
+ * grad_noisy, grad_coarse, grad_warped are accumulated (+=) and may be NULL. */
+int orc_reconstruct_level_backward(const double *noisy, const double *logits, int C,
+                                   const double *coarse, const double *warped,
+                                   const uint8_t *mask, int Wl, int Hl, const double *g,
+                                   double *grad_logits, double *grad_noisy,
+                                   double *grad_coarse, double *grad_warped) {
+    int has_up = coarse != NULL;
+    int has_t = warped != NULL;
+    int need = 25 + (has_up ? 4 : 0) + (has_t ? 25 : 0);
+    if (C < need) return ORC_ERR_ARG;
+    int64_t Nl = (int64_t)Wl * Hl;
+    int Wc = Wl / 2, Hc = Hl / 2;
+    int64_t Nc = (int64_t)Wc * Hc;
+    for (int64_t k = 0; k < (int64_t)C * Nl; ++k) grad_logits[k] = 0.0;
+    for (int y = 0; y < Hl; ++y)
+        for (int x = 0; x < Wl; ++x) {
+            int64_t idx = (int64_t)y * Wl + x;
+            int use_t = has_t && !(mask && mask[idx]);
+            int ch[54];        /* logit channel of each active kernel */
+            int64_t src[54];   /* source pixel of each tap */
+            int kind[54];      /* 0 noisy, 1 coarse, 2 warped */
+            int nk = 0;
+            for (int j = -2; j <= 2; ++j)
+                for (int i = -2; i <= 2; ++i) {
+                    int xx = orc_clampi(x + i, 0, Wl - 1), yy = orc_clampi(y + j, 0, Hl - 1);
+                    ch[nk] = (j + 2) * 5 + (i + 2);
+                    src[nk] = (int64_t)yy * Wl + xx;
+                    kind[nk++] = 0;
+                }
+            if (has_up)
+                for (int j = 0; j <= 1; ++j)
+                    for (int i = 0; i <= 1; ++i) {
+                        int xc = orc_clampi((x + i) / 2, 0, Wc - 1);
+                        int yc = orc_clampi((y + j) / 2, 0, Hc - 1);
+                        ch[nk] = 25 + 2 * j + i;
+                        src[nk] = (int64_t)yc * Wc + xc;
+                        kind[nk++] = 1;
+                    }
+            if (use_t) {
+                int base = has_up ? 29 : 25;
+                for (int j = -2; j <= 2; ++j)
+                    for (int i = -2; i <= 2; ++i) {
+                        int xx = orc_clampi(x + i, 0, Wl - 1), yy = orc_clampi(y + j, 0, Hl - 1);
+                        ch[nk] = base + (j + 2) * 5 + (i + 2);
+                        src[nk] = (int64_t)yy * Wl + xx;
+                        kind[nk++] = 2;
+                    }
+            }
+            double m = logits[(int64_t)ch[0] * Nl + idx];
+            for (int k = 1; k < nk; ++k) {
+                double v = logits[(int64_t)ch[k] * Nl + idx];
+                if (v > m) m = v;
+            }
+            double wt[54], wsum = 0.0;
+            for (int k = 0; k < nk; ++k) {
+                wt[k] = exp(logits[(int64_t)ch[k] * Nl + idx] - m);
+                wsum += wt[k];
+            }
+            for (int k = 0; k < nk; ++k) wt[k] /= wsum;
+            double q[54], qbar = 0.0;
+            for (int k = 0; k < nk; ++k) {
+                const double *img = kind[k] == 0 ? noisy : (kind[k] == 1 ? coarse : warped);
+                int64_t n = kind[k] == 1 ? Nc : Nl;
+                double acc = 0.0;
+                for (int c = 0; c < 3; ++c) acc += g[(int64_t)c * Nl + idx] * img[(int64_t)c * n + src[k]];
+                q[k] = acc;
+                qbar += wt[k] * acc;
+            }
+            for (int k = 0; k < nk; ++k) {
+                grad_logits[(int64_t)ch[k] * Nl + idx] = wt[k] * (q[k] - qbar);
+                double *dst = kind[k] == 0 ? grad_noisy : (kind[k] == 1 ? grad_coarse : grad_warped);
+                int64_t n = kind[k] == 1 ? Nc : Nl;
+                if (dst)
+                    for (int c = 0; c < 3; ++c)
+                        dst[(int64_t)c * n + src[k]] += wt[k] * g[(int64_t)c * Nl + idx];
+            }
+        }
+    return ORC_OK;
+}
+
+/* W_t backward: the bilinear weights of each pixel scatter g to the four
+ * previous-frame pixels they read; grad_prev is accumulated. */
+void orc_warp_backward(const float *mv, int W, int H, const double *g, double *grad_prev) {
+    int64_t N = (int64_t)W * H;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t idx = (int64_t)y * W + x;
+            double X = (double)x + (double)mv[idx];
+            double Y = (double)y + (double)mv[N + idx];
+            if (X < 0.0) X = 0.0;
+            if (X > (double)(W - 1)) X = (double)(W - 1);
+            if (Y < 0.0) Y = 0.0;
+            if (Y > (double)(H - 1)) Y = (double)(H - 1);
+            double x0f = floor(X), y0f = floor(Y);
+            double fx = X - x0f, fy = Y - y0f;
+            int x0 = (int)x0f, y0 = (int)y0f;
+            int x1 = x0 + 1 < W ? x0 + 1 : W - 1;
+            int y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+            for (int c = 0; c < 3; ++c) {
+                double gv = g[(int64_t)c * N + idx];
+                double *P = grad_prev + (int64_t)c * N;
+                P[(int64_t)y0 * W + x0] += (1.0 - fy) * (1.0 - fx) * gv;
+                P[(int64_t)y0 * W + x1] += (1.0 - fy) * fx * gv;
+                P[(int64_t)y1 * W + x0] += fy * (1.0 - fx) * gv;
+                P[(int64_t)y1 * W + x1] += fy * fx * gv;
+            }
+        }
+}
+
+/* Derivative of tau (Sec. 5). */
+static double orc_tau_prime(double x, double s, double h) {
+    if (x < s - 1.0) return 0.5 * exp((x + 1.0 - s) / s);
+    if (x < 1.0 - h) return 0.5;
+    return 0.5 * exp(-(x + h - 1.0) / h);
+}
+
+/* Derivative of the sRGB encoding. */
+static double orc_srgb_prime(double v) {
+    if (v <= 0.0031308) return 12.92;
+    return 1.055 / 2.4 * pow(v, 1.0 / 2.4 - 1.0);
+}
+
+/* Tone-map backward: grad_hdr += d ldr / d hdr applied to grad_ldr. */
+void orc_tonemap_backward(const double *hdr, int64_t N, double alpha, double beta, double kexp,
+                          double s, double h, const double *grad_ldr, double *grad_hdr) {
+    for (int64_t i = 0; i < N; ++i) {
+        double lg[3], v[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            v[ch] = hdr[(int64_t)ch * N + i];
+            lg[ch] = log(v[ch] < 0x1p-24 ? 0x1p-24 : v[ch]);
+        }
+        double mean = (lg[0] + lg[1] + lg[2]) / 3.0;
+        double gx[3];
+        for (int ch = 0; ch < 3; ++ch) {
+            double x = alpha * (mean + beta * (lg[ch] - mean) + kexp);
+            double t = orc_tau(x, s, h);
+            gx[ch] = grad_ldr[(int64_t)ch * N + i] * orc_srgb_prime(t) * orc_tau_prime(x, s, h);
+        }
+        double gsum = gx[0] + gx[1] + gx[2];
+        for (int j = 0; j < 3; ++j) {
+            /* dx_c/dl_j = alpha (beta [c == j] + (1 - beta)/3) */
+            double gl = alpha * (beta * gx[j] + (1.0 - beta) / 3.0 * gsum);
+            if (v[j] >= 0x1p-24) grad_hdr[(int64_t)j * N + i] += gl / v[j];
+        }
+    }
+}
+
+/* Mean absolute error of the sRGB output against a reference (the spatial
+ * loss of Eq. loss_spatial with m = 1); grad = sign(ldr - ref) / n. */
+double orc_l1_loss(const double *ldr, const double *ref, int64_t n, double *grad) {
+    double acc = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = ldr[i] - ref[i];
+        acc += fabs(d);
+        if (grad) grad[i] = (d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0)) / (double)n;
+    }
+    return acc / (double)n;
+}
+
+/* Pyramid backward (Eq. app-pyramid): grad_L0 += 4^-l grad_L^l at the
+ * coarse pixel each full-resolution pixel pools into. */
+void orc_pyramid_backward(double *const *grad_layers, int W, int H, int L, double *grad_L0) {
+    int64_t N = (int64_t)W * H;
+    for (int l = 1; l < L; ++l) {
+        int Wl = W >> l, Hl = H >> l;
+        int64_t Nl = (int64_t)Wl * Hl;
+        double sc = 1.0 / (double)((int64_t)1 << (2 * l));
+        for (int c = 0; c < 3; ++c)
+            for (int y = 0; y < H; ++y)
+                for (int x = 0; x < W; ++x)
+                    grad_L0[(int64_t)c * N + (int64_t)y * W + x] +=
+                        sc * grad_layers[l][(int64_t)c * Nl + (int64_t)(y >> l) * Wl + (x >> l)];
+    }
+}
+
+/* Splat backward (Eq. stoch_rnoisy with the ramp of Eq. relaxed_holdout):
+ *   L0_i = (sum_{k<f} S_ik + w_i S_i,f) / s_i, p_i = s_i - f_i
+ *   dL0_i/ds_i = -L0_i / s_i + [extra, linear ramp] h lam (1 - u_i) / p_i^2 S_i,f / s_i
+ * (the floor is piecewise constant, so dp/ds = 1 between integers).
+ * grad_s is overwritten. */
+void orc_splat_backward(const int64_t *offsets, const double *rgb, const double *s,
+                        const int32_t *extra, int64_t N, double lambda, int hard, uint64_t seed,
+                        uint32_t frame, const double *L0, const double *grad_L0, double *grad_s) {
+    double h = (2.0 * lambda) / (2.0 * lambda - 1.0);
+    for (int64_t i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int c = 0; c < 3; ++c) acc -= grad_L0[(int64_t)c * N + i] * L0[(int64_t)c * N + i] / s[i];
+        if (extra[i] && !hard) {
+            double f = floor(s[i]);
+            double p = s[i] - f;
+            double u = orc_pixel_uniform(seed, frame, (uint64_t)i);
+            double r = (lambda / p) * ((u + p) - 1.0);
+            if (r > 0.0 && r < 1.0) {
+                double dw = h * lambda * (1.0 - u) / (p * p);
+                int64_t last = offsets[i + 1] - 1;
+                for (int c = 0; c < 3; ++c)
+                    acc += grad_L0[(int64_t)c * N + i] * dw * rgb[last * 3 + c] / s[i];
+            }
+        }
+        grad_s[i] = acc;
+    }
+}
+
+/* Density backward (Sec. 3): s_i = phi B + (1 - phi) B N pi_i with
+ * pi = softmax(z) = d / sum d, so
+ *   dLoss/dz_j = (1 - phi) B N pi_j (g_j - sum_i pi_i g_i).
+ * grad_z is overwritten. */
+void orc_density_backward(const double *z, int64_t N, double B, double phi, const double *grad_s,
+                          double *grad_z) {
+    double m = z[0];
+    for (int64_t i = 1; i < N; ++i) if (z[i] > m) m = z[i];
+    double S = 0.0;
+    for (int64_t i = 0; i < N; ++i) S += exp(z[i] - m);
+    double dot = 0.0;
+    for (int64_t i = 0; i < N; ++i) dot += exp(z[i] - m) / S * grad_s[i];
+    double K = (1.0 - phi) * B * (double)N;
+    for (int64_t i = 0; i < N; ++i) {
+        double pi = exp(z[i] - m) / S;
+        grad_z[i] = K * pi * (grad_s[i] - dot);
+    }
+}
+
+/* Density forward in FP64 from the sampler logits z (Sec. 3): s_i =
+ * phi B + (1 - phi) B N softmax(z)_i.  Used to pin the density backward. */
+void orc_density_forward(const double *z, int64_t N, double B, double phi, double *s) {
+    double m = z[0];
+    for (int64_t i = 1; i < N; ++i) if (z[i] > m) m = z[i];
+    double S = 0.0;
+    for (int64_t i = 0; i < N; ++i) S += exp(z[i] - m);
+    for (int64_t i = 0; i < N; ++i) s[i] = phi * B + (1.0 - phi) * B * (double)N * exp(z[i] - m) / S;
+}
