@@ -259,6 +259,77 @@ int spp_reconstruct_frame(const float *const *layers, const float *const *logits
                           int H, int L, const spp_tonemap *tm, float *out_hdr, float *out_ldr,
                           void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream);
 
+/* ------------------------------------------------------ a11: backward */
+/*
+ * Gradients of the path, for training the sampler and the kernel predictor
+ * end to end (Sec. 4.3, Sec. 5, Sec. 6.3).  Each call maps the gradient of
+ * the loss with respect to a step's output to its inputs' gradients.  Unless
+ * stated otherwise a gradient output is ACCUMULATED (+=): the caller zeroes
+ * it, and several calls may add into one buffer.  Gradients scattered to
+ * neighbouring pixels are summed with floating-point atomics, so their last
+ * bits may differ from run to run.
+ */
+
+/* Reconstruction level (Appendix A) given dLoss/d out (grad_out, [3][Hl][Wl]).
+ * Recomputes each pixel's joint softmax from its logits.
+ *   grad_logits [C][Hl][Wl], OVERWRITTEN: w_k (q_k - sum_j w_j q_j) with
+ *               q_k = sum_c grad_out_c v_kc; 0 for channels without a kernel
+ *               (and for the temporal channels of disoccluded pixels).
+ *   grad_noisy  [3][Hl][Wl], grad_coarse [3][Hl/2][Wl/2], grad_warped
+ *               [3][Hl][Wl]: += w_k grad_out at each tap's source pixel
+ *               (clamp-to-edge transposed); each may be NULL.
+ * Other arguments as in spp_reconstruct_level. */
+int spp_reconstruct_level_backward(const float *noisy, const float *logits, int C,
+                                   const float *coarse, const float *warped_prev,
+                                   const uint8_t *mask, int Wl, int Hl, const float *grad_out,
+                                   float *grad_logits, float *grad_noisy, float *grad_coarse,
+                                   float *grad_warped, cudaStream_t stream);
+
+/* W_t backward: grad_prev [3][H][W] += the bilinear weights of every pixel
+ * applied to grad_warped (the transpose of spp_warp_previous). */
+int spp_warp_previous_backward(const float *mv, int W, int H, const float *grad_warped,
+                               float *grad_prev, cudaStream_t stream);
+
+/* Tone-map backward (Sec. 5): grad_hdr [3][H][W] += d sRGB(tau(x)) / d hdr
+ * applied to grad_ldr; pixels at the 2^-24 floor get no gradient. */
+int spp_tonemap_backward(const float *hdr, int W, int H, const spp_tonemap *tm,
+                         const float *grad_ldr, float *grad_hdr, cudaStream_t stream);
+
+/* Spatial loss of Eq. loss_spatial with m = 1: *loss (device float) =
+ * mean |ldr - ref| over n values; grad_ldr (OVERWRITTEN, or NULL) =
+ * sign(ldr - ref) / n. */
+int spp_l1_loss(const float *ldr, const float *ref, int64_t n, float *loss, float *grad_ldr,
+                cudaStream_t stream);
+
+/* Pyramid backward (Eq. app-pyramid): grad_L0 [3][H][W] += sum over levels
+ * l >= 1 of 4^-l grad_layers[l] at the pixel's coarse cell (grad_layers[0]
+ * is not read). */
+int spp_pyramid_backward(const float *const *grad_layers, int W, int H, int L, float *grad_L0,
+                         cudaStream_t stream);
+
+/* Splat backward (Eq. stoch_rnoisy, Eq. relaxed_holdout) with respect to the
+ * density s, the discrete choices held fixed:
+ *   grad_s_i = sum_c g_ic (-L0_ic / s_i)
+ *            + [extra, ramp in its linear part] sum_c g_ic S_i,last,c / s_i
+ *              * h lambda (1 - u_i) / p_i^2
+ * grad_s [H][W] is OVERWRITTEN.  offsets, counts, rgb, s come from the
+ * forward calls; layer0 is L0 and grad_layer0 dLoss/dL0; p the sampling
+ * parameters of the forward call (u_i is recomputed from seed and frame). */
+int spp_splat_backward(const int32_t *offsets, const int32_t *counts, const float *rgb,
+                       const float *s, const float *layer0, const float *grad_layer0,
+                       int64_t capacity, int W, int H, const spp_params *p, float *grad_s,
+                       cudaStream_t stream);
+
+/* Workspace bytes of spp_density_backward. */
+size_t spp_density_backward_workspace_bytes(void);
+
+/* Density backward (Sec. 3): with s = phi B + (1-phi) B N d / sum d and
+ * d = exp(z - max z) the sampler's softmax, grad_z (OVERWRITTEN) =
+ * (1-phi) B N pi (grad_s - sum_i pi_i grad_s_i), pi = d / sum d. */
+int spp_density_backward(const float *d, int64_t N, double budget, double uniform_fraction,
+                         const float *grad_s, float *grad_z, void *ws, size_t ws_bytes,
+                         cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

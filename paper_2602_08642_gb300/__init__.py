@@ -16,3 +16,4 @@ from ._binding import (  # noqa: F401
     spp_warp_previous,
     spp_render_synthetic, spp_splat_samples, spp_strerror)
 from .pipeline import Frame, default_capacity, logit_channels  # noqa: F401
+from . import autograd  # noqa: F401,E402

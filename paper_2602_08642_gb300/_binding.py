@@ -78,6 +78,17 @@ _SIGS = {
                                    ctypes.POINTER(spp_tonemap), _P, _P, _P, _P]),
     "spp_reconstruct_frame": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _I,
                                    ctypes.POINTER(spp_tonemap), _P, _P, _P, _SZ, _P, _P]),
+    "spp_reconstruct_level_backward": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _P, _P, _P, _P, _P,
+                                            _P]),
+    "spp_warp_previous_backward": (_I, [_P, _I, _I, _P, _P, _P]),
+    "spp_tonemap_backward": (_I, [_P, _I, _I, ctypes.POINTER(spp_tonemap), _P, _P, _P]),
+    "spp_l1_loss": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "spp_pyramid_backward": (_I, [_P, _I, _I, _I, _P, _P]),
+    "spp_splat_backward": (_I, [_P, _P, _P, _P, _P, _P, _I64, _I, _I, ctypes.POINTER(spp_params),
+                                _P, _P]),
+    "spp_density_backward_workspace_bytes": (_SZ, []),
+    "spp_density_backward": (_I, [_P, _I64, ctypes.c_double, ctypes.c_double, _P, _P, _P, _SZ,
+                                  _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -220,3 +231,62 @@ def spp_reconstruct_frame(layers, logits, C0, prev_hdr, mv, mask, W, H, L, tm, o
         _dev(out_ldr, torch.float32), _dev(ws) if ws is not None else None,
         (ws.numel() * ws.element_size()) if ws is not None else 0, _dev(status, torch.int32),
         _stream(stream))
+
+
+# --------------------------------------------------------------------------
+# backward entry points
+# --------------------------------------------------------------------------
+def spp_reconstruct_level_backward(noisy, logits, C, coarse, warped_prev, mask, Wl, Hl, grad_out,
+                                   grad_logits, grad_noisy, grad_coarse, grad_warped,
+                                   stream=None) -> int:
+    f = torch.float32
+    return lib.spp_reconstruct_level_backward(
+        _dev(noisy, f), _dev(logits, f), C, _dev(coarse, f), _dev(warped_prev, f),
+        _dev(mask, torch.uint8), Wl, Hl, _dev(grad_out, f), _dev(grad_logits, f),
+        _dev(grad_noisy, f), _dev(grad_coarse, f), _dev(grad_warped, f), _stream(stream))
+
+
+def spp_warp_previous_backward(mv, W, H, grad_warped, grad_prev, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_warp_previous_backward(_dev(mv, f), W, H, _dev(grad_warped, f),
+                                          _dev(grad_prev, f), _stream(stream))
+
+
+def spp_tonemap_backward(hdr, W, H, tm, grad_ldr, grad_hdr, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_tonemap_backward(_dev(hdr, f), W, H,
+                                    ctypes.byref(tm) if tm is not None else None,
+                                    _dev(grad_ldr, f), _dev(grad_hdr, f), _stream(stream))
+
+
+def spp_l1_loss(ldr, ref, n, loss, grad_ldr, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_l1_loss(_dev(ldr, f), _dev(ref, f), int(n), _dev(loss, f), _dev(grad_ldr, f),
+                           _stream(stream))
+
+
+def spp_pyramid_backward(grad_layers, W, H, L, grad_L0, stream=None) -> int:
+    arr = (ctypes.c_void_p * L)(*[0 if l == 0 else _dev(grad_layers[l], torch.float32).value
+                                   for l in range(L)])
+    return lib.spp_pyramid_backward(ctypes.cast(arr, _P), W, H, L, _dev(grad_L0, torch.float32),
+                                    _stream(stream))
+
+
+def spp_splat_backward(offsets, counts, rgb, s, layer0, grad_layer0, capacity, W, H,
+                       params: spp_params, grad_s, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_splat_backward(
+        _dev(offsets, torch.int32), _dev(counts, torch.int32), _dev(rgb, f), _dev(s, f),
+        _dev(layer0, f), _dev(grad_layer0, f), int(capacity), W, H, ctypes.byref(params),
+        _dev(grad_s, f), _stream(stream))
+
+
+def spp_density_backward_workspace_bytes() -> int:
+    return int(lib.spp_density_backward_workspace_bytes())
+
+
+def spp_density_backward(d, N, budget, uniform_fraction, grad_s, grad_z, ws, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_density_backward(_dev(d, f), int(N), float(budget), float(uniform_fraction),
+                                    _dev(grad_s, f), _dev(grad_z, f), _dev(ws),
+                                    ws.numel() * ws.element_size(), _stream(stream))
