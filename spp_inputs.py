@@ -185,3 +185,57 @@ def frame_inputs(W: int, H: int, L: int, frame: int, *, temporal: bool = True,
     mv = motion_affine(W, H, seed=base_seed * 1000 + 400, frame=frame)
     mask = disocclusion_mask(W, H, seed=base_seed * 1000 + 500, frame=frame)
     return dict(d=d, clean=clean, gbuf=gbuf, logits=lg, mv=mv, mask=mask)
+
+
+def unet_params(layers, seed: int = 7, head_bias: dict | None = None,
+                head_scale: float = 0.01) -> np.ndarray:
+    """Flat FP32 parameter vector for a stack of 3x3 convolutions.
+
+    ``layers`` is a list of (name, cin, cout, relu); for each layer the
+    weights [cout][cin][3][3] (He-normal, std sqrt(2 / (9 cin)); heads, the
+    layers without ReLU, scaled by ``head_scale``) are followed by the bias
+    [cout] (zero, or ``head_bias[name]`` for a head)."""
+    r = _rng(seed, 71)
+    parts = []
+    for name, cin, cout, relu in layers:
+        w = r.standard_normal((cout, cin, 3, 3)) * np.sqrt(2.0 / (9 * cin))
+        if not relu:
+            w *= head_scale
+        b = np.zeros(cout)
+        if head_bias is not None and name in head_bias:
+            b[:] = head_bias[name]
+        parts += [w.ravel(), b]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def fixed_head_bias() -> dict:
+    """Head biases that make a network with near-zero head weights start as
+    the plain fixed-kernel method (the values of :func:`fixed_logits`, zero
+    density logit)."""
+    g = np.zeros(25, np.float32)
+    for j in range(-2, 3):
+        for i in range(-2, 3):
+            g[(j + 2) * 5 + (i + 2)] = -(i * i + j * j) / 2.0
+    h0 = np.zeros(55, np.float32)
+    h0[:25] = g
+    h1 = np.zeros(29, np.float32)
+    h1[:25] = g
+    return {"h0": h0, "h1": h1, "h2": g.copy()}
+
+
+def scene_motion(W: int, H: int, frame: int = 1) -> np.ndarray:
+    """Motion vectors (current -> previous frame, pixels) of :func:`scene`,
+    whose content drifts by (+1.5, -0.75) px per frame: the constant field
+    (-1.5, +0.75)."""
+    mv = np.empty((2, H, W), np.float32)
+    mv[0] = -1.5
+    mv[1] = 0.75
+    return mv
+
+
+def training_pair(size: int, seed: int, frame: int = 1):
+    """Two consecutive frames of one procedural scene at size x size: dict
+    with clean / gbuf of frames t-1 and t and the true motion of frame t."""
+    c0, g0 = scene(size, size, seed=seed, frame=frame - 1)
+    c1, g1 = scene(size, size, seed=seed, frame=frame)
+    return dict(clean_prev=c0, gbuf_prev=g0, clean=c1, gbuf=g1, mv=scene_motion(size, size, frame))
