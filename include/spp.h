@@ -330,6 +330,105 @@ int spp_density_backward(const float *d, int64_t N, double budget, double unifor
                          const float *grad_s, float *grad_z, void *ws, size_t ws_bytes,
                          cudaStream_t stream);
 
+
+/* --------------------------------------------- a10: learned predictor */
+/*
+ * The network that predicts the sampling density and the per-level kernel
+ * logits from G-buffers and the previous output (Sec. 3, Sec. 6.3,
+ * Appendix A): a U-Net of 3x3 convolutions (zero padding, bias), ReLU after
+ * the hidden layers, 2x2 average pooling on the way down, nearest
+ * upsampling and channel concatenation on the way up.  The paper prints no
+ * layer table; this library's reading, in parameter order
+ * (spp_unet_layer):
+ *    0 e0a  12->32            1 e0b 32->32       level 0 (full resolution)
+ *    2 e1a  32->64  (input: 2x2 pool of e0b)      3 e1b 64->64    level 1
+ *    4 e2a  64->128 (input: 2x2 pool of e1b)      5 e2b 128->128  level 2
+ *    6 h2  128->25  level-2 kernel logits (linear)
+ *    7 d1a 192->64  (input: concat [e1b, upsampled e2b])  8 d1b 64->64
+ *    9 h1   64->29  level-1 kernel logits (linear)
+ *   10 d0a  96->32  (input: concat [e0b, upsampled d1b]) 11 d0b 32->32
+ *   12 h0   32->55  level-0 kernel logits (channels 0..53: kd 25, ku 4,
+ *                   kt 25) and the density logit z (channel 54)
+ * Parameters theta: FP32, for each layer in order the weights
+ * [cout][cin][3][3] followed by the bias [cout].
+ *
+ * Precision: BF16 weights and activations (round to nearest even), FP32
+ * accumulation on the tcgen05 tensor cores, FP32 biases and logits.
+ * Activations are stored NHWC (channels innermost) in BF16; the images the
+ * reconstruction reads (logits, density) are planar FP32.
+ */
+#define SPP_UNET_LAYERS 13
+#define SPP_UNET_FEATURES 12
+#define SPP_UNET_DENSITY_CHANNEL 54
+
+/* Shape of layer i (0..12): input and output channels, 1 if ReLU follows.
+ * SPP_ERR_ARG for i out of range or a null pointer. */
+int spp_unet_layer(int i, int *cin, int *cout, int *relu);
+
+/* Number of FP32 parameters in theta (535565). */
+int64_t spp_unet_param_count(void);
+
+/* Bytes of the packed parameter blob: BF16 weights in the tensor-core
+ * operand layout and FP32 biases of every layer, plus, when with_backward
+ * is non-zero, the flipped and transposed weights the data gradient uses. */
+size_t spp_unet_packed_bytes(int with_backward);
+
+/* Packs theta (device FP32, spp_unet_param_count values) into `packed`
+ * (device, spp_unet_packed_bytes(with_backward) bytes, 256-byte aligned).
+ * Re-run after every change of theta. */
+int spp_unet_pack(const float *theta, int with_backward, void *packed, size_t packed_bytes,
+                  cudaStream_t stream);
+
+/* Network input of one W x H frame (Sec. 6.3 G-buffer inputs plus the
+ * previous output of Sec. 3): in12 [12][H][W] = albedo [3], normal [3],
+ * ln(depth)/ln(100) [1] (depth [H][W] > 0), motion / 8 px [2] (mv
+ * [2][H][W]), previous LDR output warped to this frame [3] (prev_ldr; NULL
+ * gives zeros, the first frame). */
+int spp_assemble_features(const float *albedo, const float *normal, const float *depth,
+                          const float *mv, const float *prev_ldr, int W, int H, float *in12,
+                          cudaStream_t stream);
+
+/* Workspace bytes of spp_predict_density_and_kernels for B frames of
+ * W x H (the activations of every layer; the backward reads them). */
+size_t spp_predict_workspace_bytes(int B, int W, int H);
+
+/* Forward pass of the predictor on B frames (W, H divisible by 4):
+ *   in12     [B][12][H][W] FP32 input features
+ *   density  [B][H][W] FP32: d = exp(z - max z) per frame, the unnormalised
+ *            spatial softmax (Sec. 3) that spp_alloc_sample_map normalises
+ *   logits0  [B][55][H][W] FP32: planes 0..53 are the level-0 kernel logits
+ *            (the first 29 planes are the logits without the temporal
+ *            term), plane 54 the density logit z
+ *   logits1  [B][29][H/2][W/2], logits2 [B][25][H/4][W/4] FP32
+ * packed comes from spp_unet_pack; ws keeps the activations for the
+ * backward.  Device-side errors (a tensor-core pipeline wait that gave up)
+ * land in *status. */
+int spp_predict_density_and_kernels(const void *packed, const float *in12, int B, int W, int H,
+                                    float *density, float *logits0, float *logits1,
+                                    float *logits2, void *ws, size_t ws_bytes, int32_t *status,
+                                    cudaStream_t stream);
+
+/* Single 3x3 convolution layers on the tensor cores (the building block of
+ * the predictor, exposed for testing and reuse).  Tensors are BF16 (as
+ * uint16_t bit patterns) in NHWC layout [B][H][W][C]; weights w
+ * [cout][cin][3][3] and bias [cout] are FP32 and are packed into ws.
+ * Channel counts of BF16 tensors must be multiples of 8; the output channel
+ * count of a call (cout for the forward, cin for the data gradient) must be
+ * one of 16, 32, 64, 96, 128, 192. */
+size_t spp_conv3x3_workspace_bytes(int cin, int cout);
+
+/* y = conv3x3(x, w) + bias, then max(., 0) if relu. */
+int spp_conv3x3_forward(const uint16_t *x, int B, int W, int H, int cin, int cout, const float *w,
+                        const float *bias, int relu, uint16_t *y, void *ws, size_t ws_bytes,
+                        int32_t *status, cudaStream_t stream);
+
+/* Data gradient: gx = conv3x3^T(g) (g [B][H][W][cout], gx [B][H][W][cin]),
+ * multiplied by (act > 0) elementwise when act ([B][H][W][cin]) is given
+ * (the ReLU of the layer that produced the input). */
+int spp_conv3x3_backward_data(const uint16_t *g, int B, int W, int H, int cin, int cout,
+                              const float *w, const uint16_t *act, uint16_t *gx, void *ws,
+                              size_t ws_bytes, int32_t *status, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

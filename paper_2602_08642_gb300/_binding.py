@@ -89,6 +89,17 @@ _SIGS = {
     "spp_density_backward_workspace_bytes": (_SZ, []),
     "spp_density_backward": (_I, [_P, _I64, ctypes.c_double, ctypes.c_double, _P, _P, _P, _SZ,
                                   _P]),
+    "spp_unet_layer": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "spp_unet_param_count": (_I64, []),
+    "spp_unet_packed_bytes": (_SZ, [_I]),
+    "spp_unet_pack": (_I, [_P, _I, _P, _SZ, _P]),
+    "spp_assemble_features": (_I, [_P, _P, _P, _P, _P, _I, _I, _P, _P]),
+    "spp_predict_workspace_bytes": (_SZ, [_I, _I, _I]),
+    "spp_predict_density_and_kernels": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P, _P, _SZ, _P,
+                                             _P]),
+    "spp_conv3x3_workspace_bytes": (_SZ, [_I, _I]),
+    "spp_conv3x3_forward": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _I, _P, _P, _SZ, _P, _P]),
+    "spp_conv3x3_backward_data": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -290,3 +301,65 @@ def spp_density_backward(d, N, budget, uniform_fraction, grad_s, grad_z, ws, str
     return lib.spp_density_backward(_dev(d, f), int(N), float(budget), float(uniform_fraction),
                                     _dev(grad_s, f), _dev(grad_z, f), _dev(ws),
                                     ws.numel() * ws.element_size(), _stream(stream))
+
+
+# ------------------------------------------------------------ a10: predictor
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def spp_unet_layer(i: int):
+    """(cin, cout, relu) of layer i."""
+    a, b, c = _I(), _I(), _I()
+    check(lib.spp_unet_layer(i, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "layer")
+    return a.value, b.value, c.value
+
+
+def spp_unet_param_count() -> int:
+    return int(lib.spp_unet_param_count())
+
+
+def spp_unet_packed_bytes(with_backward: bool) -> int:
+    return int(lib.spp_unet_packed_bytes(int(with_backward)))
+
+
+def spp_unet_pack(theta, with_backward, packed, stream=None) -> int:
+    return lib.spp_unet_pack(_dev(theta, torch.float32), int(with_backward), _dev(packed),
+                             _nbytes(packed), _stream(stream))
+
+
+def spp_assemble_features(albedo, normal, depth, mv, prev_ldr, W, H, in12, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_assemble_features(_dev(albedo, f), _dev(normal, f), _dev(depth, f), _dev(mv, f),
+                                     _dev(prev_ldr, f), W, H, _dev(in12, f), _stream(stream))
+
+
+def spp_predict_workspace_bytes(B: int, W: int, H: int) -> int:
+    return int(lib.spp_predict_workspace_bytes(B, W, H))
+
+
+def spp_predict_density_and_kernels(packed, in12, B, W, H, density, logits0, logits1, logits2,
+                                    ws, status, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_predict_density_and_kernels(
+        _dev(packed), _dev(in12, f), B, W, H, _dev(density, f), _dev(logits0, f),
+        _dev(logits1, f), _dev(logits2, f), _dev(ws), _nbytes(ws), _dev(status, torch.int32),
+        _stream(stream))
+
+
+def spp_conv3x3_workspace_bytes(cin: int, cout: int) -> int:
+    return int(lib.spp_conv3x3_workspace_bytes(cin, cout))
+
+
+def spp_conv3x3_forward(x, B, W, H, cin, cout, w, bias, relu, y, ws, status, stream=None) -> int:
+    bf = torch.bfloat16
+    return lib.spp_conv3x3_forward(_dev(x, bf), B, W, H, cin, cout, _dev(w, torch.float32),
+                                   _dev(bias, torch.float32), int(relu), _dev(y, bf), _dev(ws),
+                                   _nbytes(ws), _dev(status, torch.int32), _stream(stream))
+
+
+def spp_conv3x3_backward_data(g, B, W, H, cin, cout, w, act, gx, ws, status, stream=None) -> int:
+    bf = torch.bfloat16
+    return lib.spp_conv3x3_backward_data(_dev(g, bf), B, W, H, cin, cout, _dev(w, torch.float32),
+                                         _dev(act, bf), _dev(gx, bf), _dev(ws), _nbytes(ws),
+                                         _dev(status, torch.int32), _stream(stream))

@@ -1,0 +1,441 @@
+// 3x3 convolution (zero padding, stride 1) as an implicit GEMM on the
+// tcgen05 tensor cores: BF16 operands, FP32 accumulation in TMEM.
+//
+// GEMM view: M = 128 output pixels of one image row, N = output channels,
+// K = 9 taps x input channels.  One CTA per SM runs persistently over
+// tiles of TR rows x 128 pixels; the accumulator of each row is an
+// M=128 x N block of TMEM columns, double-buffered across tiles so the
+// epilogue of one tile overlaps the main loop of the next.
+//
+// Warp roles (288 threads):
+//   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
+//              lanes 32w..32w+31 = pixels), bias / ReLU / mask, stores;
+//   warps 4-7  producers: per K chunk of 16 input channels they stage the
+//              (TR+2) x 130 pixel halo of the tile in shared memory in the
+//              K-major core-matrix layout [kgroup 2][row][pixel][8 ch], with
+//              zero padding, fused 2x2 pooling, fused upsample + concat or
+//              FP32 -> BF16 conversion on the way; one elected thread
+//              bulk-copies the pre-packed weights of the chunk;
+//   warp 8     lane 0 issues the MMAs: for each row r and tap (dy, dx) the A
+//              operand is the halo window starting at row r+dy, pixel dx
+//              (a 16-byte-aligned start address; SBO = 128 B because the
+//              pixels of a row are consecutive 16-byte rows), the B operand
+//              the tap's weight block.  No im2col copy is made.
+//
+// Stages are recycled through full/empty mbarriers (producers -> MMA via
+// arrival counts and transaction bytes, MMA -> producers via
+// tcgen05.commit).  Every wait is bounded: on expiry the CTA records
+// SPP_ERR_TIMEOUT in the status word, the other roles leave at their next
+// wait, the MMA thread waits for its issued MMAs, the copy thread for its
+// copies in flight, and TMEM is freed before the kernel returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "conv_tc.cuh"
+#include "spp_internal.cuh"
+#include "tc_common.cuh"
+
+namespace spp {
+namespace conv {
+namespace {
+
+constexpr int kTileX = 128;  // output pixels per row tile (MMA M)
+constexpr int kPitch = 130;  // staged halo pixels per row
+constexpr int kThreads = 288;
+constexpr int kHeader = 256;  // barriers, TMEM slot, abort flag
+constexpr int kSmemBudget = 220 * 1024;
+
+template <int N>
+struct Cfg {
+    static constexpr int TR = N <= 64 ? 4 : N <= 128 ? 2 : 1;  // rows per tile
+    static constexpr int kA = 2 * (TR + 2) * kPitch * 16;       // halo bytes per stage
+    static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per stage
+    static constexpr int kStage = kA + kB;
+    static constexpr int kNS0 = (kSmemBudget - kHeader) / kStage;
+    static constexpr int kNS = kNS0 > 4 ? 4 : kNS0;
+    static constexpr int kCols = tc::pow2_cols(2 * TR * N);
+    static constexpr int kSmem = kHeader + kNS * kStage + 128;  // + alignment slack
+    static_assert(kNS >= 2, "stage does not fit twice");
+    static_assert(2 * TR * N <= 512, "accumulators exceed TMEM");
+};
+
+struct Bars {
+    uint64_t full[4];   // producers' halo stores (128 arrivals)
+    uint64_t wfull[4];  // weight bulk copy (1 arrival + bytes)
+    uint64_t empty[4];  // MMA done with the stage (tcgen05.commit)
+    uint64_t accf[2];   // accumulator ready (tcgen05.commit)
+    uint64_t acce[2];   // accumulator drained by the epilogue (128 arrivals)
+    uint64_t drain;     // abort path: all issued MMAs complete
+    uint32_t tmem_base;
+    int abort;
+};
+static_assert(sizeof(Bars) <= kHeader, "header");
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ float2 unpack_bf16x2(uint32_t u) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&u);
+    return __bfloat1622float2(h);
+}
+
+__device__ __forceinline__ uint4 ldg16(const __nv_bfloat16 *p) {
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// 8 input channels [ch, ch+8) of pixel (b, y, x) of the conceptual input.
+__device__ __forceinline__ uint4 load_chunk(const ConvArgs &a, int b, int y, int x, int ch) {
+    const uint4 zero = make_uint4(0, 0, 0, 0);
+    if (y < 0 || y >= a.H || x < 0 || x >= a.W) return zero;
+    switch (a.src_mode) {
+        case kSrcNHWC:
+            if (ch >= a.c0) return zero;
+            return ldg16(a.src0 + ((static_cast<size_t>(b) * a.H + y) * a.W + x) * a.c0 + ch);
+        case kSrcPool: {
+            if (ch >= a.c0) return zero;
+            const int Wf = 2 * a.W;
+            const __nv_bfloat16 *p =
+                a.src0 + ((static_cast<size_t>(b) * 2 * a.H + 2 * y) * Wf + 2 * x) * a.c0 + ch;
+            const uint4 q0 = ldg16(p), q1 = ldg16(p + a.c0);
+            const uint4 q2 = ldg16(p + static_cast<size_t>(Wf) * a.c0);
+            const uint4 q3 = ldg16(p + static_cast<size_t>(Wf) * a.c0 + a.c0);
+            const uint32_t *u0 = &q0.x, *u1 = &q1.x, *u2 = &q2.x, *u3 = &q3.x;
+            uint4 r;
+            uint32_t *ro = &r.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 f0 = unpack_bf16x2(u0[k]), f1 = unpack_bf16x2(u1[k]);
+                const float2 f2 = unpack_bf16x2(u2[k]), f3 = unpack_bf16x2(u3[k]);
+                ro[k] = pack_bf16x2(((f0.x + f1.x) + (f2.x + f3.x)) * 0.25f,
+                                    ((f0.y + f1.y) + (f2.y + f3.y)) * 0.25f);
+            }
+            return r;
+        }
+        case kSrcConcatUp:
+            if (ch < a.c0)
+                return ldg16(a.src0 + ((static_cast<size_t>(b) * a.H + y) * a.W + x) * a.c0 + ch);
+            if (ch - a.c0 >= a.c1) return zero;
+            return ldg16(a.src1 +
+                         ((static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) * (a.W >> 1) + (x >> 1)) *
+                             a.c1 +
+                         (ch - a.c0));
+        default: {  // kSrcPlanarF32
+            const size_t plane = static_cast<size_t>(a.H) * a.W;
+            const float *p = a.srcf + (static_cast<size_t>(b) * a.cf + ch) * plane +
+                             static_cast<size_t>(y) * a.W + x;
+            float v[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = (ch + e < a.cf) ? __ldg(p + e * plane) : 0.f;
+            return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+        }
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) {
+    using C = Cfg<N>;
+    constexpr int TR = C::TR, NS = C::kNS;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+    Bars &bars = *reinterpret_cast<Bars *>(base);
+    unsigned char *stages = base + kHeader;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    const int tiles_x = (a.W + kTileX - 1) / kTileX;
+    const int tiles_y = (a.H + TR - 1) / TR;
+    const int per_img = tiles_x * tiles_y;
+    const int ntiles = a.B * per_img;
+    const int kchunks = a.cin_pad / 16;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            tc::mbar_init(&bars.full[s], 128);
+            tc::mbar_init(&bars.wfull[s], 1);
+            tc::mbar_init(&bars.empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&bars.accf[i], 1);
+            tc::mbar_init(&bars.acce[i], 128);
+        }
+        tc::mbar_init(&bars.drain, 1);
+        bars.abort = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 8) tc::tmem_alloc(&bars.tmem_base, C::kCols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = bars.tmem_base;
+    volatile int *abort_flag = &bars.abort;
+    auto fail = [&]() {
+        *abort_flag = 1;
+        set_status(a.status, SPP_ERR_TIMEOUT);
+    };
+
+    if (warp >= 4 && warp < 8) {
+        // ---------------------------------------------------------- producers
+        const int ptid = tid - 128;
+        constexpr int kTasks = 2 * (TR + 2) * kPitch;  // 16-byte chunks per stage
+        constexpr int kUnroll = 4;
+        uint32_t it = 0;
+        uint32_t issued = 0;  // weight copies issued (by ptid 0)
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int b = t / per_img, r = t - b * per_img;
+            const int y0 = (r / tiles_x) * TR, x0 = (r % tiles_x) * kTileX;
+            for (int c = 0; c < kchunks; ++c, ++it) {
+                const int s = static_cast<int>(it % NS);
+                const uint32_t ph = (it / NS) & 1u;
+                if (!tc::mbar_wait(&bars.empty[s], ph ^ 1u, abort_flag)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                unsigned char *As = stages + s * C::kStage;
+                if (ptid == 0) {
+                    tc::mbar_arrive_expect_tx(&bars.wfull[s], C::kB);
+                    tc::bulk_g2s(As + C::kA,
+                                 reinterpret_cast<const unsigned char *>(a.wpack) +
+                                     static_cast<size_t>(c) * C::kB,
+                                 C::kB, &bars.wfull[s]);
+                    ++issued;
+                }
+                // task j -> kgroup j / ((TR+2) * kPitch), row, pixel; the
+                // shared-memory offset of task j is 16 j
+#pragma unroll 1
+                for (int j0 = 0; j0 < kTasks; j0 += 128 * kUnroll) {
+                    uint4 v[kUnroll];
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int j = j0 + u * 128 + ptid;
+                        v[u] = make_uint4(0, 0, 0, 0);
+                        if (j < kTasks) {
+                            const int px = j % kPitch, q = j / kPitch;
+                            const int row = q % (TR + 2), kg = q / (TR + 2);
+                            v[u] = load_chunk(a, b, y0 - 1 + row, x0 - 1 + px, c * 16 + kg * 8);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kUnroll; ++u) {
+                        const int j = j0 + u * 128 + ptid;
+                        if (j < kTasks) *reinterpret_cast<uint4 *>(As + 16 * j) = v[u];
+                    }
+                }
+                tc::fence_proxy_async();
+                tc::mbar_arrive(&bars.full[s]);
+            }
+        }
+        if (!ok && ptid == 0) {
+            // wait (bounded, ignoring the abort flag) for the copies still in flight
+            const uint32_t first = issued > NS ? issued - NS : 0;
+            for (uint32_t k = first; k < issued; ++k)
+                (void)tc::mbar_wait(&bars.wfull[k % NS], (k / NS) & 1u, nullptr);
+        }
+    } else if (warp == 8) {
+        // -------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, N);
+            constexpr uint32_t kLboA = (TR + 2) * kPitch * 16, kLboB = N * 16;
+            uint32_t it = 0, tl = 0;
+            bool ok = true, pending = false;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+                const int acc = tl & 1;
+                if (!tc::mbar_wait(&bars.acce[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) {
+                    fail();
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                const uint32_t d0 = tmem + acc * TR * N;
+                for (int c = 0; c < kchunks; ++c, ++it) {
+                    const int s = static_cast<int>(it % NS);
+                    const uint32_t ph = (it / NS) & 1u;
+                    if (!tc::mbar_wait(&bars.full[s], ph, abort_flag) ||
+                        !tc::mbar_wait(&bars.wfull[s], ph, abort_flag)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a_base = tc::smem_u32(stages + s * C::kStage);
+                    const uint32_t b_base = a_base + C::kA;
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap % 3;
+                        const uint64_t bd = tc::smem_desc(b_base + tap * 2 * N * 16, kLboB, 128);
+#pragma unroll
+                        for (int r = 0; r < TR; ++r) {
+                            const uint64_t ad = tc::smem_desc(
+                                a_base + ((r + dy) * kPitch + dx) * 16, kLboA, 128);
+                            tc::mma_bf16(d0 + r * N, ad, bd, idesc, (c | tap) != 0);
+                        }
+                    }
+                    pending = true;
+                    tc::mma_commit(&bars.empty[s]);
+                }
+                if (!ok) break;
+                tc::mma_commit(&bars.accf[acc]);
+            }
+            if (!ok && pending) {
+                tc::mma_commit(&bars.drain);
+                (void)tc::mbar_wait(&bars.drain, 0, nullptr);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ----------------------------------------------------------- epilogue
+        uint32_t tl = 0;
+        const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const int acc = tl & 1;
+            if (!tc::mbar_wait(&bars.accf[acc], (tl >> 1) & 1u, abort_flag)) {
+                fail();
+                break;
+            }
+            tc::tc_fence_after();
+            const int b = t / per_img, rr = t - b * per_img;
+            const int y0 = (rr / tiles_x) * TR, x = (rr % tiles_x) * kTileX + warp * 32 + lane;
+#pragma unroll 1
+            for (int r = 0; r < TR; ++r) {
+                const int y = y0 + r;
+                const bool inside = (x < a.W) && (y < a.H);
+                const size_t pix = (static_cast<size_t>(b) * a.H + y) * a.W + x;
+#pragma unroll 1
+                for (int j0 = 0; j0 < N; j0 += 16) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(tmem + lane_base + acc * TR * N + r * N + j0, v);
+                    tc::tmem_wait_ld();
+                    if (!inside) continue;
+                    float f[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[e]);
+                    if (a.epi_mode == kEpiF32Planar) {
+                        const size_t plane = static_cast<size_t>(a.H) * a.W;
+                        float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
+                                   static_cast<size_t>(y) * a.W + x;
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int n = j0 + e;
+                            if (n < a.cout) o[n * plane] = f[e] + (a.bias ? __ldg(a.bias + n) : 0.f);
+                        }
+                        continue;
+                    }
+                    if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
+                        if (a.bias) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) f[e] += __ldg(a.bias + j0 + e);
+                        }
+                        if (a.epi_mode == kEpiReluBF16) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
+                        }
+                    } else if (a.epi_mode == kEpiMaskBF16) {
+                        const uint4 *m = reinterpret_cast<const uint4 *>(a.act + pix * N + j0);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint4 q = __ldg(m + h);
+                            const uint32_t *u = &q.x;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const float2 mv = unpack_bf16x2(u[k]);
+                                f[8 * h + 2 * k] = mv.x > 0.f ? f[8 * h + 2 * k] : 0.f;
+                                f[8 * h + 2 * k + 1] = mv.y > 0.f ? f[8 * h + 2 * k + 1] : 0.f;
+                            }
+                        }
+                    }
+                    uint4 *o = reinterpret_cast<uint4 *>(a.out + pix * N + j0);
+                    o[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                      pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+                    o[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
+                                      pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&bars.acce[acc]);
+        }
+    }
+
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 8) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, C::kCols);
+    }
+}
+
+__global__ void pack_weights_kernel(const float *__restrict__ w, int cin, int cout, int transpose,
+                                    int cin_pad, int n, __nv_bfloat16 *__restrict__ dst) {
+    const int64_t total = static_cast<int64_t>(cin_pad / 16) * 9 * 2 * n * 8;
+    for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int e = static_cast<int>(idx % 8);
+        const int o = static_cast<int>((idx / 8) % n);
+        const int kg = static_cast<int>((idx / (8 * n)) % 2);
+        const int tap = static_cast<int>((idx / (16 * n)) % 9);
+        const int c = static_cast<int>(idx / (144 * static_cast<int64_t>(n)));
+        const int k = c * 16 + kg * 8 + e;  // input channel of this convolution
+        const int dy = tap / 3, dx = tap % 3;
+        float v = 0.f;
+        if (!transpose) {
+            if (o < cout && k < cin) v = w[((static_cast<int64_t>(o) * cin + k) * 3 + dy) * 3 + dx];
+        } else {  // data gradient: input channel k is an output channel of w
+            if (o < cin && k < cout)
+                v = w[((static_cast<int64_t>(k) * cin + o) * 3 + (2 - dy)) * 3 + (2 - dx)];
+        }
+        dst[idx] = __float2bfloat16_rn(v);
+    }
+}
+
+template <int N>
+int launch(const ConvArgs &a, cudaStream_t stream) {
+    using C = Cfg<N>;
+    static int configured_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_dev != dev) {
+        if (cudaFuncSetAttribute(conv3x3_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::kSmem) != cudaSuccess)
+            return SPP_ERR_CUDA;
+        configured_dev = dev;
+    }
+    const int64_t ntiles = static_cast<int64_t>(a.B) * ((a.H + C::TR - 1) / C::TR) *
+                           ((a.W + kTileX - 1) / kTileX);
+    if (ntiles == 0) return SPP_OK;
+    const int grid = static_cast<int>(std::min<int64_t>(ntiles, sm_count()));
+    conv3x3_kernel<N><<<grid, kThreads, C::kSmem, stream>>>(a);
+    count_launch();
+    return launch_status();
+}
+
+}  // namespace
+
+int pack_weights(const float *w, int cin, int cout, int transpose, int cin_pad, int n,
+                 __nv_bfloat16 *dst, cudaStream_t stream) {
+    const int64_t total = static_cast<int64_t>(cin_pad / 16) * 9 * 2 * n * 8;
+    if (total == 0) return SPP_OK;
+    const int grid = static_cast<int>(std::min<int64_t>((total + 255) / 256, 4 * sm_count()));
+    pack_weights_kernel<<<grid, 256, 0, stream>>>(w, cin, cout, transpose, cin_pad, n, dst);
+    count_launch();
+    return launch_status();
+}
+
+int conv3x3(const ConvArgs &a, cudaStream_t stream) {
+    if (a.B < 0 || a.H < 0 || a.W < 0 || a.cin_pad <= 0 || a.cin_pad % 16 || !supported_n(a.n))
+        return SPP_ERR_ARG;
+    if (!a.wpack || !aligned16(a.wpack)) return SPP_ERR_ALIGN;
+    switch (a.n) {
+        case 16: return launch<16>(a, stream);
+        case 32: return launch<32>(a, stream);
+        case 64: return launch<64>(a, stream);
+        case 96: return launch<96>(a, stream);
+        case 128: return launch<128>(a, stream);
+        default: return launch<192>(a, stream);
+    }
+}
+
+}  // namespace conv
+}  // namespace spp

@@ -1,0 +1,378 @@
+// The learned predictor (Sec. 3, Sec. 6.3): a U-Net of 3x3 convolutions on
+// the tensor cores (conv_tc.cu) that maps the G-buffer features and the
+// previous output to the density logit and the kernel logits of the three
+// pyramid levels.  This file holds the layer table, parameter packing, the
+// feature assembly, the density softmax and the forward orchestration.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "conv_tc.cuh"
+#include "spp_internal.cuh"
+#include "unet_internal.cuh"
+
+namespace spp {
+namespace unet {
+
+const Layer kLayers[kNumLayers] = {
+    {12, 32, 1},  {32, 32, 1},  {32, 64, 1}, {64, 64, 1}, {64, 128, 1},
+    {128, 128, 1}, {128, 25, 0}, {192, 64, 1}, {64, 64, 1}, {64, 29, 0},
+    {96, 32, 1},  {32, 32, 1},  {32, 55, 0},
+};
+
+int round16(int c) { return (c + 15) / 16 * 16; }
+
+// MMA width of a layer's forward convolution (its output channels, padded).
+int fwd_n(int i) { return kLayers[i].relu ? kLayers[i].cout : (kLayers[i].cout <= 32 ? 32 : 64); }
+
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+PackedLayout packed_layout(int with_backward) {
+    PackedLayout L{};
+    size_t off = 0;
+    int64_t toff = 0;
+    for (int i = 0; i < kNumLayers; ++i) {
+        const Layer &l = kLayers[i];
+        L.theta_w[i] = toff;
+        L.theta_b[i] = toff + static_cast<int64_t>(l.cout) * l.cin * 9;
+        toff = L.theta_b[i] + l.cout;
+        L.fwd[i] = off;
+        off = align256(off + conv::packed_bytes(round16(l.cin), fwd_n(i)));
+        L.bias[i] = off;
+        off = align256(off + sizeof(float) * fwd_n(i));
+    }
+    L.param_count = toff;
+    for (int i = 0; i < kNumLayers; ++i) {
+        L.bwd[i] = 0;
+        if (with_backward && i > 0) {  // no data gradient is needed for the input layer
+            L.bwd[i] = off;
+            off = align256(off + conv::packed_bytes(round16(kLayers[i].cout), kLayers[i].cin));
+        }
+    }
+    L.total = off;
+    return L;
+}
+
+ActLayout act_layout(int B, int W, int H) {
+    ActLayout A{};
+    const size_t p0 = static_cast<size_t>(B) * H * W, p1 = p0 / 4, p2 = p0 / 16;
+    size_t off = 0;
+    auto take = [&](size_t elems) {
+        const size_t o = off;
+        off = align256(off + elems * sizeof(__nv_bfloat16));
+        return o;
+    };
+    A.e0a = take(p0 * 32);
+    A.s0 = take(p0 * 32);
+    A.e1a = take(p1 * 64);
+    A.s1 = take(p1 * 64);
+    A.e2a = take(p2 * 128);
+    A.bt = take(p2 * 128);
+    A.d1a = take(p1 * 64);
+    A.t1 = take(p1 * 64);
+    A.d0a = take(p0 * 32);
+    A.t0 = take(p0 * 32);
+    A.zmax = off;
+    off = align256(off + sizeof(uint32_t) * std::max(B, 1));
+    A.total = off;
+    return A;
+}
+
+namespace {
+
+__global__ void assemble_kernel(const float *__restrict__ albedo, const float *__restrict__ normal,
+                                const float *__restrict__ depth, const float *__restrict__ mv,
+                                const float *__restrict__ prev, int64_t n, float *__restrict__ out) {
+    const float inv_ln100 = 1.0f / 4.605170185988091f;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        out[i] = albedo[i];
+        out[n + i] = albedo[n + i];
+        out[2 * n + i] = albedo[2 * n + i];
+        out[3 * n + i] = normal[i];
+        out[4 * n + i] = normal[n + i];
+        out[5 * n + i] = normal[2 * n + i];
+        out[6 * n + i] = logf(depth[i]) * inv_ln100;
+        out[7 * n + i] = mv[i] * 0.125f;
+        out[8 * n + i] = mv[n + i] * 0.125f;
+        out[9 * n + i] = prev ? prev[i] : 0.f;
+        out[10 * n + i] = prev ? prev[n + i] : 0.f;
+        out[11 * n + i] = prev ? prev[2 * n + i] : 0.f;
+    }
+}
+
+__global__ void copy_bias_kernel(const float *__restrict__ b, int cout, int n, float *__restrict__ dst) {
+    const int i = threadIdx.x;
+    if (i < n) dst[i] = i < cout ? b[i] : 0.f;
+}
+
+// Order-preserving map of a float to an unsigned integer (for atomicMax).
+__device__ __forceinline__ uint32_t ordered(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// zmax[b] = max over the frame of z = logits0[b][54]
+__global__ void zmax_kernel(const float *__restrict__ logits0, int64_t hw, int B,
+                            uint32_t *__restrict__ zmax) {
+    const int b = blockIdx.y;
+    const float *z = logits0 + (static_cast<int64_t>(b) * 55 + kDensityChannel) * hw;
+    float m = -INFINITY;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < hw;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        m = fmaxf(m, z[i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? wm[threadIdx.x] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) atomicMax(zmax + b, ordered(m));
+    }
+}
+
+__global__ void density_kernel(const float *__restrict__ logits0, int64_t hw,
+                               const uint32_t *__restrict__ zmax, float *__restrict__ d) {
+    const int b = blockIdx.y;
+    const float *z = logits0 + (static_cast<int64_t>(b) * 55 + kDensityChannel) * hw;
+    const float m = unordered(zmax[b]);
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < hw;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        d[static_cast<int64_t>(b) * hw + i] = expf(z[i] - m);
+}
+
+}  // namespace
+
+int forward(const unsigned char *packed, const float *in12, int B, int W, int H, float *density,
+            float *logits0, float *logits1, float *logits2, unsigned char *ws, int32_t *status,
+            cudaStream_t stream) {
+    const PackedLayout P = packed_layout(0);
+    const ActLayout A = act_layout(B, W, H);
+    auto act = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(ws + off); };
+    auto wp = [&](int i) { return reinterpret_cast<const __nv_bfloat16 *>(packed + P.fwd[i]); };
+    auto bias = [&](int i) { return reinterpret_cast<const float *>(packed + P.bias[i]); };
+    const int W1 = W / 2, H1 = H / 2, W2 = W / 4, H2 = H / 4;
+    int rc = SPP_OK;
+    auto run = [&](int i, int w, int h, int mode, const __nv_bfloat16 *s0, int c0,
+                   const __nv_bfloat16 *s1, int c1, const float *sf, int cf, __nv_bfloat16 *out,
+                   float *outf) {
+        if (rc != SPP_OK) return;
+        conv::ConvArgs a;
+        a.B = B;
+        a.H = h;
+        a.W = w;
+        a.cin_pad = round16(kLayers[i].cin);
+        a.n = fwd_n(i);
+        a.cout = kLayers[i].cout;
+        a.src_mode = mode;
+        a.src0 = s0;
+        a.c0 = c0;
+        a.src1 = s1;
+        a.c1 = c1;
+        a.srcf = sf;
+        a.cf = cf;
+        a.wpack = wp(i);
+        a.bias = bias(i);
+        a.epi_mode = kLayers[i].relu ? conv::kEpiReluBF16 : conv::kEpiF32Planar;
+        a.out = out;
+        a.outf = outf;
+        a.status = status;
+        rc = conv::conv3x3(a, stream);
+    };
+    using namespace conv;
+    run(0, W, H, kSrcPlanarF32, nullptr, 0, nullptr, 0, in12, 12, act(A.e0a), nullptr);
+    run(1, W, H, kSrcNHWC, act(A.e0a), 32, nullptr, 0, nullptr, 0, act(A.s0), nullptr);
+    run(2, W1, H1, kSrcPool, act(A.s0), 32, nullptr, 0, nullptr, 0, act(A.e1a), nullptr);
+    run(3, W1, H1, kSrcNHWC, act(A.e1a), 64, nullptr, 0, nullptr, 0, act(A.s1), nullptr);
+    run(4, W2, H2, kSrcPool, act(A.s1), 64, nullptr, 0, nullptr, 0, act(A.e2a), nullptr);
+    run(5, W2, H2, kSrcNHWC, act(A.e2a), 128, nullptr, 0, nullptr, 0, act(A.bt), nullptr);
+    run(6, W2, H2, kSrcNHWC, act(A.bt), 128, nullptr, 0, nullptr, 0, nullptr, logits2);
+    run(7, W1, H1, kSrcConcatUp, act(A.s1), 64, act(A.bt), 128, nullptr, 0, act(A.d1a), nullptr);
+    run(8, W1, H1, kSrcNHWC, act(A.d1a), 64, nullptr, 0, nullptr, 0, act(A.t1), nullptr);
+    run(9, W1, H1, kSrcNHWC, act(A.t1), 64, nullptr, 0, nullptr, 0, nullptr, logits1);
+    run(10, W, H, kSrcConcatUp, act(A.s0), 32, act(A.t1), 64, nullptr, 0, act(A.d0a), nullptr);
+    run(11, W, H, kSrcNHWC, act(A.d0a), 32, nullptr, 0, nullptr, 0, act(A.t0), nullptr);
+    run(12, W, H, kSrcNHWC, act(A.t0), 32, nullptr, 0, nullptr, 0, nullptr, logits0);
+    if (rc != SPP_OK) return rc;
+    uint32_t *zmax = reinterpret_cast<uint32_t *>(ws + A.zmax);
+    if (cudaMemsetAsync(zmax, 0, sizeof(uint32_t) * B, stream) != cudaSuccess) return SPP_ERR_CUDA;
+    const int64_t hw = static_cast<int64_t>(W) * H;
+    const int gx = static_cast<int>(std::min<int64_t>((hw + 255) / 256, 2 * sm_count()));
+    zmax_kernel<<<dim3(gx, B), 256, 0, stream>>>(logits0, hw, B, zmax);
+    density_kernel<<<dim3(gx, B), 256, 0, stream>>>(logits0, hw, zmax, density);
+    count_launch(2);
+    return launch_status();
+}
+
+int pack(const float *theta, int with_backward, unsigned char *packed, cudaStream_t stream) {
+    const PackedLayout P = packed_layout(with_backward);
+    for (int i = 0; i < kNumLayers; ++i) {
+        const Layer &l = kLayers[i];
+        int rc = conv::pack_weights(theta + P.theta_w[i], l.cin, l.cout, 0, round16(l.cin), fwd_n(i),
+                                    reinterpret_cast<__nv_bfloat16 *>(packed + P.fwd[i]), stream);
+        if (rc != SPP_OK) return rc;
+        copy_bias_kernel<<<1, 256, 0, stream>>>(theta + P.theta_b[i], l.cout, fwd_n(i),
+                                                reinterpret_cast<float *>(packed + P.bias[i]));
+        count_launch();
+        if (with_backward && i > 0) {
+            rc = conv::pack_weights(theta + P.theta_w[i], l.cin, l.cout, 1, round16(l.cout), l.cin,
+                                    reinterpret_cast<__nv_bfloat16 *>(packed + P.bwd[i]), stream);
+            if (rc != SPP_OK) return rc;
+        }
+    }
+    return launch_status();
+}
+
+int assemble(const float *albedo, const float *normal, const float *depth, const float *mv,
+             const float *prev, int W, int H, float *in12, cudaStream_t stream) {
+    const int64_t n = static_cast<int64_t>(W) * H;
+    if (n == 0) return SPP_OK;
+    const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 4 * sm_count()));
+    assemble_kernel<<<grid, 256, 0, stream>>>(albedo, normal, depth, mv, prev, n, in12);
+    count_launch();
+    return launch_status();
+}
+
+}  // namespace unet
+}  // namespace spp
+
+// ------------------------------------------------------------------ C ABI
+using spp::aligned16;
+
+extern "C" int spp_unet_layer(int i, int *cin, int *cout, int *relu) {
+    if (i < 0 || i >= spp::unet::kNumLayers || !cin || !cout || !relu) return SPP_ERR_ARG;
+    *cin = spp::unet::kLayers[i].cin;
+    *cout = spp::unet::kLayers[i].cout;
+    *relu = spp::unet::kLayers[i].relu;
+    return SPP_OK;
+}
+
+extern "C" int64_t spp_unet_param_count(void) { return spp::unet::packed_layout(0).param_count; }
+
+extern "C" size_t spp_unet_packed_bytes(int with_backward) {
+    return spp::unet::packed_layout(with_backward).total;
+}
+
+extern "C" int spp_unet_pack(const float *theta, int with_backward, void *packed,
+                             size_t packed_bytes, cudaStream_t stream) {
+    if (!theta || !packed) return SPP_ERR_ARG;
+    if (!aligned16(theta) || (reinterpret_cast<uintptr_t>(packed) & 255u)) return SPP_ERR_ALIGN;
+    if (packed_bytes < spp::unet::packed_layout(with_backward).total) return SPP_ERR_WORKSPACE;
+    return spp::unet::pack(theta, with_backward, static_cast<unsigned char *>(packed), stream);
+}
+
+extern "C" int spp_assemble_features(const float *albedo, const float *normal, const float *depth,
+                                     const float *mv, const float *prev_ldr, int W, int H,
+                                     float *in12, cudaStream_t stream) {
+    if (W < 0 || H < 0 || !albedo || !normal || !depth || !mv || !in12) return SPP_ERR_ARG;
+    if (!aligned16(albedo) || !aligned16(normal) || !aligned16(depth) || !aligned16(mv) ||
+        !aligned16(in12) || (prev_ldr && !aligned16(prev_ldr)))
+        return SPP_ERR_ALIGN;
+    return spp::unet::assemble(albedo, normal, depth, mv, prev_ldr, W, H, in12, stream);
+}
+
+extern "C" size_t spp_predict_workspace_bytes(int B, int W, int H) {
+    if (B < 0 || W < 0 || H < 0) return 0;
+    return spp::unet::act_layout(B, W, H).total;
+}
+
+extern "C" int spp_predict_density_and_kernels(const void *packed, const float *in12, int B, int W,
+                                               int H, float *density, float *logits0,
+                                               float *logits1, float *logits2, void *ws,
+                                               size_t ws_bytes, int32_t *status,
+                                               cudaStream_t stream) {
+    if (B < 0 || W < 0 || H < 0 || !packed || !in12 || !density || !logits0 || !logits1 ||
+        !logits2 || !ws)
+        return SPP_ERR_ARG;
+    if (W % 4 || H % 4) return SPP_ERR_SHAPE;
+    if ((reinterpret_cast<uintptr_t>(packed) & 255u) || (reinterpret_cast<uintptr_t>(ws) & 255u) ||
+        !aligned16(in12) || !aligned16(density) || !aligned16(logits0) || !aligned16(logits1) ||
+        !aligned16(logits2))
+        return SPP_ERR_ALIGN;
+    if (ws_bytes < spp::unet::act_layout(B, W, H).total) return SPP_ERR_WORKSPACE;
+    if (static_cast<int64_t>(B) * W * H == 0) return SPP_OK;
+    return spp::unet::forward(static_cast<const unsigned char *>(packed), in12, B, W, H, density,
+                              logits0, logits1, logits2, static_cast<unsigned char *>(ws), status,
+                              stream);
+}
+
+// ----------------------------------------------------- single conv layers
+extern "C" size_t spp_conv3x3_workspace_bytes(int cin, int cout) {
+    if (cin <= 0 || cout <= 0) return 0;
+    using spp::unet::round16;
+    return std::max(spp::conv::packed_bytes(round16(cin), round16(cout)),
+                    spp::conv::packed_bytes(round16(cout), round16(cin)));
+}
+
+static int conv_layer_common(const void *in, int B, int W, int H, int cin_conv, int n_conv,
+                             const float *w, void *out, void *ws, size_t ws_bytes) {
+    if (B < 0 || W < 0 || H < 0 || cin_conv <= 0 || !in || !w || !out || !ws) return SPP_ERR_ARG;
+    if (cin_conv % 8 || !spp::conv::supported_n(n_conv)) return SPP_ERR_ARG;
+    if (!aligned16(in) || !aligned16(out) || !aligned16(w) || !aligned16(ws)) return SPP_ERR_ALIGN;
+    if (ws_bytes < spp::conv::packed_bytes(spp::unet::round16(cin_conv), n_conv))
+        return SPP_ERR_WORKSPACE;
+    return SPP_OK;
+}
+
+extern "C" int spp_conv3x3_forward(const uint16_t *x, int B, int W, int H, int cin, int cout,
+                                   const float *w, const float *bias, int relu, uint16_t *y,
+                                   void *ws, size_t ws_bytes, int32_t *status,
+                                   cudaStream_t stream) {
+    int rc = conv_layer_common(x, B, W, H, cin, cout, w, y, ws, ws_bytes);
+    if (rc != SPP_OK) return rc;
+    const int cin_pad = spp::unet::round16(cin);
+    auto *wp = static_cast<__nv_bfloat16 *>(ws);
+    rc = spp::conv::pack_weights(w, cin, cout, 0, cin_pad, cout, wp, stream);
+    if (rc != SPP_OK) return rc;
+    spp::conv::ConvArgs a;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.cin_pad = cin_pad;
+    a.n = cout;
+    a.cout = cout;
+    a.src_mode = spp::conv::kSrcNHWC;
+    a.src0 = reinterpret_cast<const __nv_bfloat16 *>(x);
+    a.c0 = cin;
+    a.wpack = wp;
+    a.bias = bias;
+    a.epi_mode = relu ? spp::conv::kEpiReluBF16 : spp::conv::kEpiBF16;
+    a.out = reinterpret_cast<__nv_bfloat16 *>(y);
+    a.status = status;
+    return spp::conv::conv3x3(a, stream);
+}
+
+extern "C" int spp_conv3x3_backward_data(const uint16_t *g, int B, int W, int H, int cin, int cout,
+                                         const float *w, const uint16_t *act, uint16_t *gx,
+                                         void *ws, size_t ws_bytes, int32_t *status,
+                                         cudaStream_t stream) {
+    int rc = conv_layer_common(g, B, W, H, cout, cin, w, gx, ws, ws_bytes);
+    if (rc != SPP_OK) return rc;
+    if (act && !aligned16(act)) return SPP_ERR_ALIGN;
+    const int cin_pad = spp::unet::round16(cout);
+    auto *wp = static_cast<__nv_bfloat16 *>(ws);
+    rc = spp::conv::pack_weights(w, cin, cout, 1, cin_pad, cin, wp, stream);
+    if (rc != SPP_OK) return rc;
+    spp::conv::ConvArgs a;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.cin_pad = cin_pad;
+    a.n = cin;
+    a.cout = cin;
+    a.src_mode = spp::conv::kSrcNHWC;
+    a.src0 = reinterpret_cast<const __nv_bfloat16 *>(g);
+    a.c0 = cout;
+    a.wpack = wp;
+    a.epi_mode = act ? spp::conv::kEpiMaskBF16 : spp::conv::kEpiBF16;
+    a.act = reinterpret_cast<const __nv_bfloat16 *>(act);
+    a.out = reinterpret_cast<__nv_bfloat16 *>(gx);
+    a.status = status;
+    return spp::conv::conv3x3(a, stream);
+}

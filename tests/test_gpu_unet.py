@@ -1,0 +1,283 @@
+"""Parity of the tensor-core predictor (a10) with the FP64 network oracle.
+
+Precision model (both sides): BF16 inputs, weights and hidden activations
+(round to nearest even), FP32 accumulation on the GPU, FP64 in the oracle.
+
+* Single layers: the oracle replays the rounding (the exact FP64 sum of the
+  same BF16 operands, then one rounding to BF16).  The GPU's FP32
+  accumulation can move a value across a BF16 rounding boundary only when
+  the exact sum lies within the accumulation error of it, so every element
+  is within one BF16 unit in the last place and almost all are equal.
+* Layer by layer inside the network (each layer fed the GPU's own inputs):
+  the same one-ulp criterion, which also covers the fused pooling,
+  upsample + concatenation, FP32 input and FP32 head paths.
+* Whole network: a BF16 network is chaotic under rounding.  Measured on the
+  oracle alone, a relative jitter of 1e-7 (FP32 accumulation level) on the
+  pre-activations moves its BF16-rounded logits by about 0.5 % of their RMS
+  (2.8 % at the worst element), because every flipped rounding propagates;
+  BF16 against exact FP64 differs by about 0.8 % RMS (3.8 % worst).  So the
+  GPU is held to the BF16 error level against both oracles: RMS difference
+  < 1.5 % and worst element < 8 % of the logits' RMS.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle.unet as U
+import spp_inputs as inp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spp():
+    from conftest import build_spp_lib
+    build_spp_lib()
+    import paper_2602_08642_gb300 as spp
+    torch.cuda.set_device(0)
+    return spp
+
+
+def bf16_ulp(v):
+    """Spacing of BF16 numbers at |v| (8 significant bits)."""
+    a = np.maximum(np.abs(v), 2.0 ** -126)
+    return 2.0 ** (np.floor(np.log2(a)) - 7)
+
+
+def _nchw(t_nhwc):
+    return t_nhwc.float().cpu().numpy().astype(np.float64).transpose(0, 3, 1, 2)
+
+
+CASES = [  # cin, cout, B, H, W
+    (16, 32, 2, 6, 200), (32, 32, 1, 5, 128), (64, 64, 2, 4, 130), (128, 128, 1, 3, 300),
+    (192, 64, 1, 4, 256), (96, 32, 1, 7, 70), (32, 192, 1, 2, 129), (8, 16, 1, 4, 50),
+    (64, 96, 1, 3, 257), (32, 128, 3, 2, 33),
+]
+
+
+@pytest.mark.parametrize("cin,cout,B,H,W", CASES)
+def test_conv3x3_forward_parity(spp, cin, cout, B, H, W):
+    g = torch.Generator().manual_seed(cin * 1000 + cout + W)
+    x = torch.randn(B, H, W, cin, generator=g).to(torch.bfloat16)
+    w = (torch.randn(cout, cin, 3, 3, generator=g) / np.sqrt(9 * cin)).float()
+    bias = (0.1 * torch.randn(cout, generator=g)).float()
+    y = torch.empty(B, H, W, cout, dtype=torch.bfloat16, device="cuda")
+    ws = torch.empty(spp.binding.spp_conv3x3_workspace_bytes(cin, cout), dtype=torch.uint8,
+                     device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")[:1]
+    spp.check(spp.binding.spp_conv3x3_forward(x.cuda(), B, W, H, cin, cout, w.cuda(), bias.cuda(),
+                                              True, y, ws, st))
+    assert spp.binding.spp_get_status(st) == 0
+    got = _nchw(y)
+    xb = _nchw(x)
+    wb = U.round_bf16(w.numpy())
+    exact = np.stack([np.maximum(U.conv3x3(xb[b], wb, bias.numpy()), 0) for b in range(B)])
+    ref = U.round_bf16(exact)
+    # FP32 accumulation error bound of a sum of 9 cin + 1 terms
+    absterm = np.stack([U.conv3x3(np.abs(xb[b]), np.abs(wb), np.abs(bias.numpy()))
+                        for b in range(B)])
+    acc = (9 * cin + 1) * 2.0 ** -24 * absterm
+    diff = np.abs(got - ref)
+    assert np.all(diff <= np.maximum(bf16_ulp(ref) * 1.0001, 2 * acc + bf16_ulp(acc))), \
+        float((diff / bf16_ulp(ref)).max())
+    assert np.mean(diff == 0) > 0.99
+    # stated bound against the exact value: BF16 rounding (half an ulp,
+    # 2^-9 relative, taken as 2^-8 for the rounding of the accumulated
+    # value) plus the accumulation error
+    assert np.all(np.abs(got - exact) <= 2.0 ** -8 * np.abs(exact) + acc + 1e-30)
+
+
+@pytest.mark.parametrize("cin,cout,B,H,W", [(32, 32, 2, 5, 140), (64, 128, 1, 4, 128),
+                                            (192, 64, 1, 3, 200), (96, 32, 1, 4, 64),
+                                            (32, 64, 1, 6, 33), (128, 25 + 7, 1, 4, 96)])
+@pytest.mark.parametrize("masked", [False, True])
+def test_conv3x3_backward_data_parity(spp, cin, cout, B, H, W, masked):
+    g = torch.Generator().manual_seed(cin * 7 + cout + W + masked)
+    gy = torch.randn(B, H, W, cout, generator=g).to(torch.bfloat16)
+    w = (torch.randn(cout, cin, 3, 3, generator=g) / np.sqrt(9 * cout)).float()
+    act = torch.randn(B, H, W, cin, generator=g).to(torch.bfloat16) if masked else None
+    gx = torch.empty(B, H, W, cin, dtype=torch.bfloat16, device="cuda")
+    ws = torch.empty(spp.binding.spp_conv3x3_workspace_bytes(cin, cout), dtype=torch.uint8,
+                     device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")[:1]
+    spp.check(spp.binding.spp_conv3x3_backward_data(
+        gy.cuda(), B, W, H, cin, cout, w.cuda(), None if act is None else act.cuda(), gx, ws, st))
+    assert spp.binding.spp_get_status(st) == 0
+    got = _nchw(gx)
+    gb = _nchw(gy)
+    wb = U.round_bf16(w.numpy())
+    dummy = np.zeros((cin, H, W))
+    exact = np.stack([U.conv3x3_backward(dummy, wb, gb[b])[0] for b in range(B)])
+    if masked:
+        exact = exact * (_nchw(act) > 0)
+    ref = U.round_bf16(exact)
+    absterm = np.stack([U.conv3x3_backward(dummy, np.abs(wb), np.abs(gb[b]))[0] for b in range(B)])
+    acc = (9 * cout) * 2.0 ** -24 * absterm
+    diff = np.abs(got - ref)
+    assert np.all(diff <= np.maximum(bf16_ulp(ref) * 1.0001, 2 * acc + bf16_ulp(acc)))
+    assert np.mean(diff == 0) > 0.99
+
+
+def _features(B, W, H, seed):
+    xs = []
+    for b in range(B):
+        clean, gb = inp.scene(W, H, seed=seed + b)
+        mv = inp.motion_affine(W, H, seed=seed + b)
+        prev = np.clip(clean / 4.0, 0, 1).astype(np.float32)
+        xs.append(U.features(gb["albedo"], gb["normal"], gb["depth"], mv, prev))
+    return np.stack(xs)
+
+
+def test_assemble_features_parity(spp):
+    W, H = 96, 40
+    clean, gb = inp.scene(W, H, seed=5)
+    mv = inp.motion_affine(W, H, seed=5)
+    prev = np.clip(clean / 4.0, 0, 1).astype(np.float32)
+    out = torch.empty(12, H, W, device="cuda")
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    spp.check(spp.binding.spp_assemble_features(c(gb["albedo"]), c(gb["normal"]), c(gb["depth"]),
+                                                c(mv), c(prev), W, H, out))
+    ref = U.features(gb["albedo"], gb["normal"], gb["depth"], mv, prev)
+    assert np.allclose(out.cpu().numpy(), ref, rtol=2e-7, atol=2e-7)
+    spp.check(spp.binding.spp_assemble_features(c(gb["albedo"]), c(gb["normal"]), c(gb["depth"]),
+                                                c(mv), None, W, H, out))
+    assert torch.all(out[9:] == 0)
+
+
+def _theta(weight_noise=0.0):
+    """He-initialised parameters with random biases.  The whole-network test
+    keeps the He scale (gain about 1 per layer) so that rounding differences
+    are not amplified layer after layer; the layer-wise test also perturbs
+    the weights, which it can afford since every layer is checked alone."""
+    table, total = U.param_offsets()
+    theta = inp.unet_params(U.LAYERS, seed=21, head_scale=1.0).astype(np.float64)
+    rng = np.random.default_rng(22)
+    for name, cin, cout, wo, bo in table:
+        theta[bo:bo + cout] = 0.05 * rng.standard_normal(cout)
+        theta[wo:bo] += weight_noise * rng.standard_normal(bo - wo)
+    return theta.astype(np.float32)
+
+
+def _act_views(ws, B, W, H):
+    """(byte offset, pixels, channels) of the BF16 NHWC activations the
+    forward keeps in its workspace, in the library's order (each region
+    256-byte aligned)."""
+    p0 = B * H * W
+    sizes = [("e0a", p0, 32), ("s0", p0, 32), ("e1a", p0 // 4, 64), ("s1", p0 // 4, 64),
+             ("e2a", p0 // 16, 128), ("bt", p0 // 16, 128), ("d1a", p0 // 4, 64),
+             ("t1", p0 // 4, 64), ("d0a", p0, 32), ("t0", p0, 32)]
+    out, off = {}, 0
+    for name, n, c in sizes:
+        out[name] = (off, n, c)
+        off = (off + n * c * 2 + 255) // 256 * 256
+    return out
+
+
+def _read_act(ws, spec, B, h, w):
+    off, n, c = spec
+    t = ws[off:off + n * c * 2].view(torch.bfloat16).view(B, h, w, c)
+    return _nchw(t)
+
+
+def _predict(spp, theta, x, B, W, H, return_ws=False):
+    packed = torch.empty(spp.binding.spp_unet_packed_bytes(False), dtype=torch.uint8,
+                         device="cuda")
+    spp.check(spp.binding.spp_unet_pack(torch.from_numpy(theta).cuda(), False, packed))
+    ws = torch.empty(spp.binding.spp_predict_workspace_bytes(B, W, H), dtype=torch.uint8,
+                     device="cuda")
+    d = torch.empty(B, H, W, device="cuda")
+    l0 = torch.empty(B, 55, H, W, device="cuda")
+    l1 = torch.empty(B, 29, H // 2, W // 2, device="cuda")
+    l2 = torch.empty(B, 25, H // 4, W // 4, device="cuda")
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")[:1]
+    spp.check(spp.binding.spp_predict_density_and_kernels(
+        packed, torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda(), B, W, H, d, l0, l1,
+        l2, ws, st))
+    assert spp.binding.spp_get_status(st) == 0
+    res = [t.cpu().numpy().astype(np.float64) for t in (d, l0, l1, l2)]
+    return (res, ws) if return_ws else res
+
+
+def test_predict_layerwise_parity(spp):
+    """Each layer of the network, fed the GPU's own BF16 inputs (read back
+    from the workspace), against the oracle layer with the same rounding:
+    covers the fused pooling, upsample + concatenation, FP32 input and FP32
+    planar head paths of the convolution."""
+    B, W, H = 2, 48, 32
+    theta = _theta(weight_noise=0.05)
+    x = _features(B, W, H, seed=30)
+    (d, l0, l1, l2), ws = _predict(spp, theta, x, B, W, H, return_ws=True)
+    sp = _act_views(ws, B, W, H)
+    dims = {"e0a": (H, W), "s0": (H, W), "e1a": (H // 2, W // 2), "s1": (H // 2, W // 2),
+            "e2a": (H // 4, W // 4), "bt": (H // 4, W // 4), "d1a": (H // 2, W // 2),
+            "t1": (H // 2, W // 2), "d0a": (H, W), "t0": (H, W)}
+    A = {k: _read_act(ws, sp[k], B, *dims[k]) for k in sp}
+    P = {k: (U.round_bf16(w), b) for k, (w, b) in U.unpack(theta).items()}
+    xb = U.round_bf16(x)
+
+    def pool(a):
+        return U.round_bf16(np.stack([U.pool2(a[b]) for b in range(B)]))
+
+    def up(a):
+        return np.stack([U.up2(a[b]) for b in range(B)])
+
+    inputs = {
+        "e0a": xb, "e0b": A["e0a"], "e1a": pool(A["s0"]), "e1b": A["e1a"], "e2a": pool(A["s1"]),
+        "e2b": A["e2a"], "h2": A["bt"], "d1a": np.concatenate([A["s1"], up(A["bt"])], axis=1),
+        "d1b": A["d1a"], "h1": A["t1"], "d0a": np.concatenate([A["s0"], up(A["t1"])], axis=1),
+        "d0b": A["d0a"], "h0": A["t0"]}
+    outputs = {"e0a": A["e0a"], "e0b": A["s0"], "e1a": A["e1a"], "e1b": A["s1"],
+               "e2a": A["e2a"], "e2b": A["bt"], "h2": l2, "d1a": A["d1a"], "d1b": A["t1"],
+               "h1": l1, "d0a": A["d0a"], "d0b": A["t0"], "h0": l0}
+    report = {}
+    for name, cin, cout, relu in U.LAYERS:
+        w, b = P[name]
+        xin = inputs[name]
+        exact = np.stack([U.conv3x3(xin[i], w, b) for i in range(B)])
+        absterm = np.stack([U.conv3x3(np.abs(xin[i]), np.abs(w), np.abs(b)) for i in range(B)])
+        acc = (9 * cin + 1) * 2.0 ** -24 * absterm
+        got = outputs[name]
+        if relu:
+            ref = U.round_bf16(np.maximum(exact, 0))
+            tol = np.maximum(bf16_ulp(ref) * 1.0001, 2 * acc + bf16_ulp(acc))
+        else:
+            ref = exact
+            tol = 2 * acc + 1e-30
+        diff = np.abs(got - ref)
+        report[name] = (float((diff / np.maximum(tol, 1e-30)).max()), float(np.mean(diff == 0)))
+    print("layer: max |diff| / tolerance, fraction equal:", report)
+    bad = {k: v for k, v in report.items() if v[0] > 1.0}
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("B,W,H", [(2, 48, 32), (1, 264, 12)])
+def test_predict_parity(spp, B, W, H):
+    theta = _theta()
+    x = _features(B, W, H, seed=30)
+    d, l0, l1, l2 = _predict(spp, theta, x, B, W, H)
+    worst = {}
+    for b in range(B):
+        fr = U.forward(theta, x[b], round_bf16_acts=True)
+        fe = U.forward(theta, x[b], round_bf16_acts=False)
+        refs = [fr["logits"][0], fr["logits"][1], fr["logits"][2], fr["z"]]
+        gots = [l0[b, :54], l1[b], l2[b], l0[b, 54]]
+        exacts = [fe["logits"][0], fe["logits"][1], fe["logits"][2], fe["z"]]
+        for k, (g, r, e) in enumerate(zip(gots, refs, exacts)):
+            scale = np.sqrt(np.mean(r * r))
+            err = np.abs(g - r).max() / scale
+            print("output", k, "max |gpu - oracle(bf16)| / rms", err,
+                  "rms", np.sqrt(np.mean((g - r) ** 2)) / scale)
+            assert err < 8e-2, (b, k, err)
+            assert np.sqrt(np.mean((g - r) ** 2)) / scale < 1.5e-2
+            err_exact = np.sqrt(np.mean((g - e) ** 2)) / scale
+            assert err_exact < 1.5e-2, (b, k, err_exact)
+            assert np.abs(g - e).max() / scale < 8e-2
+            worst[k] = max(worst.get(k, 0), err_exact)
+        # d = exp(z - max z): its relative error is the absolute error of z
+        dz = np.exp(fr["z"] - fr["z"].max())
+        zs = np.sqrt(np.mean(fr["z"] ** 2))
+        assert np.all(np.abs(d[b] - dz) <= (0.16 * zs) * dz + 1e-7)
+        # and it is exp of the GPU's own z minus the GPU's own maximum
+        zg = l0[b, 54]
+        assert np.allclose(np.log(d[b]) + zg.max(), zg, rtol=0, atol=2e-6 * (1 + np.abs(zg).max()))
+    print("rms error vs exact FP64 (logits l0, l1, l2, z):", worst)
