@@ -197,6 +197,12 @@ int spp_splat_samples(const int32_t *offsets, const float *rgb, const float *s,
  * the warped previous frame). */
 size_t spp_reconstruct_workspace_bytes(int W, int H, int L);
 
+/* Tone map of a whole image (Sec. 5, the epilogue of the full-resolution
+ * reconstruction applied on its own): ldr [3][H][W] = sRGB(tau(x)) of hdr
+ * [3][H][W], for reference images and the recurrent network input. */
+int spp_tonemap_image(const float *hdr, int W, int H, const spp_tonemap *tm, float *ldr,
+                      cudaStream_t stream);
+
 /*
  * W_t L_{t-1}: the previous HDR output warped along the motion vectors
  * (App. A, Eq. app-recon-full; Sec. 6.1).  warped(x, y) is the bilinear sample
@@ -300,6 +306,11 @@ int spp_tonemap_backward(const float *hdr, int W, int H, const spp_tonemap *tm,
  * sign(ldr - ref) / n. */
 int spp_l1_loss(const float *ldr, const float *ref, int64_t n, float *loss, float *grad_ldr,
                 cudaStream_t stream);
+
+/* Evaluation metric: *mse (device double, OVERWRITTEN) = mean over the n
+ * elements of (a - b)^2, accumulated in FP64.  PSNR = -10 log10(mse) for
+ * images in [0, 1]. */
+int spp_mse(const float *a, const float *b, int64_t n, double *mse, cudaStream_t stream);
 
 /* Pyramid backward (Eq. app-pyramid): grad_L0 [3][H][W] += sum over levels
  * l >= 1 of 4^-l grad_layers[l] at the pixel's coarse cell (grad_layers[0]
@@ -428,6 +439,47 @@ int spp_conv3x3_forward(const uint16_t *x, int B, int W, int H, int cin, int cou
 int spp_conv3x3_backward_data(const uint16_t *g, int B, int W, int H, int cin, int cout,
                               const float *w, const uint16_t *act, uint16_t *gx, void *ws,
                               size_t ws_bytes, int32_t *status, cudaStream_t stream);
+
+
+/* Weight gradient of a 3x3 layer: gw [cout][cin][3][3] = sum over pixels
+ * of g (x) the shifted x, gb [cout] = sum over pixels of g (both FP32,
+ * OVERWRITTEN; gb may be NULL).  x [B][H][W][cin] and g [B][H][W][cout] are
+ * BF16 NHWC (cin, cout multiples of 8, cout <= 128).  The partial sums of
+ * the pixel splits are added in a fixed order, so the result is
+ * deterministic. */
+size_t spp_conv3x3_backward_weights_workspace_bytes(int B, int W, int H, int cin, int cout);
+int spp_conv3x3_backward_weights(const uint16_t *x, const uint16_t *g, int B, int W, int H,
+                                 int cin, int cout, float *gw, float *gb, void *ws,
+                                 size_t ws_bytes, int32_t *status, cudaStream_t stream);
+
+/* ------------------------------------- a11: training the predictor */
+/* Workspace bytes of spp_unet_backward. */
+size_t spp_unet_backward_workspace_bytes(int B, int W, int H);
+
+/* Backward of spp_predict_density_and_kernels (Sec. 6.3 training): from the
+ * gradients of the loss with respect to its outputs,
+ *   grad_logits0 [B][55][H][W] (planes 0..53 the level-0 kernel logits,
+ *                plane 54 the density logit z, e.g. from
+ *                spp_density_backward),
+ *   grad_logits1 [B][29][H/2][W/2], grad_logits2 [B][25][H/4][W/4],
+ * computes grad_theta (FP32, the layout of theta, OVERWRITTEN).  packed must
+ * come from spp_unet_pack(theta, with_backward = 1); fwd_ws is the
+ * workspace of the forward call on the same in12 (its activations are read,
+ * not recomputed).  Gradients between layers are BF16 NHWC; every
+ * contraction runs on the tensor cores with FP32 accumulation. */
+int spp_unet_backward(const void *packed, const float *in12, int B, int W, int H,
+                      const void *fwd_ws, size_t fwd_ws_bytes, const float *grad_logits0,
+                      const float *grad_logits1, const float *grad_logits2, float *grad_theta,
+                      void *ws, size_t ws_bytes, int32_t *status, cudaStream_t stream);
+
+/* One AdamW step (Loshchilov & Hutter, decoupled weight decay) on n FP32
+ * parameters, step >= 1 (bias correction 1 - beta^step):
+ *   g = grad_scale * grad; m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ *   theta -= lr (m / (1-b1^step) / (sqrt(v / (1-b2^step)) + eps) + wd theta).
+ * m and v start at zero. */
+int spp_adamw_step(float *theta, const float *grad, float *m, float *v, int64_t n, int step,
+                   float lr, float beta1, float beta2, float eps, float weight_decay,
+                   float grad_scale, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

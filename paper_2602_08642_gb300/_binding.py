@@ -100,6 +100,14 @@ _SIGS = {
     "spp_conv3x3_workspace_bytes": (_SZ, [_I, _I]),
     "spp_conv3x3_forward": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _I, _P, _P, _SZ, _P, _P]),
     "spp_conv3x3_backward_data": (_I, [_P, _I, _I, _I, _I, _I, _P, _P, _P, _P, _SZ, _P, _P]),
+    "spp_conv3x3_backward_weights_workspace_bytes": (_SZ, [_I, _I, _I, _I, _I]),
+    "spp_conv3x3_backward_weights": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _SZ, _P, _P]),
+    "spp_unet_backward_workspace_bytes": (_SZ, [_I, _I, _I]),
+    "spp_unet_backward": (_I, [_P, _P, _I, _I, _I, _P, _SZ, _P, _P, _P, _P, _P, _SZ, _P, _P]),
+    "spp_adamw_step": (_I, [_P, _P, _P, _P, _I64, _I, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
+    "spp_tonemap_image": (_I, [_P, _I, _I, ctypes.POINTER(spp_tonemap), _P, _P]),
+    "spp_mse": (_I, [_P, _P, _I64, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -363,3 +371,47 @@ def spp_conv3x3_backward_data(g, B, W, H, cin, cout, w, act, gx, ws, status, str
     return lib.spp_conv3x3_backward_data(_dev(g, bf), B, W, H, cin, cout, _dev(w, torch.float32),
                                          _dev(act, bf), _dev(gx, bf), _dev(ws), _nbytes(ws),
                                          _dev(status, torch.int32), _stream(stream))
+
+
+def spp_conv3x3_backward_weights_workspace_bytes(B, W, H, cin, cout) -> int:
+    return int(lib.spp_conv3x3_backward_weights_workspace_bytes(B, W, H, cin, cout))
+
+
+def spp_conv3x3_backward_weights(x, g, B, W, H, cin, cout, gw, gb, ws, status, stream=None) -> int:
+    bf, f = torch.bfloat16, torch.float32
+    return lib.spp_conv3x3_backward_weights(_dev(x, bf), _dev(g, bf), B, W, H, cin, cout,
+                                            _dev(gw, f), _dev(gb, f), _dev(ws), _nbytes(ws),
+                                            _dev(status, torch.int32), _stream(stream))
+
+
+# ------------------------------------------------------------ a11: training
+def spp_unet_backward_workspace_bytes(B: int, W: int, H: int) -> int:
+    return int(lib.spp_unet_backward_workspace_bytes(B, W, H))
+
+
+def spp_unet_backward(packed, in12, B, W, H, fwd_ws, g0, g1, g2, grad_theta, ws, status,
+                      stream=None) -> int:
+    f = torch.float32
+    return lib.spp_unet_backward(_dev(packed), _dev(in12, f), B, W, H, _dev(fwd_ws),
+                                 _nbytes(fwd_ws), _dev(g0, f), _dev(g1, f), _dev(g2, f),
+                                 _dev(grad_theta, f), _dev(ws), _nbytes(ws),
+                                 _dev(status, torch.int32), _stream(stream))
+
+
+def spp_adamw_step(theta, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   weight_decay=1e-4, grad_scale=1.0, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_adamw_step(_dev(theta, f), _dev(grad, f), _dev(m, f), _dev(v, f),
+                              theta.numel(), int(step), lr, beta1, beta2, eps, weight_decay,
+                              grad_scale, _stream(stream))
+
+
+def spp_tonemap_image(hdr, W, H, tm, ldr, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_tonemap_image(_dev(hdr, f), W, H, ctypes.byref(tm), _dev(ldr, f),
+                                 _stream(stream))
+
+
+def spp_mse(a, b, n, out, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_mse(_dev(a, f), _dev(b, f), int(n), _dev(out, torch.float64), _stream(stream))

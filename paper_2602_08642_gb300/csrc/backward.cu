@@ -303,6 +303,27 @@ l1_loss_kernel(const float *__restrict__ a, const float *__restrict__ b, long lo
     }
 }
 
+// Mean squared difference (for PSNR); partial sums in FP64, one atomic per block.
+__global__ void sq_err_kernel(const float *__restrict__ a, const float *__restrict__ b, long long n,
+                              double *__restrict__ out) {
+    double v = 0.0;
+    for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const double d = static_cast<double>(a[i]) - static_cast<double>(b[i]);
+        v += d * d;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __shared__ double part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += part[w];
+        atomicAdd(out, t / static_cast<double>(n));
+    }
+}
+
 // Eq. app-pyramid backward: grad_L0 += 4^-l grad_L^l at the parent cell.
 struct GradLayers {
     const float *p[5];
@@ -500,6 +521,18 @@ int spp_l1_loss(const float *ldr, const float *ref, int64_t n, float *loss, floa
     if (n == 0) return SPP_OK;
     l1_loss_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
         ldr, ref, static_cast<long long>(n), loss, grad_ldr);
+    count_launch();
+    return launch_status();
+}
+
+int spp_mse(const float *a, const float *b, int64_t n, double *mse, cudaStream_t stream) {
+    using namespace spp;
+    if (n < 0 || !a || !b || !mse) return SPP_ERR_ARG;
+    if (!aligned16(a) || !aligned16(b) || !aligned16(mse)) return SPP_ERR_ALIGN;
+    if (cudaMemsetAsync(mse, 0, sizeof(double), stream) != cudaSuccess) return SPP_ERR_CUDA;
+    if (n == 0) return SPP_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4LL * sm_count());
+    sq_err_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(a, b, n, mse);
     count_launch();
     return launch_status();
 }

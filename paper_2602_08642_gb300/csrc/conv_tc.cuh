@@ -63,6 +63,24 @@ int pack_weights(const float *w, int cin, int cout, int transpose, int cin_pad, 
 // Runs the convolution; returns SPP_OK or an SPP error code.
 int conv3x3(const ConvArgs &a, cudaStream_t stream);
 
+// Weight gradient (wgrad_tc.cu).  x describes the layer's input exactly as
+// the forward convolution reads it (B, H, W, cin_pad and the source mode);
+// g the gradient with respect to the layer's output before its ReLU
+// (kSrcNHWC with c0 = its channel count, or kSrcPlanarF32 with cf = cout),
+// on the same grid.  gw [cout][cin][3][3] and gb [cout] are overwritten.
+struct WgradArgs {
+    ConvArgs x;
+    ConvArgs g;
+    int cin = 0, cout = 0;  // real channel counts
+    int n = 0;              // cout padded: 32, 64 or 128 (the MMA N)
+    float *partial = nullptr;
+    float *pbias = nullptr;
+    int32_t *status = nullptr;
+};
+int wgrad_splits(int B, int W, int H, int cin_pad);
+size_t wgrad_workspace_bytes(int B, int W, int H, int cin_pad, int n);
+int wgrad(const WgradArgs &a, float *gw, float *gb, void *ws, cudaStream_t stream);
+
 // Supported MMA widths of conv3x3.
 inline bool supported_n(int n) {
     return n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 192;

@@ -11,6 +11,8 @@
 // vector), so that the 5 x 5 gathers read shared memory.  The per-pixel
 // logits are read once, coalesced along x, and the joint softmax is evaluated
 // in registers.
+#include <algorithm>
+
 #include "recon_common.cuh"
 
 namespace spp {
@@ -158,6 +160,20 @@ void launch_level(bool tone, dim3 grid, dim3 block, cudaStream_t st, const float
                                                               Wl, Hl, out, out_ldr, tm);
 }
 
+// Tone map of a whole HDR image (Sec. 5), for reference images and the
+// recurrent network input.
+__global__ void tonemap_image_kernel(const float *__restrict__ hdr, int64_t n,
+                                     float *__restrict__ ldr, ToneArgs tm) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float r, g, b;
+        tone_map(hdr[i], hdr[n + i], hdr[2 * n + i], tm, r, g, b);
+        ldr[i] = r;
+        ldr[n + i] = g;
+        ldr[2 * n + i] = b;
+    }
+}
+
 ToneArgs tone_args(const spp_tonemap *tm) {
     ToneArgs t{1.0f, 1.0f, 0.0f, 0.5f, 0.5f};
     if (tm) {
@@ -181,6 +197,21 @@ size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
 }  // namespace spp
 
 extern "C" {
+
+int spp_tonemap_image(const float *hdr, int W, int H, const spp_tonemap *tm, float *ldr,
+                      cudaStream_t stream) {
+    using namespace spp;
+    if (W < 0 || H < 0 || !hdr || !ldr) return SPP_ERR_ARG;
+    if (!aligned16(hdr) || !aligned16(ldr)) return SPP_ERR_ALIGN;
+    const ToneArgs t = tone_args(tm);
+    if (!tone_ok(t)) return SPP_ERR_ARG;
+    const int64_t n = static_cast<int64_t>(W) * H;
+    if (n == 0) return SPP_OK;
+    const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 8 * sm_count()));
+    tonemap_image_kernel<<<grid, 256, 0, stream>>>(hdr, n, ldr, t);
+    count_launch();
+    return launch_status();
+}
 
 int spp_warp_previous(const float *prev_hdr, const float *mv, int W, int H, float *warped,
                       cudaStream_t stream) {

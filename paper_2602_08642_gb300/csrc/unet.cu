@@ -149,57 +149,78 @@ __global__ void density_kernel(const float *__restrict__ logits0, int64_t hw,
 
 }  // namespace
 
+conv::ConvArgs layer_input(int i, int B, int W, int H, const float *in12,
+                           const unsigned char *ws) {
+    const ActLayout A = act_layout(B, W, H);
+    auto act = [&](size_t off) { return reinterpret_cast<const __nv_bfloat16 *>(ws + off); };
+    conv::ConvArgs a;
+    const int level = (i == E1A || i == E1B || i == D1A || i == D1B || i == H1)   ? 1
+                      : (i == E2A || i == E2B || i == H2) ? 2
+                                                          : 0;
+    a.B = B;
+    a.W = W >> level;
+    a.H = H >> level;
+    a.cin_pad = round16(kLayers[i].cin);
+    a.src_mode = conv::kSrcNHWC;
+    switch (i) {
+        case E0A: a.src_mode = conv::kSrcPlanarF32; a.srcf = in12; a.cf = 12; break;
+        case E0B: a.src0 = act(A.e0a); a.c0 = 32; break;
+        case E1A: a.src_mode = conv::kSrcPool; a.src0 = act(A.s0); a.c0 = 32; break;
+        case E1B: a.src0 = act(A.e1a); a.c0 = 64; break;
+        case E2A: a.src_mode = conv::kSrcPool; a.src0 = act(A.s1); a.c0 = 64; break;
+        case E2B: a.src0 = act(A.e2a); a.c0 = 128; break;
+        case H2: a.src0 = act(A.bt); a.c0 = 128; break;
+        case D1A:
+            a.src_mode = conv::kSrcConcatUp;
+            a.src0 = act(A.s1); a.c0 = 64; a.src1 = act(A.bt); a.c1 = 128;
+            break;
+        case D1B: a.src0 = act(A.d1a); a.c0 = 64; break;
+        case H1: a.src0 = act(A.t1); a.c0 = 64; break;
+        case D0A:
+            a.src_mode = conv::kSrcConcatUp;
+            a.src0 = act(A.s0); a.c0 = 32; a.src1 = act(A.t1); a.c1 = 64;
+            break;
+        case D0B: a.src0 = act(A.d0a); a.c0 = 32; break;
+        default: a.src0 = act(A.t0); a.c0 = 32; break;  // H0
+    }
+    return a;
+}
+
+size_t layer_output(int i, const ActLayout &A) {
+    static const int idx[kNumLayers] = {0, 1, 2, 3, 4, 5, -1, 6, 7, -1, 8, 9, -1};
+    const size_t offs[10] = {A.e0a, A.s0, A.e1a, A.s1, A.e2a, A.bt, A.d1a, A.t1, A.d0a, A.t0};
+    return idx[i] < 0 ? static_cast<size_t>(-1) : offs[idx[i]];
+}
+
 int forward(const unsigned char *packed, const float *in12, int B, int W, int H, float *density,
             float *logits0, float *logits1, float *logits2, unsigned char *ws, int32_t *status,
             cudaStream_t stream) {
     const PackedLayout P = packed_layout(0);
     const ActLayout A = act_layout(B, W, H);
-    auto act = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(ws + off); };
-    auto wp = [&](int i) { return reinterpret_cast<const __nv_bfloat16 *>(packed + P.fwd[i]); };
-    auto bias = [&](int i) { return reinterpret_cast<const float *>(packed + P.bias[i]); };
-    const int W1 = W / 2, H1 = H / 2, W2 = W / 4, H2 = H / 4;
-    int rc = SPP_OK;
-    auto run = [&](int i, int w, int h, int mode, const __nv_bfloat16 *s0, int c0,
-                   const __nv_bfloat16 *s1, int c1, const float *sf, int cf, __nv_bfloat16 *out,
-                   float *outf) {
-        if (rc != SPP_OK) return;
-        conv::ConvArgs a;
-        a.B = B;
-        a.H = h;
-        a.W = w;
-        a.cin_pad = round16(kLayers[i].cin);
+    float *heads[kNumLayers] = {};
+    heads[H0] = logits0;
+    heads[H1] = logits1;
+    heads[H2] = logits2;
+    static const int order[kNumLayers] = {E0A, E0B, E1A, E1B, E2A, E2B, H2,
+                                          D1A, D1B, H1,  D0A, D0B, H0};
+    for (int k = 0; k < kNumLayers; ++k) {
+        const int i = order[k];
+        conv::ConvArgs a = layer_input(i, B, W, H, in12, ws);
         a.n = fwd_n(i);
         a.cout = kLayers[i].cout;
-        a.src_mode = mode;
-        a.src0 = s0;
-        a.c0 = c0;
-        a.src1 = s1;
-        a.c1 = c1;
-        a.srcf = sf;
-        a.cf = cf;
-        a.wpack = wp(i);
-        a.bias = bias(i);
-        a.epi_mode = kLayers[i].relu ? conv::kEpiReluBF16 : conv::kEpiF32Planar;
-        a.out = out;
-        a.outf = outf;
+        a.wpack = reinterpret_cast<const __nv_bfloat16 *>(packed + P.fwd[i]);
+        a.bias = reinterpret_cast<const float *>(packed + P.bias[i]);
         a.status = status;
-        rc = conv::conv3x3(a, stream);
-    };
-    using namespace conv;
-    run(0, W, H, kSrcPlanarF32, nullptr, 0, nullptr, 0, in12, 12, act(A.e0a), nullptr);
-    run(1, W, H, kSrcNHWC, act(A.e0a), 32, nullptr, 0, nullptr, 0, act(A.s0), nullptr);
-    run(2, W1, H1, kSrcPool, act(A.s0), 32, nullptr, 0, nullptr, 0, act(A.e1a), nullptr);
-    run(3, W1, H1, kSrcNHWC, act(A.e1a), 64, nullptr, 0, nullptr, 0, act(A.s1), nullptr);
-    run(4, W2, H2, kSrcPool, act(A.s1), 64, nullptr, 0, nullptr, 0, act(A.e2a), nullptr);
-    run(5, W2, H2, kSrcNHWC, act(A.e2a), 128, nullptr, 0, nullptr, 0, act(A.bt), nullptr);
-    run(6, W2, H2, kSrcNHWC, act(A.bt), 128, nullptr, 0, nullptr, 0, nullptr, logits2);
-    run(7, W1, H1, kSrcConcatUp, act(A.s1), 64, act(A.bt), 128, nullptr, 0, act(A.d1a), nullptr);
-    run(8, W1, H1, kSrcNHWC, act(A.d1a), 64, nullptr, 0, nullptr, 0, act(A.t1), nullptr);
-    run(9, W1, H1, kSrcNHWC, act(A.t1), 64, nullptr, 0, nullptr, 0, nullptr, logits1);
-    run(10, W, H, kSrcConcatUp, act(A.s0), 32, act(A.t1), 64, nullptr, 0, act(A.d0a), nullptr);
-    run(11, W, H, kSrcNHWC, act(A.d0a), 32, nullptr, 0, nullptr, 0, act(A.t0), nullptr);
-    run(12, W, H, kSrcNHWC, act(A.t0), 32, nullptr, 0, nullptr, 0, nullptr, logits0);
-    if (rc != SPP_OK) return rc;
+        if (kLayers[i].relu) {
+            a.epi_mode = conv::kEpiReluBF16;
+            a.out = reinterpret_cast<__nv_bfloat16 *>(ws + layer_output(i, A));
+        } else {
+            a.epi_mode = conv::kEpiF32Planar;
+            a.outf = heads[i];
+        }
+        const int rc = conv::conv3x3(a, stream);
+        if (rc != SPP_OK) return rc;
+    }
     uint32_t *zmax = reinterpret_cast<uint32_t *>(ws + A.zmax);
     if (cudaMemsetAsync(zmax, 0, sizeof(uint32_t) * B, stream) != cudaSuccess) return SPP_ERR_CUDA;
     const int64_t hw = static_cast<int64_t>(W) * H;

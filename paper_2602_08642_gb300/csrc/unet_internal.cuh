@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "conv_tc.cuh"
+
 namespace spp {
 namespace unet {
 
@@ -43,9 +45,22 @@ struct ActLayout {
 };
 ActLayout act_layout(int B, int W, int H);
 
+// Input of layer i as its convolution reads it (grid, source mode, pointers
+// into the forward workspace `ws`, cin_pad); the caller fills the rest.
+conv::ConvArgs layer_input(int i, int B, int W, int H, const float *in12,
+                           const unsigned char *ws);
+// Byte offset of layer i's BF16 output in the forward workspace (heads: -1).
+size_t layer_output(int i, const ActLayout &A);
+
 int forward(const unsigned char *packed, const float *in12, int B, int W, int H, float *density,
             float *logits0, float *logits1, float *logits2, unsigned char *ws, int32_t *status,
             cudaStream_t stream);
+size_t backward_workspace_bytes(int B, int W, int H);
+int backward(const unsigned char *packed, const float *in12, int B, int W, int H,
+             const unsigned char *fws, const float *g0, const float *g1, const float *g2,
+             float *grad_theta, unsigned char *bws, int32_t *status, cudaStream_t stream);
+int adamw(float *theta, const float *grad, float *m, float *v, int64_t n, int step, float lr,
+          float b1, float b2, float eps, float wd, float grad_scale, cudaStream_t stream);
 int pack(const float *theta, int with_backward, unsigned char *packed, cudaStream_t stream);
 int assemble(const float *albedo, const float *normal, const float *depth, const float *mv,
              const float *prev, int W, int H, float *in12, cudaStream_t stream);

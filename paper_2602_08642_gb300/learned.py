@@ -1,0 +1,277 @@
+"""The learned sampler / kernel predictor (Sec. 3, Sec. 6.3) and its
+training loop, driven over the C ABI.
+
+Every arithmetic step runs in ``libspp.so``: feature assembly, the tensor-
+core U-Net forward and backward, the density softmax and its gradient, the
+sampling, splatting and reconstruction with their backward passes, the L1
+loss in tone-mapped sRGB, AdamW and the parameter packing.  This module
+allocates the buffers (PyTorch) and calls the entry points in order.
+
+One training step (after Sec. 6.3, two-frame window):
+  frame t-1  features without a previous output -> network -> density and
+             logits -> samples -> reconstruction without the temporal term
+  frame t    previous output warped along the motion vectors and tone
+             mapped -> features -> network -> samples -> reconstruction with
+             the temporal term -> L1 against the tone-mapped reference;
+             gradients flow back through the tone map, the reconstruction
+             (kernel logits), the splat (density s through 1/s and the
+             holdout ramp, Sec. 4.3) and the spatial softmax into the
+             network, whose parameters take one AdamW step.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _binding as B
+from .pipeline import Frame
+
+LEVELS = 3
+PHI = 0.125
+
+
+def _zeros(*shape, dtype=torch.float32):
+    return torch.zeros(*shape, dtype=dtype, device="cuda")
+
+
+class Predictor:
+    """Device state of the network for batches of B frames of W x H."""
+
+    def __init__(self, theta: torch.Tensor, B_: int, W: int, H: int, train: bool = False):
+        if W % 4 or H % 4:
+            raise ValueError("W and H must be divisible by 4")
+        self.B, self.W, self.H, self.train = B_, W, H, train
+        self.theta = theta.detach().to("cuda", torch.float32).contiguous().clone()
+        if self.theta.numel() != B.spp_unet_param_count():
+            raise ValueError("theta has the wrong size")
+        self.packed = self._aligned(B.spp_unet_packed_bytes(train))
+        self.fws = self._aligned(B.spp_predict_workspace_bytes(B_, W, H))
+        self.in12 = _zeros(B_, 12, H, W)
+        self.density = _zeros(B_, H, W)
+        self.logits = [_zeros(B_, 55, H, W), _zeros(B_, 29, H // 2, W // 2),
+                       _zeros(B_, 25, H // 4, W // 4)]
+        self.status = _zeros(4, dtype=torch.int32)[:1]
+        if train:
+            self.bws = self._aligned(B.spp_unet_backward_workspace_bytes(B_, W, H))
+            self.grad = _zeros(self.theta.numel())
+            self.m = _zeros(self.theta.numel())
+            self.v = _zeros(self.theta.numel())
+            self.g_logits = [torch.zeros_like(t) for t in self.logits]
+            self.step_count = 0
+        self.pack()
+
+    @staticmethod
+    def _aligned(n: int) -> torch.Tensor:
+        buf = torch.empty(int(n) + 256, dtype=torch.uint8, device="cuda")
+        off = (-buf.data_ptr()) % 256
+        return buf[off:off + int(n)]
+
+    def pack(self):
+        B.check(B.spp_unet_pack(self.theta, self.train, self.packed), "spp_unet_pack")
+
+    def features(self, b: int, albedo, normal, depth, mv, prev_ldr=None):
+        B.check(B.spp_assemble_features(albedo, normal, depth, mv, prev_ldr, self.W, self.H,
+                                        self.in12[b]), "spp_assemble_features")
+
+    def forward(self):
+        B.check(B.spp_predict_density_and_kernels(self.packed, self.in12, self.B, self.W, self.H,
+                                                  self.density, *self.logits, self.fws,
+                                                  self.status), "spp_predict")
+
+    def backward(self):
+        B.check(B.spp_unet_backward(self.packed, self.in12, self.B, self.W, self.H, self.fws,
+                                    *self.g_logits, self.grad, self.bws, self.status),
+                "spp_unet_backward")
+
+    def adamw(self, lr: float, weight_decay: float = 1e-4, grad_scale: float = 1.0):
+        self.step_count += 1
+        B.check(B.spp_adamw_step(self.theta, self.grad, self.m, self.v, self.step_count, lr=lr,
+                                 weight_decay=weight_decay, grad_scale=grad_scale), "adamw")
+        self.pack()
+
+    def frame_logits(self, b: int, temporal: bool):
+        l0 = self.logits[0][b, :54] if temporal else self.logits[0][b, :29]
+        return [l0, self.logits[1][b], self.logits[2][b]]
+
+
+class FrameData:
+    """Device copies of one training / evaluation sample: two consecutive
+    frames (clean radiance and G-buffer) and the motion of the second."""
+
+    def __init__(self, pair: dict):
+        c = lambda a: torch.from_numpy(a).contiguous().cuda()
+        self.clean_prev, self.clean = c(pair["clean_prev"]), c(pair["clean"])
+        self.gprev = {k: c(v) for k, v in pair["gbuf_prev"].items()}
+        self.g = {k: c(v) for k, v in pair["gbuf"].items()}
+        self.mv = c(pair["mv"])
+        self.H, self.W = self.clean.shape[1:]
+
+
+class Renderer:
+    """Per-frame sampling / reconstruction state for B frames of W x H."""
+
+    def __init__(self, B_: int, W: int, H: int, budget: float):
+        self.B, self.W, self.H, self.budget = B_, W, H, budget
+        self.frames = [Frame(W, H, LEVELS, max_budget=budget) for _ in range(B_)]
+        self.tm = B.make_tonemap()
+        self.hdr_prev = [_zeros(3, H, W) for _ in range(B_)]
+        self.warped = [_zeros(3, H, W) for _ in range(B_)]
+        self.prev_ldr = [_zeros(3, H, W) for _ in range(B_)]
+        self.ref = [_zeros(3, H, W) for _ in range(B_)]
+        self.mask = _zeros(H, W, dtype=torch.uint8)
+        self.hats = [[_zeros(3, H >> l, W >> l) for l in range(LEVELS)] for _ in range(B_)]
+        self.hdr = [_zeros(3, H, W) for _ in range(B_)]
+        self.ldr = [_zeros(3, H, W) for _ in range(B_)]
+        self.loss = [_zeros(4)[:1] for _ in range(B_)]
+        self.g_ldr = _zeros(3, H, W)
+        self.g_hdr = [_zeros(3, H >> l, W >> l) for l in range(LEVELS)]
+        self.g_noisy = [_zeros(3, H >> l, W >> l) for l in range(LEVELS)]
+        self.g_warped = _zeros(3, H, W)
+        self.g_s = _zeros(W * H)
+        self.mse = torch.zeros(2, dtype=torch.float64, device="cuda")[:1]
+        self.dws = Predictor._aligned(B.spp_density_backward_workspace_bytes())
+        self.cur_params = [None] * B_
+
+    def params(self, frame: int, seed: int):
+        return B.make_params(self.budget, uniform_fraction=PHI, seed=seed, frame=frame)
+
+    def previous_frame(self, b: int, d, logits, clean, seed: int, frame: int):
+        """Frame t-1 of sample b (no temporal term); its output goes to hdr_prev[b]."""
+        fr = self.frames[b]
+        fr.alloc(d, self.params(frame, seed))
+        fr.render(clean, seed ^ 0xC0FFEE, frame)
+        fr.splat()
+        out = fr.reconstruct(logits, tm=self.tm)
+        self.hdr_prev[b].copy_(out)
+
+    def warp_previous(self, b: int, mv):
+        B.check(B.spp_warp_previous(self.hdr_prev[b], mv, self.W, self.H, self.warped[b]), "warp")
+        B.check(B.spp_tonemap_image(self.warped[b], self.W, self.H, self.tm, self.prev_ldr[b]),
+                "tonemap")
+
+    def current_frame(self, b: int, d, logits, clean, seed: int, frame: int):
+        """Frame t of sample b, level by level (the coarse outputs are kept
+        for the backward), with the temporal term over warped[b]."""
+        fr = self.frames[b]
+        self.cur_params[b] = self.params(frame, seed)
+        fr.alloc(d, self.cur_params[b])
+        fr.render(clean, seed ^ 0xC0FFEE, frame)
+        fr.splat()
+        hats = self.hats[b]
+        for l in range(LEVELS - 1, 0, -1):
+            B.check(B.spp_reconstruct_level(fr.layers[l], logits[l], logits[l].shape[0],
+                                            hats[l + 1] if l + 1 < LEVELS else None, None, None,
+                                            self.W >> l, self.H >> l, None, hats[l], None),
+                    "level")
+        B.check(B.spp_reconstruct_level(fr.layers[0], logits[0], logits[0].shape[0], hats[1],
+                                        self.warped[b], self.mask, self.W, self.H, self.tm,
+                                        self.hdr[b], self.ldr[b]), "level 0")
+
+    def reference(self, b: int, clean):
+        B.check(B.spp_tonemap_image(clean, self.W, self.H, self.tm, self.ref[b]), "tonemap")
+
+    def backward(self, b: int, d, logits, g_logits):
+        """L1 loss of sample b and its gradient into g_logits (level 0 planes
+        0..53 and the density plane 54, levels 1 and 2)."""
+        fr = self.frames[b]
+        n = 3 * self.W * self.H
+        B.check(B.spp_l1_loss(self.ldr[b], self.ref[b], n, self.loss[b], self.g_ldr), "l1")
+        g = self.g_hdr[0]
+        g.zero_()
+        B.check(B.spp_tonemap_backward(self.hdr[b], self.W, self.H, self.tm, self.g_ldr, g),
+                "tonemap backward")
+        for t in self.g_noisy:
+            t.zero_()
+        self.g_warped.zero_()
+        hats = self.hats[b]
+        for l in range(LEVELS):
+            gc = self.g_hdr[l + 1] if l + 1 < LEVELS else None
+            if gc is not None:
+                gc.zero_()
+            B.check(B.spp_reconstruct_level_backward(
+                fr.layers[l], logits[l], logits[l].shape[0], hats[l + 1] if l + 1 < LEVELS else None,
+                self.warped[b] if l == 0 else None, self.mask if l == 0 else None,
+                self.W >> l, self.H >> l, self.g_hdr[l], g_logits[l], self.g_noisy[l], gc,
+                self.g_warped if l == 0 else None), "level backward")
+        B.check(B.spp_pyramid_backward(self.g_noisy, self.W, self.H, LEVELS, self.g_noisy[0]),
+                "pyramid backward")
+        B.check(B.spp_splat_backward(fr.offsets, fr.counts, fr.rgb, fr.s, fr.layers[0],
+                                     self.g_noisy[0], fr.capacity, self.W, self.H,
+                                     self.cur_params[b], self.g_s),
+                "splat backward")
+        B.check(B.spp_density_backward(d, self.W * self.H, self.budget, PHI, self.g_s,
+                                       g_logits[3], self.dws), "density backward")
+
+    def psnr(self, b: int) -> float:
+        B.check(B.spp_mse(self.ldr[b], self.ref[b], 3 * self.W * self.H, self.mse), "mse")
+        m = float(self.mse.item())
+        return -10.0 * math.log10(max(m, 1e-30))
+
+
+class Trainer:
+    """Trains the predictor on batches of two-frame samples."""
+
+    def __init__(self, theta: torch.Tensor, batch: int, size: int, budget: float = 0.25,
+                 lr: float = 1e-3, weight_decay: float = 1e-4):
+        self.net = Predictor(theta, batch, size, size, train=True)
+        self.rnd = Renderer(batch, size, size, budget)
+        self.lr, self.wd = lr, weight_decay
+        self.step_index = 0
+
+    def step(self, samples: list[FrameData], seed: int) -> float:
+        """One optimisation step on len(samples) == batch samples; returns
+        the mean loss (reading it synchronises)."""
+        net, rnd = self.net, self.rnd
+        f_prev, f_cur = 2 * self.step_index, 2 * self.step_index + 1
+        for b, s in enumerate(samples):
+            net.features(b, s.gprev["albedo"], s.gprev["normal"], s.gprev["depth"], s.mv, None)
+        net.forward()
+        for b, s in enumerate(samples):
+            rnd.previous_frame(b, net.density[b], net.frame_logits(b, False), s.clean_prev,
+                               seed + b, f_prev)
+            rnd.warp_previous(b, s.mv)
+            net.features(b, s.g["albedo"], s.g["normal"], s.g["depth"], s.mv, rnd.prev_ldr[b])
+        net.forward()
+        for b, s in enumerate(samples):
+            logits = net.frame_logits(b, True)
+            rnd.current_frame(b, net.density[b], logits, s.clean, seed + b, f_cur)
+            rnd.reference(b, s.clean)
+            gl = [net.g_logits[0][b, :54], net.g_logits[1][b], net.g_logits[2][b],
+                  net.g_logits[0][b, 54]]
+            rnd.backward(b, net.density[b], logits, gl)
+        net.backward()
+        net.adamw(self.lr, self.wd, grad_scale=1.0 / len(samples))
+        self.step_index += 1
+        return float(sum(l.item() for l in rnd.loss)) / len(samples)
+
+
+def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None,
+             fixed_logits: list[torch.Tensor] | None = None, seed: int = 99) -> list[float]:
+    """PSNR (tone-mapped sRGB against the tone-mapped clean image) of frame
+    t of each sample.  theta None runs the plain method: uniform density
+    d = 1 and the fixed logits (54 / 29 / 25 channels)."""
+    W, H = samples[0].W, samples[0].H
+    rnd = Renderer(1, W, H, budget)
+    net = Predictor(theta, 1, W, H) if theta is not None else None
+    ones = torch.ones(H, W, device="cuda")
+    out = []
+    for i, s in enumerate(samples):
+        if net is not None:
+            net.features(0, s.gprev["albedo"], s.gprev["normal"], s.gprev["depth"], s.mv, None)
+            net.forward()
+            d, lg = net.density[0], net.frame_logits(0, False)
+        else:
+            d, lg = ones, [fixed_logits[0][:29], fixed_logits[1], fixed_logits[2]]
+        rnd.previous_frame(0, d, lg, s.clean_prev, seed + i, 0)
+        rnd.warp_previous(0, s.mv)
+        if net is not None:
+            net.features(0, s.g["albedo"], s.g["normal"], s.g["depth"], s.mv, rnd.prev_ldr[0])
+            net.forward()
+            d, lg = net.density[0], net.frame_logits(0, True)
+        else:
+            lg = [fixed_logits[0], fixed_logits[1], fixed_logits[2]]
+        rnd.current_frame(0, d, lg, s.clean, seed + i, 1)
+        rnd.reference(0, s.clean)
+        out.append(rnd.psnr(0))
+    return out
