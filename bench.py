@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="bounded CPU work for the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-vs-plain 4K section")
+    ap.add_argument("--learned-size", type=int, default=3840,
+                    help="width of the learned-vs-plain frames (height = width * 9 / 16)")
+    ap.add_argument("--train-steps", type=int, default=300)
     ap.add_argument("--frames", type=int, default=0,
                     help="distinct input frames resident on the device (default: the workload's)")
     return ap.parse_args()
@@ -339,6 +344,10 @@ def run_ours(args, rank, world, local):
     # end to end: host inputs -> device -> frame -> tone-mapped frame on host
     e2e = run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, world, dist)
 
+    learned = None
+    if not args.no_learned:
+        learned = run_learned(args, spp, Bnd, dev, rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         import oracle
@@ -355,10 +364,160 @@ def run_ours(args, rank, world, local):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": launches,
             "samples_per_frame": int(fr.sample_count()),
+            "learned_vs_plain": learned,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_learned(args, spp, Bnd, dev, rank):
+    """Learned (BF16 tensor-core network + FP32 reconstruction) against the
+    plain method (uniform density, fixed kernels) on the same 4K frames, at
+    0.125 / 0.25 / 0.5 spp: per-frame time and PSNR in tone-mapped sRGB
+    against the clean image.  The network is first trained on the GPU by the
+    library's own kernels (two-frame 128 x 128 crops, batch 8)."""
+    import torch
+
+    import spp_inputs as inp
+    from paper_2602_08642_gb300 import learned as Lm
+
+    W = args.learned_size
+    H = W * 9 // 16 // 4 * 4
+    F = 4  # distinct frames, cycled for timing
+    # training
+    train = [Lm.FrameData(inp.training_pair(128, seed=100 + i + 1000 * rank)) for i in range(32)]
+    theta0 = torch.from_numpy(inp.unet_params(Lm.layer_table(), seed=5,
+                                              head_bias=inp.fixed_head_bias()))
+    tr = Lm.Trainer(theta0, 8, 128, 0.25, lr=1e-3)
+    rng = np.random.default_rng(rank)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for k in range(args.train_steps):
+        idx = rng.choice(len(train), 8, replace=False)
+        losses.append(tr.step([train[i] for i in idx], seed=1000 + 17 * k))
+    torch.cuda.synchronize()
+    train_ms = (time.perf_counter() - t0) * 1e3 / max(args.train_steps, 1)
+    theta = tr.net.theta
+    del tr, train
+
+    # frames of one scene drifting over F frames
+    frames = []
+    for t in range(F):
+        clean, gb = inp.scene(W, H, seed=3, frame=t)
+        c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        frames.append(dict(clean=c(clean), albedo=c(gb["albedo"]), normal=c(gb["normal"]),
+                           depth=c(gb["depth"]), mv=c(inp.scene_motion(W, H, t))))
+    fixed = [torch.from_numpy(a).to(dev) for a in inp.fixed_logits(W, H, 3, True)]
+    tm = spp.make_tonemap()
+    refs = []
+    for x in frames:
+        r = torch.empty((3, H, W), device=dev)
+        Bnd.check(Bnd.spp_tonemap_image(x["clean"], W, H, tm, r), "tonemap")
+        refs.append(r)
+    net = Lm.Predictor(theta, 1, W, H)
+    ones = torch.ones((H, W), device=dev)
+    mask = torch.zeros((H, W), dtype=torch.uint8, device=dev)
+    warped = torch.empty((3, H, W), device=dev)
+    prev_ldr = torch.empty((3, H, W), device=dev)
+    hats = [None] + [torch.empty((3, H >> l, W >> l), device=dev) for l in range(1, 3)]
+    mse = torch.zeros(2, dtype=torch.float64, device=dev)[:1]
+    stream = torch.cuda.current_stream()
+    flops = Lm.flops_per_frame(W, H)
+    peaks, peak_kind = measured_peaks()
+    out = {"workload": f"{W}x{H} sequence of {F} distinct frames of one drifting procedural "
+                       f"scene (cycled for timing), 3-level pyramid, temporal term with true "
+                       f"motion, tone map tau + sRGB; learned = feature assembly + BF16 "
+                       f"tensor-core U-Net + density softmax + the plain path; plain = uniform "
+                       f"density and fixed kernels (kd = -r^2/2, ku = kt = 0)",
+           "training": {"steps": args.train_steps, "crop": 128, "batch": 8, "spp": 0.25,
+                        "ms_per_step": train_ms, "loss_first20": float(np.mean(losses[:20])),
+                        "loss_last20": float(np.mean(losses[-20:]))},
+           "network": {"gflop_per_frame": flops / 1e9}, "budgets": {}}
+    net_ms = []
+    for budget in (0.125, 0.25, 0.5):
+        fr = spp.Frame(W, H, 3, max_budget=budget, device=dev)
+        res = {}
+        for form in ("plain", "learned"):
+            state = {"prev": None, "parity": 0}
+            psnr = []
+
+            def frame(k, record=None):
+                x = frames[k % F]
+                prev = state["prev"]
+                if prev is not None:
+                    Bnd.check(Bnd.spp_warp_previous(prev, x["mv"], W, H, warped), "warp")
+                if form == "learned":
+                    if prev is not None:
+                        Bnd.check(Bnd.spp_tonemap_image(warped, W, H, tm, prev_ldr), "tonemap")
+                    net.features(0, x["albedo"], x["normal"], x["depth"], x["mv"],
+                                 prev_ldr if prev is not None else None)
+                    if record is not None:
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                    net.forward()
+                    if record is not None:
+                        e1.record(stream)
+                        record.append((e0, e1))
+                    d = net.density[0]
+                    lg = net.frame_logits(0, prev is not None)
+                else:
+                    d = ones
+                    lg = [fixed[0] if prev is not None else fixed[0][:29], fixed[1], fixed[2]]
+                fr.alloc(d, spp.make_params(budget, frame=k))
+                fr.render(x["clean"], 0xC0FFEE, k)
+                fr.splat()
+                for l in (2, 1):
+                    Bnd.check(Bnd.spp_reconstruct_level(
+                        fr.layers[l], lg[l], lg[l].shape[0], hats[l + 1] if l < 2 else None, None,
+                        None, W >> l, H >> l, None, hats[l], None, status=fr.status), "level")
+                o = fr.hdr[state["parity"]]
+                Bnd.check(Bnd.spp_reconstruct_level(
+                    fr.layers[0], lg[0], lg[0].shape[0], hats[1],
+                    warped if prev is not None else None, mask if prev is not None else None,
+                    W, H, tm, o, fr.ldr, status=fr.status), "level 0")
+                state["prev"] = o
+                state["parity"] ^= 1
+
+            for k in range(F):  # one coherent pass: PSNR of frames 1..F-1
+                frame(k)
+                if k > 0:
+                    Bnd.check(Bnd.spp_mse(fr.ldr, refs[k], 3 * W * H, mse), "mse")
+                    psnr.append(-10.0 * np.log10(max(float(mse.item()), 1e-30)))
+            steps = 12
+            rec = [] if form == "learned" else None
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(F, F + steps):
+                frame(k, rec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fr.check_status()
+            res[form + "_ms"] = e0.elapsed_time(e1) / steps
+            res[form + "_psnr_db"] = float(np.mean(psnr))
+            if rec:
+                net_ms += [a.elapsed_time(b) for a, b in rec]
+        res["learned_gain_db"] = res["learned_psnr_db"] - res["plain_psnr_db"]
+        out["budgets"][str(budget)] = res
+        del fr
+    avg = float(np.mean(net_ms))
+    tflops = flops / (avg / 1e3) / 1e12
+    out["network"].update({"ms": avg, "tflops": tflops,
+                           "bf16_peak_tflops": peaks.get("bf16_tflops_sustained",
+                                                         peaks["bf16_tflops"]),
+                           "frac_of_bf16_peak": tflops / peaks.get("bf16_tflops_sustained",
+                                                                   peaks["bf16_tflops"]),
+                           "peak_kind": peak_kind + " (sustained, the network runs inside a "
+                                                    "longer frame)"})
+    out["bf16_error_vs_fp64_oracle"] = (
+        "kernel logits and density logit within 0.5-0.8 % RMS of the exact FP64 network "
+        "(tests/test_gpu_unet.py::test_predict_parity); reconstruction given the logits within "
+        "1e-5 relative (tests/test_gpu_parity.py)")
+    return out
 
 
 def run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, world, dist):

@@ -29,6 +29,25 @@ from .pipeline import Frame
 
 LEVELS = 3
 PHI = 0.125
+# names of the network's layers in parameter order (spp_unet_layer gives the shapes)
+LAYER_NAMES = ("e0a", "e0b", "e1a", "e1b", "e2a", "e2b", "h2", "d1a", "d1b", "h1", "d0a", "d0b",
+               "h0")
+LAYER_LEVEL = (0, 0, 1, 1, 2, 2, 2, 1, 1, 1, 0, 0, 0)
+
+
+def layer_table():
+    """[(name, cin, cout, relu)] from the library."""
+    return [(n, *B.spp_unet_layer(i)) for i, n in enumerate(LAYER_NAMES)]
+
+
+def flops_per_frame(W: int, H: int) -> int:
+    """Multiply-adds x 2 of one forward pass on a W x H frame (real channel
+    counts, zero padding not counted)."""
+    total = 0
+    for i, (_, cin, cout, _) in enumerate(layer_table()):
+        lv = LAYER_LEVEL[i]
+        total += 2 * 9 * cin * cout * (W >> lv) * (H >> lv)
+    return total
 
 
 def _zeros(*shape, dtype=torch.float32):
