@@ -78,5 +78,32 @@ __device__ __forceinline__ uint4 load_chunk(const ConvArgs &a, int b, int y, int
 }
 
 
+// Global address of the 8-channel chunk [ch, ch+8) of pixel (b, y, x) for
+// the sources that need no arithmetic (NHWC, upsample + concatenation), or
+// nullptr where the chunk is zero padding.
+__device__ __forceinline__ const __nv_bfloat16 *chunk_address(const ConvArgs &a, int b, int y,
+                                                              int x, int ch) {
+    if (y < 0 || y >= a.H || x < 0 || x >= a.W) return nullptr;
+    if (ch < a.c0) return a.src0 + ((static_cast<size_t>(b) * a.H + y) * a.W + x) * a.c0 + ch;
+    if (a.src_mode != kSrcConcatUp || ch - a.c0 >= a.c1) return nullptr;
+    return a.src1 + ((static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) * (a.W >> 1) + (x >> 1)) * a.c1 +
+           (ch - a.c0);
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros
+// (and reads nothing).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace conv
 }  // namespace spp

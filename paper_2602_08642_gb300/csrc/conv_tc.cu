@@ -31,11 +31,13 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "conv_src.cuh"
 #include "conv_tc.cuh"
 #include "spp_internal.cuh"
 #include "tc_common.cuh"
+#include "tma_host.cuh"
 
 namespace spp {
 namespace conv {
@@ -47,24 +49,36 @@ constexpr int kThreads = 288;
 constexpr int kHeader = 256;  // barriers, TMEM slot, abort flag
 constexpr int kSmemBudget = 220 * 1024;
 
-template <int N>
+constexpr int kResidentMax = 80 * 1024;  // weights kept in shared memory up to this size
+
+// RES: all weights of the layer stay resident in shared memory (loaded once
+// per CTA); otherwise each stage carries its chunk's weights.
+template <int N, bool RES>
 struct Cfg {
     static constexpr int TR = N <= 64 ? 4 : N <= 128 ? 2 : 1;  // rows per tile
     static constexpr int kA = 2 * (TR + 2) * kPitch * 16;       // halo bytes per stage
-    static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per stage
-    static constexpr int kStage = kA + kB;
-    static constexpr int kNS0 = (kSmemBudget - kHeader) / kStage;
-    static constexpr int kNS = kNS0 > 4 ? 4 : kNS0;
+    static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per K chunk
+    static constexpr int kStage = RES ? kA : kA + kB;
+    static constexpr int kWRegion = RES ? kResidentMax : 0;
+    static constexpr int kNS0 = (kSmemBudget - kHeader - kWRegion) / kStage;
+    static constexpr int kNS = kNS0 > 8 ? 8 : kNS0;
+    // a stage is published kLag stages after its copies were issued; kLag <=
+    // kNS - 2 lets the MMAs of one stage run while the next is published
+    static constexpr int kLag = kNS - 2;
     static constexpr int kCols = tc::pow2_cols(2 * TR * N);
-    static constexpr int kSmem = kHeader + kNS * kStage + 128;  // + alignment slack
+    // FP32 planar outputs leave through two 8 KB staging buffers ([16 ch][128 px])
+    // and TMA tensor stores (resident-weight variants; the heads are)
+    static constexpr int kEpiOff = (kHeader + kWRegion + kNS * kStage + 127) / 128 * 128;
+    static constexpr int kEpiBytes = RES ? 2 * 16 * kTileX * 4 : 0;
+    static constexpr int kSmem = kEpiOff + kEpiBytes + 128;  // + alignment slack
     static_assert(kNS >= 2, "stage does not fit twice");
     static_assert(2 * TR * N <= 512, "accumulators exceed TMEM");
 };
 
 struct Bars {
-    uint64_t full[4];   // producers' halo stores (128 arrivals)
-    uint64_t wfull[4];  // weight bulk copy (1 arrival + bytes)
-    uint64_t empty[4];  // MMA done with the stage (tcgen05.commit)
+    uint64_t full[8];   // producers' halo stores (128 arrivals)
+    uint64_t wfull[8];  // weight bulk copies (1 arrival + bytes); [0] only when resident
+    uint64_t empty[8];  // MMA done with the stage (tcgen05.commit)
     uint64_t accf[2];   // accumulator ready (tcgen05.commit)
     uint64_t acce[2];   // accumulator drained by the epilogue (128 arrivals)
     uint64_t drain;     // abort path: all issued MMAs complete
@@ -73,14 +87,37 @@ struct Bars {
 };
 static_assert(sizeof(Bars) <= kHeader, "header");
 
-template <int N>
-__global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) {
-    using C = Cfg<N>;
+__device__ __forceinline__ void named_bar_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// TMA tensor store of a [16][1][128] FP32 box from shared memory at (x, y, c, b).
+__device__ __forceinline__ void tma_store_planes(const CUtensorMap *map, const void *src, int x,
+                                                 int y, int c, int b) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(tc::smem_u32(src)), "r"(x), "r"(y), "r"(c), "r"(b)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// the stores committed before the last `pending` have finished reading shared memory
+template <int P>
+__device__ __forceinline__ void tma_store_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(P) : "memory");
+}
+__device__ __forceinline__ void tma_store_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <int N, bool RES>
+__global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
+                                                             const __grid_constant__ CUtensorMap omap) {
+    using C = Cfg<N, RES>;
     constexpr int TR = C::TR, NS = C::kNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     Bars &bars = *reinterpret_cast<Bars *>(base);
-    unsigned char *stages = base + kHeader;
+    unsigned char *wres = base + kHeader;              // resident weights (RES)
+    unsigned char *stages = base + kHeader + C::kWRegion;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int tiles_x = (a.W + kTileX - 1) / kTileX;
@@ -118,14 +155,31 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
         // ---------------------------------------------------------- producers
         const int ptid = tid - 128;
         constexpr int kTasks = 2 * (TR + 2) * kPitch;  // 16-byte chunks per stage
-        constexpr int kUnroll = 4;
         uint32_t it = 0;
         uint32_t issued = 0;  // weight copies issued (by ptid 0)
         bool ok = true;
+        // Sources that need no arithmetic go through cp.async (zero-fill for
+        // the padding); a stage is published NS-1 stages later, so that up to
+        // NS-1 stages of copies are in flight per thread.  The other modes
+        // (FP32 planar gradients of the heads, pooling on load) stage through
+        // registers and publish at once.
+        const bool async_src = a.src_mode == kSrcNHWC || a.src_mode == kSrcConcatUp;
+        constexpr uint32_t kLag = C::kLag;
+        uint32_t published = 0;
+        if (RES && ptid == 0) {
+            // the whole packed weight operand, once
+            tc::mbar_arrive_expect_tx(&bars.wfull[0], static_cast<uint32_t>(kchunks * C::kB));
+            for (int c = 0; c < kchunks; ++c)
+                tc::bulk_g2s(wres + c * C::kB,
+                             reinterpret_cast<const unsigned char *>(a.wpack) +
+                                 static_cast<size_t>(c) * C::kB,
+                             C::kB, &bars.wfull[0]);
+            issued = 1;
+        }
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             const int b = t / per_img, r = t - b * per_img;
             const int y0 = (r / tiles_x) * TR, x0 = (r % tiles_x) * kTileX;
-            for (int c = 0; c < kchunks; ++c, ++it) {
+            for (int c = 0; c < kchunks; ++c) {
                 const int s = static_cast<int>(it % NS);
                 const uint32_t ph = (it / NS) & 1u;
                 if (!tc::mbar_wait(&bars.empty[s], ph ^ 1u, abort_flag)) {
@@ -134,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
                     break;
                 }
                 unsigned char *As = stages + s * C::kStage;
-                if (ptid == 0) {
+                if (!RES && ptid == 0) {
                     tc::mbar_arrive_expect_tx(&bars.wfull[s], C::kB);
                     tc::bulk_g2s(As + C::kA,
                                  reinterpret_cast<const unsigned char *>(a.wpack) +
@@ -144,34 +198,67 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
                 }
                 // task j -> kgroup j / ((TR+2) * kPitch), row, pixel; the
                 // shared-memory offset of task j is 16 j
+                if (async_src) {
+                    const uint32_t sbase = tc::smem_u32(As);
+#pragma unroll 4
+                    for (int j = ptid; j < kTasks; j += 128) {
+                        const int px = j % kPitch, q = j / kPitch;
+                        const int row = q % (TR + 2), kg = q / (TR + 2);
+                        const __nv_bfloat16 *src = chunk_address(a, b, y0 - 1 + row, x0 - 1 + px,
+                                                                 c * 16 + kg * 8);
+                        cp_async16(sbase + 16 * j, src ? src : a.src0, src ? 16u : 0u);
+                    }
+                    cp_async_commit();
+                    ++it;
+                    if (it > kLag) {
+                        cp_async_wait<kLag>();
+                        tc::fence_proxy_async();
+                        tc::mbar_arrive(&bars.full[published % NS]);
+                        ++published;
+                    }
+                } else {
+                    constexpr int kUnroll = 4;
 #pragma unroll 1
-                for (int j0 = 0; j0 < kTasks; j0 += 128 * kUnroll) {
-                    uint4 v[kUnroll];
+                    for (int j0 = 0; j0 < kTasks; j0 += 128 * kUnroll) {
+                        uint4 v[kUnroll];
 #pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        const int j = j0 + u * 128 + ptid;
-                        v[u] = make_uint4(0, 0, 0, 0);
-                        if (j < kTasks) {
-                            const int px = j % kPitch, q = j / kPitch;
-                            const int row = q % (TR + 2), kg = q / (TR + 2);
-                            v[u] = load_chunk(a, b, y0 - 1 + row, x0 - 1 + px, c * 16 + kg * 8);
+                        for (int u = 0; u < kUnroll; ++u) {
+                            const int j = j0 + u * 128 + ptid;
+                            v[u] = make_uint4(0, 0, 0, 0);
+                            if (j < kTasks) {
+                                const int px = j % kPitch, q = j / kPitch;
+                                const int row = q % (TR + 2), kg = q / (TR + 2);
+                                v[u] = load_chunk(a, b, y0 - 1 + row, x0 - 1 + px,
+                                                  c * 16 + kg * 8);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kUnroll; ++u) {
+                            const int j = j0 + u * 128 + ptid;
+                            if (j < kTasks) *reinterpret_cast<uint4 *>(As + 16 * j) = v[u];
                         }
                     }
-#pragma unroll
-                    for (int u = 0; u < kUnroll; ++u) {
-                        const int j = j0 + u * 128 + ptid;
-                        if (j < kTasks) *reinterpret_cast<uint4 *>(As + 16 * j) = v[u];
-                    }
+                    tc::fence_proxy_async();
+                    tc::mbar_arrive(&bars.full[s]);
+                    ++it;
+                    ++published;
                 }
-                tc::fence_proxy_async();
-                tc::mbar_arrive(&bars.full[s]);
             }
         }
+        // publish the stages still in flight (also on the abort path, where the
+        // copies must land before the CTA exits)
+        cp_async_wait<0>();
+        tc::fence_proxy_async();
+        for (; published < it; ++published) tc::mbar_arrive(&bars.full[published % NS]);
         if (!ok && ptid == 0) {
             // wait (bounded, ignoring the abort flag) for the copies still in flight
-            const uint32_t first = issued > NS ? issued - NS : 0;
-            for (uint32_t k = first; k < issued; ++k)
-                (void)tc::mbar_wait(&bars.wfull[k % NS], (k / NS) & 1u, nullptr);
+            if (RES) {
+                if (issued) (void)tc::mbar_wait(&bars.wfull[0], 0, nullptr);
+            } else {
+                const uint32_t first = issued > NS ? issued - NS : 0;
+                for (uint32_t k = first; k < issued; ++k)
+                    (void)tc::mbar_wait(&bars.wfull[k % NS], (k / NS) & 1u, nullptr);
+            }
         }
     } else if (warp == 8) {
         // -------------------------------------------------------- MMA issuer
@@ -180,6 +267,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
             constexpr uint32_t kLboA = (TR + 2) * kPitch * 16, kLboB = N * 16;
             uint32_t it = 0, tl = 0;
             bool ok = true, pending = false;
+            if (RES && ntiles > static_cast<int>(blockIdx.x) &&
+                !tc::mbar_wait(&bars.wfull[0], 0, abort_flag)) {
+                fail();
+                ok = false;
+            }
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
                 const int acc = tl & 1;
                 if (!tc::mbar_wait(&bars.acce[acc], ((tl >> 1) & 1u) ^ 1u, abort_flag)) {
@@ -193,14 +285,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
                     const int s = static_cast<int>(it % NS);
                     const uint32_t ph = (it / NS) & 1u;
                     if (!tc::mbar_wait(&bars.full[s], ph, abort_flag) ||
-                        !tc::mbar_wait(&bars.wfull[s], ph, abort_flag)) {
+                        (!RES && !tc::mbar_wait(&bars.wfull[s], ph, abort_flag))) {
                         fail();
                         ok = false;
                         break;
                     }
                     tc::tc_fence_after();
                     const uint32_t a_base = tc::smem_u32(stages + s * C::kStage);
-                    const uint32_t b_base = a_base + C::kA;
+                    const uint32_t b_base =
+                        RES ? tc::smem_u32(wres + c * C::kB) : a_base + C::kA;
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap) {
                         const int dy = tap / 3, dx = tap % 3;
@@ -227,6 +320,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
     } else {
         // ----------------------------------------------------------- epilogue
         uint32_t tl = 0;
+        uint32_t eblk = 0;  // TMA-stored blocks (planar outputs)
         const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
             const int acc = tl & 1;
@@ -237,64 +331,168 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a) 
             tc::tc_fence_after();
             const int b = t / per_img, rr = t - b * per_img;
             const int y0 = (rr / tiles_x) * TR, x = (rr % tiles_x) * kTileX + warp * 32 + lane;
+            const uint32_t abase = tmem + lane_base + acc * TR * N;
+            // BF16 NHWC store of 16 channels [j, j+16) of one pixel
+            auto store16 = [&](__nv_bfloat16 *dst, const float *f) {
+                uint4 *o = reinterpret_cast<uint4 *>(dst);
+                o[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                  pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+                o[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
+                                  pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
+            };
+            if (TR % 2 == 0 && a.pool_out) {
+                // ReLU rows in pairs, plus the 2x2 average of their BF16 values
+                // (lanes x and x^1 hold horizontal neighbours); 32 columns of
+                // both rows per TMEM round trip
+                constexpr int kCB = N < 32 ? N : 32;
+#pragma unroll 1
+                for (int r = 0; r < TR; r += 2) {
+                    const int y = y0 + r;
+                    const bool in0 = (x < a.W) && (y < a.H), in1 = (x < a.W) && (y + 1 < a.H);
+                    const size_t pix0 = (static_cast<size_t>(b) * a.H + y) * a.W + x;
+                    const size_t pix1 = pix0 + a.W;
+#pragma unroll 1
+                    for (int j0 = 0; j0 < N; j0 += kCB) {
+                        uint32_t v0[kCB], v1[kCB];
+#pragma unroll
+                        for (int q = 0; q < kCB / 16; ++q) {
+                            tc::tmem_ld16(abase + r * N + j0 + 16 * q,
+                                          *reinterpret_cast<uint32_t(*)[16]>(v0 + 16 * q));
+                            tc::tmem_ld16(abase + (r + 1) * N + j0 + 16 * q,
+                                          *reinterpret_cast<uint32_t(*)[16]>(v1 + 16 * q));
+                        }
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int q = 0; q < kCB / 16; ++q) {
+                            const int j = j0 + 16 * q;
+                            float f0[16], f1[16], sum[16];
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const float bb = a.bias ? __ldg(a.bias + j + e) : 0.f;
+                                f0[e] = __bfloat162float(__float2bfloat16_rn(
+                                    fmaxf(__uint_as_float(v0[16 * q + e]) + bb, 0.f)));
+                                f1[e] = __bfloat162float(__float2bfloat16_rn(
+                                    fmaxf(__uint_as_float(v1[16 * q + e]) + bb, 0.f)));
+                                sum[e] = f0[e] + f1[e];
+                            }
+#pragma unroll
+                            for (int e = 0; e < 16; ++e)
+                                sum[e] += __shfl_xor_sync(0xffffffffu, sum[e], 1);
+                            if (in0) store16(a.out + pix0 * N + j, f0);
+                            if (in1) store16(a.out + pix1 * N + j, f1);
+                            if (in1 && !(lane & 1)) {
+                                const size_t pp = (static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) *
+                                                      (a.W >> 1) + (x >> 1);
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) sum[e] *= 0.25f;
+                                store16(a.pool_out + pp * N + j, sum);
+                            }
+                        }
+                    }
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(&bars.acce[acc]);
+                continue;
+            }
+            if (RES && a.epi_mode == kEpiF32Planar && a.tma_out) {
+                // stage 16 output planes of the row in shared memory, store them
+                // with one TMA tensor store (clipped at W and at cout)
+                float *ebuf = reinterpret_cast<float *>(base + C::kEpiOff);
+                const int px = warp * 32 + lane;
+                const int x0 = (rr % tiles_x) * kTileX;
+#pragma unroll 1
+                for (int r = 0; r < TR; ++r) {
+                    const int y = y0 + r;
+#pragma unroll 1
+                    for (int j0 = 0; j0 < N; j0 += 16) {
+                        uint32_t v[16];
+                        tc::tmem_ld16(abase + r * N + j0, v);
+                        tc::tmem_wait_ld();
+                        if (j0 >= a.cout) continue;  // padding columns
+                        float *buf = ebuf + (eblk & 1) * (16 * kTileX);
+                        if (tid == 0) tma_store_wait_read<1>();
+                        named_bar_epilogue();
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int n = j0 + e;
+                            buf[e * kTileX + px] =
+                                __uint_as_float(v[e]) + ((a.bias && n < a.cout) ? __ldg(a.bias + n) : 0.f);
+                        }
+                        tc::fence_proxy_async();
+                        named_bar_epilogue();
+                        if (tid == 0 && y < a.H) tma_store_planes(&omap, buf, x0, y, j0, b);
+                        ++eblk;
+                    }
+                }
+                tc::tc_fence_before();
+                tc::mbar_arrive(&bars.acce[acc]);
+                continue;
+            }
+            // one row at a time, up to 32 columns per TMEM round trip
+            constexpr int kCB = N < 32 ? N : 32;
 #pragma unroll 1
             for (int r = 0; r < TR; ++r) {
                 const int y = y0 + r;
                 const bool inside = (x < a.W) && (y < a.H);
                 const size_t pix = (static_cast<size_t>(b) * a.H + y) * a.W + x;
 #pragma unroll 1
-                for (int j0 = 0; j0 < N; j0 += 16) {
-                    uint32_t v[16];
-                    tc::tmem_ld16(tmem + lane_base + acc * TR * N + r * N + j0, v);
+                for (int j0 = 0; j0 < N; j0 += kCB) {
+                    uint32_t v[kCB];
+#pragma unroll
+                    for (int q = 0; q < kCB / 16; ++q)
+                        tc::tmem_ld16(abase + r * N + j0 + 16 * q,
+                                      *reinterpret_cast<uint32_t(*)[16]>(v + 16 * q));
                     tc::tmem_wait_ld();
                     if (!inside) continue;
-                    float f[16];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[e]);
-                    if (a.epi_mode == kEpiF32Planar) {
-                        const size_t plane = static_cast<size_t>(a.H) * a.W;
-                        float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
-                                   static_cast<size_t>(y) * a.W + x;
+                    for (int q = 0; q < kCB / 16; ++q) {
+                        const int j = j0 + 16 * q;
+                        float f[16];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int n = j0 + e;
-                            if (n < a.cout) o[n * plane] = f[e] + (a.bias ? __ldg(a.bias + n) : 0.f);
+                        for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[16 * q + e]);
+                        if (a.epi_mode == kEpiF32Planar) {
+                            const size_t plane = static_cast<size_t>(a.H) * a.W;
+                            float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
+                                       static_cast<size_t>(y) * a.W + x;
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int n = j + e;
+                                if (n < a.cout)
+                                    __stcs(o + n * plane, f[e] + (a.bias ? __ldg(a.bias + n) : 0.f));
+                            }
+                            continue;
                         }
-                        continue;
-                    }
-                    if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
-                        if (a.bias) {
+                        if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
+                            if (a.bias) {
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) f[e] += __ldg(a.bias + j0 + e);
-                        }
-                        if (a.epi_mode == kEpiReluBF16) {
+                                for (int e = 0; e < 16; ++e) f[e] += __ldg(a.bias + j + e);
+                            }
+                            if (a.epi_mode == kEpiReluBF16) {
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
-                        }
-                    } else if (a.epi_mode == kEpiMaskBF16) {
-                        const uint4 *m = reinterpret_cast<const uint4 *>(a.act + pix * N + j0);
+                                for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
+                            }
+                        } else if (a.epi_mode == kEpiMaskBF16) {
+                            const uint4 *m = reinterpret_cast<const uint4 *>(a.act + pix * N + j);
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const uint4 q = __ldg(m + h);
-                            const uint32_t *u = &q.x;
+                            for (int h = 0; h < 2; ++h) {
+                                const uint4 qq = __ldg(m + h);
+                                const uint32_t *u = &qq.x;
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float2 mv = unpack_bf16x2(u[k]);
-                                f[8 * h + 2 * k] = mv.x > 0.f ? f[8 * h + 2 * k] : 0.f;
-                                f[8 * h + 2 * k + 1] = mv.y > 0.f ? f[8 * h + 2 * k + 1] : 0.f;
+                                for (int k = 0; k < 4; ++k) {
+                                    const float2 mv = unpack_bf16x2(u[k]);
+                                    f[8 * h + 2 * k] = mv.x > 0.f ? f[8 * h + 2 * k] : 0.f;
+                                    f[8 * h + 2 * k + 1] = mv.y > 0.f ? f[8 * h + 2 * k + 1] : 0.f;
+                                }
                             }
                         }
+                        store16(a.out + pix * N + j, f);
                     }
-                    uint4 *o = reinterpret_cast<uint4 *>(a.out + pix * N + j0);
-                    o[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
-                                      pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
-                    o[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
-                                      pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
                 }
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&bars.acce[acc]);
         }
+        if (tid == 0 && eblk) tma_store_wait_all();
     }
 
     tc::tc_fence_before();
@@ -328,14 +526,15 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, int cin, int co
     }
 }
 
-template <int N>
-int launch(const ConvArgs &a, cudaStream_t stream) {
-    using C = Cfg<N>;
+template <int N, bool RES>
+int launch_variant(const ConvArgs &a, cudaStream_t stream) {
+    using C = Cfg<N, RES>;
     static int configured_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured_dev != dev) {
-        if (cudaFuncSetAttribute(conv3x3_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(conv3x3_kernel<N, RES>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  C::kSmem) != cudaSuccess)
             return SPP_ERR_CUDA;
         configured_dev = dev;
@@ -344,9 +543,36 @@ int launch(const ConvArgs &a, cudaStream_t stream) {
                            ((a.W + kTileX - 1) / kTileX);
     if (ntiles == 0) return SPP_OK;
     const int grid = static_cast<int>(std::min<int64_t>(ntiles, sm_count()));
-    conv3x3_kernel<N><<<grid, kThreads, C::kSmem, stream>>>(a);
+    CUtensorMap omap;
+    memset(&omap, 0, sizeof(omap));
+    ConvArgs b = a;
+    b.tma_out = 0;
+    if (RES && a.epi_mode == kEpiF32Planar && a.W % 4 == 0) {
+        // [B][cout][H][W] FP32 as a 4-D tensor (x, y, plane, image), box 128 x 1 x 16 x 1
+        auto enc = tensor_map_encoder();
+        cuuint64_t dims[4] = {static_cast<cuuint64_t>(a.W), static_cast<cuuint64_t>(a.H),
+                              static_cast<cuuint64_t>(a.cout), static_cast<cuuint64_t>(a.B)};
+        cuuint64_t strides[3] = {static_cast<cuuint64_t>(a.W) * 4ull,
+                                 static_cast<cuuint64_t>(a.W) * a.H * 4ull,
+                                 static_cast<cuuint64_t>(a.W) * a.H * a.cout * 4ull};
+        cuuint32_t box[4] = {static_cast<cuuint32_t>(kTileX), 1, 16, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (enc && enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.outf, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                       CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            b.tma_out = 1;
+    }
+    conv3x3_kernel<N, RES><<<grid, kThreads, C::kSmem, stream>>>(b, omap);
     count_launch();
     return launch_status();
+}
+
+template <int N>
+int launch(const ConvArgs &a, cudaStream_t stream) {
+    const int64_t wbytes = static_cast<int64_t>(a.cin_pad / 16) * Cfg<N, false>::kB;
+    if (wbytes <= kResidentMax) return launch_variant<N, true>(a, stream);
+    return launch_variant<N, false>(a, stream);
 }
 
 }  // namespace

@@ -44,6 +44,10 @@ struct ConvArgs {
     __nv_bfloat16 *out = nullptr;          // NHWC, channel stride n
     const __nv_bfloat16 *act = nullptr;    // kEpiMaskBF16: NHWC, channel stride n
     float *outf = nullptr;                 // [B][cout][H][W]
+    // kEpiReluBF16 only: also write the 2x2 average of the stored BF16 values
+    // to pool_out [B][H/2][W/2][n] (H and W even)
+    __nv_bfloat16 *pool_out = nullptr;
+    int tma_out = 0;  // set by the launcher: FP32 planar output through TMA stores
     int32_t *status = nullptr;
 };
 

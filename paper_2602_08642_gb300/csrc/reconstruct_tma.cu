@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "recon_common.cuh"
+#include "tma_host.cuh"
 
 namespace spp {
 namespace {
@@ -439,25 +440,10 @@ warp_prev_kernel(const float *__restrict__ prev, const float *__restrict__ mv, i
 }
 
 // ------------------------------------------------------------ host side
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static std::mutex mu;
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
 // 3-D FP32 map over planar [planes][H][W] with a box (bx, by, bz).
 bool make_map(CUtensorMap *map, const float *base, int W, int H, int planes, int bx, int by,
               int bz) {
-    auto fn = encode_fn();
+    auto fn = tensor_map_encoder();
     if (!fn) return false;
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(W), static_cast<cuuint64_t>(H),
                           static_cast<cuuint64_t>(planes)};

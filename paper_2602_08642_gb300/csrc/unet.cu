@@ -62,10 +62,13 @@ ActLayout act_layout(int B, int W, int H) {
         off = align256(off + elems * sizeof(__nv_bfloat16));
         return o;
     };
+    A.x16 = take(p0 * 16);
     A.e0a = take(p0 * 32);
     A.s0 = take(p0 * 32);
+    A.p0 = take(p1 * 32);
     A.e1a = take(p1 * 64);
     A.s1 = take(p1 * 64);
+    A.p1 = take(p2 * 64);
     A.e2a = take(p2 * 128);
     A.bt = take(p2 * 128);
     A.d1a = take(p1 * 64);
@@ -98,6 +101,28 @@ __global__ void assemble_kernel(const float *__restrict__ albedo, const float *_
         out[9 * n + i] = prev ? prev[i] : 0.f;
         out[10 * n + i] = prev ? prev[n + i] : 0.f;
         out[11 * n + i] = prev ? prev[2 * n + i] : 0.f;
+    }
+}
+
+// in12 [B][12][H][W] FP32 -> BF16 [B][H][W][16] (round to nearest even,
+// channels 12..15 zero): the layout the first convolution streams.
+__global__ void features_nhwc16_kernel(const float *__restrict__ in12, int64_t n, int64_t hw,
+                                       __nv_bfloat16 *__restrict__ out) {
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t b = p / hw, i = p - b * hw;
+        const float *src = in12 + b * 12 * hw + i;
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(__ldg(src + (2 * k) * hw),
+                                                     __ldg(src + (2 * k + 1) * hw));
+            w[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        w[6] = w[7] = 0;
+        uint4 *o = reinterpret_cast<uint4 *>(out + p * 16);
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
     }
 }
 
@@ -149,7 +174,7 @@ __global__ void density_kernel(const float *__restrict__ logits0, int64_t hw,
 
 }  // namespace
 
-conv::ConvArgs layer_input(int i, int B, int W, int H, const float *in12,
+conv::ConvArgs layer_input(int i, int B, int W, int H, const float * /*in12*/,
                            const unsigned char *ws) {
     const ActLayout A = act_layout(B, W, H);
     auto act = [&](size_t off) { return reinterpret_cast<const __nv_bfloat16 *>(ws + off); };
@@ -163,11 +188,11 @@ conv::ConvArgs layer_input(int i, int B, int W, int H, const float *in12,
     a.cin_pad = round16(kLayers[i].cin);
     a.src_mode = conv::kSrcNHWC;
     switch (i) {
-        case E0A: a.src_mode = conv::kSrcPlanarF32; a.srcf = in12; a.cf = 12; break;
+        case E0A: a.src0 = act(A.x16); a.c0 = 16; break;
         case E0B: a.src0 = act(A.e0a); a.c0 = 32; break;
-        case E1A: a.src_mode = conv::kSrcPool; a.src0 = act(A.s0); a.c0 = 32; break;
+        case E1A: a.src0 = act(A.p0); a.c0 = 32; break;
         case E1B: a.src0 = act(A.e1a); a.c0 = 64; break;
-        case E2A: a.src_mode = conv::kSrcPool; a.src0 = act(A.s1); a.c0 = 64; break;
+        case E2A: a.src0 = act(A.p1); a.c0 = 64; break;
         case E2B: a.src0 = act(A.e2a); a.c0 = 128; break;
         case H2: a.src0 = act(A.bt); a.c0 = 128; break;
         case D1A:
@@ -201,6 +226,14 @@ int forward(const unsigned char *packed, const float *in12, int B, int W, int H,
     heads[H0] = logits0;
     heads[H1] = logits1;
     heads[H2] = logits2;
+    {
+        const int64_t n = static_cast<int64_t>(B) * W * H;
+        const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 8 * sm_count()));
+        features_nhwc16_kernel<<<grid, 256, 0, stream>>>(
+            in12, n, static_cast<int64_t>(W) * H, reinterpret_cast<__nv_bfloat16 *>(ws + A.x16));
+        count_launch();
+        if (launch_status() != SPP_OK) return SPP_ERR_CUDA;
+    }
     static const int order[kNumLayers] = {E0A, E0B, E1A, E1B, E2A, E2B, H2,
                                           D1A, D1B, H1,  D0A, D0B, H0};
     for (int k = 0; k < kNumLayers; ++k) {
@@ -214,6 +247,8 @@ int forward(const unsigned char *packed, const float *in12, int B, int W, int H,
         if (kLayers[i].relu) {
             a.epi_mode = conv::kEpiReluBF16;
             a.out = reinterpret_cast<__nv_bfloat16 *>(ws + layer_output(i, A));
+            if (i == E0B) a.pool_out = reinterpret_cast<__nv_bfloat16 *>(ws + A.p0);
+            if (i == E1B) a.pool_out = reinterpret_cast<__nv_bfloat16 *>(ws + A.p1);
         } else {
             a.epi_mode = conv::kEpiF32Planar;
             a.outf = heads[i];

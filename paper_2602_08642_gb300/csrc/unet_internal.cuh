@@ -39,7 +39,8 @@ PackedLayout packed_layout(int with_backward);
 
 // Byte offsets of the BF16 NHWC activations inside the forward workspace.
 struct ActLayout {
-    size_t e0a, s0, e1a, s1, e2a, bt, d1a, t1, d0a, t0;
+    size_t x16;  // the input features, BF16 [B][H][W][16] (channels 12..15 zero)
+    size_t e0a, s0, p0, e1a, s1, p1, e2a, bt, d1a, t1, d0a, t0;  // p0, p1: 2x2 pools of s0, s1
     size_t zmax;
     size_t total;
 };

@@ -1,7 +1,10 @@
 // Status codes, launch counter and small utilities of the C ABI.
 #include <mutex>
 
+#include <mutex>
+
 #include "spp_internal.cuh"
+#include "tma_host.cuh"
 
 namespace spp {
 
@@ -19,6 +22,21 @@ int sm_count() {
         n = 152;
     if (dev < 64) cache[dev] = n;
     return n;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
 }
 
 }  // namespace spp

@@ -163,7 +163,8 @@ def _act_views(ws, B, W, H):
     forward keeps in its workspace, in the library's order (each region
     256-byte aligned)."""
     p0 = B * H * W
-    sizes = [("e0a", p0, 32), ("s0", p0, 32), ("e1a", p0 // 4, 64), ("s1", p0 // 4, 64),
+    sizes = [("x16", p0, 16), ("e0a", p0, 32), ("s0", p0, 32), ("p0", p0 // 4, 32),
+             ("e1a", p0 // 4, 64), ("s1", p0 // 4, 64), ("p1", p0 // 16, 64),
              ("e2a", p0 // 16, 128), ("bt", p0 // 16, 128), ("d1a", p0 // 4, 64),
              ("t1", p0 // 4, 64), ("d0a", p0, 32), ("t0", p0, 32)]
     out, off = {}, 0
@@ -208,7 +209,8 @@ def test_predict_layerwise_parity(spp):
     x = _features(B, W, H, seed=30)
     (d, l0, l1, l2), ws = _predict(spp, theta, x, B, W, H, return_ws=True)
     sp = _act_views(ws, B, W, H)
-    dims = {"e0a": (H, W), "s0": (H, W), "e1a": (H // 2, W // 2), "s1": (H // 2, W // 2),
+    dims = {"x16": (H, W), "p0": (H // 2, W // 2), "p1": (H // 4, W // 4),
+            "e0a": (H, W), "s0": (H, W), "e1a": (H // 2, W // 2), "s1": (H // 2, W // 2),
             "e2a": (H // 4, W // 4), "bt": (H // 4, W // 4), "d1a": (H // 2, W // 2),
             "t1": (H // 2, W // 2), "d0a": (H, W), "t0": (H, W)}
     A = {k: _read_act(ws, sp[k], B, *dims[k]) for k in sp}
@@ -221,6 +223,11 @@ def test_predict_layerwise_parity(spp):
     def up(a):
         return np.stack([U.up2(a[b]) for b in range(B)])
 
+    # the stored input features and pooled skips are exactly the oracle's
+    # BF16 roundings of the GPU's own tensors
+    assert np.array_equal(A["x16"][:, :12], xb) and np.all(A["x16"][:, 12:] == 0)
+    assert np.array_equal(A["p0"], pool(A["s0"]))
+    assert np.array_equal(A["p1"], pool(A["s1"]))
     inputs = {
         "e0a": xb, "e0b": A["e0a"], "e1a": pool(A["s0"]), "e1b": A["e1a"], "e2a": pool(A["s1"]),
         "e2b": A["e2a"], "h2": A["bt"], "d1a": np.concatenate([A["s1"], up(A["bt"])], axis=1),
