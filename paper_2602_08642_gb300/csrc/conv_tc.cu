@@ -47,7 +47,8 @@ constexpr int kTileX = 128;  // output pixels per row tile (MMA M)
 constexpr int kPitch = 130;  // staged halo pixels per row
 constexpr int kThreads = 288;
 constexpr int kHeader = 256;  // barriers, TMEM slot, abort flag
-constexpr int kSmemBudget = 220 * 1024;
+constexpr int kSmemLimit = 227 * 1024;             // dynamic shared memory per CTA
+constexpr int kSmemBudget = kSmemLimit - 512;      // minus alignment slack
 
 constexpr int kResidentMax = 80 * 1024;  // weights kept in shared memory up to this size
 
@@ -56,11 +57,16 @@ constexpr int kResidentMax = 80 * 1024;  // weights kept in shared memory up to 
 template <int N, bool RES>
 struct Cfg {
     static constexpr int TR = N <= 64 ? 4 : N <= 128 ? 2 : 1;  // rows per tile
-    static constexpr int kA = 2 * (TR + 2) * kPitch * 16;       // halo bytes per stage
+    // bytes between the two 8-channel groups of a stage (the A operand's LBO):
+    // at least one group, and 64 mod 128 so that the two 16-byte halves of a
+    // pixel's 32 bytes, written by neighbouring threads, hit different banks
+    static constexpr int kKg = ((TR + 2) * kPitch * 16 - 64 + 127) / 128 * 128 + 64;
+    static constexpr int kA = 2 * kKg;                          // halo bytes per stage
     static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per K chunk
     static constexpr int kStage = RES ? kA : kA + kB;
     static constexpr int kWRegion = RES ? kResidentMax : 0;
-    static constexpr int kNS0 = (kSmemBudget - kHeader - kWRegion) / kStage;
+    static constexpr int kEpiBytes = RES ? 2 * 16 * kTileX * 4 : 0;
+    static constexpr int kNS0 = (kSmemBudget - kHeader - kWRegion - kEpiBytes) / kStage;
     static constexpr int kNS = kNS0 > 8 ? 8 : kNS0;
     // a stage is published kLag stages after its copies were issued; kLag <=
     // kNS - 2 lets the MMAs of one stage run while the next is published
@@ -69,8 +75,8 @@ struct Cfg {
     // FP32 planar outputs leave through two 8 KB staging buffers ([16 ch][128 px])
     // and TMA tensor stores (resident-weight variants; the heads are)
     static constexpr int kEpiOff = (kHeader + kWRegion + kNS * kStage + 127) / 128 * 128;
-    static constexpr int kEpiBytes = RES ? 2 * 16 * kTileX * 4 : 0;
     static constexpr int kSmem = kEpiOff + kEpiBytes + 128;  // + alignment slack
+    static_assert(kSmem <= kSmemLimit, "shared memory over the per-CTA limit");
     static_assert(kNS >= 2, "stage does not fit twice");
     static_assert(2 * TR * N <= 512, "accumulators exceed TMEM");
 };
@@ -155,6 +161,15 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         // ---------------------------------------------------------- producers
         const int ptid = tid - 128;
         constexpr int kTasks = 2 * (TR + 2) * kPitch;  // 16-byte chunks per stage
+        constexpr int kPer = (kTasks + 127) / 128;
+        // this thread's tasks (the same in every stage): row << 10 | px << 1 | kg
+        int tinfo[kPer];
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int j = u * 128 + ptid;
+            tinfo[u] = j < kTasks ? (((j >> 1) / kPitch) << 10) | (((j >> 1) % kPitch) << 1) | (j & 1)
+                                  : -1;
+        }
         uint32_t it = 0;
         uint32_t issued = 0;  // weight copies issued (by ptid 0)
         bool ok = true;
@@ -196,17 +211,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                                  C::kB, &bars.wfull[s]);
                     ++issued;
                 }
-                // task j -> kgroup j / ((TR+2) * kPitch), row, pixel; the
-                // shared-memory offset of task j is 16 j
+                // task j -> 8-channel group j & 1 (fastest), then pixel, then row;
+                // shared-memory offset kg * kKg + (row * kPitch + px) * 16
                 if (async_src) {
                     const uint32_t sbase = tc::smem_u32(As);
-#pragma unroll 4
-                    for (int j = ptid; j < kTasks; j += 128) {
-                        const int px = j % kPitch, q = j / kPitch;
-                        const int row = q % (TR + 2), kg = q / (TR + 2);
+#pragma unroll
+                    for (int u = 0; u < kPer; ++u) {
+                        if (tinfo[u] < 0) continue;
+                        const int row = tinfo[u] >> 10, px = (tinfo[u] >> 1) & 511, kg = tinfo[u] & 1;
                         const __nv_bfloat16 *src = chunk_address(a, b, y0 - 1 + row, x0 - 1 + px,
                                                                  c * 16 + kg * 8);
-                        cp_async16(sbase + 16 * j, src ? src : a.src0, src ? 16u : 0u);
+                        cp_async16(sbase + kg * C::kKg + (row * kPitch + px) * 16,
+                                   src ? src : a.src0, src ? 16u : 0u);
                     }
                     cp_async_commit();
                     ++it;
@@ -226,8 +242,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             const int j = j0 + u * 128 + ptid;
                             v[u] = make_uint4(0, 0, 0, 0);
                             if (j < kTasks) {
-                                const int px = j % kPitch, q = j / kPitch;
-                                const int row = q % (TR + 2), kg = q / (TR + 2);
+                                const int kg = j & 1, px = (j >> 1) % kPitch, row = (j >> 1) / kPitch;
                                 v[u] = load_chunk(a, b, y0 - 1 + row, x0 - 1 + px,
                                                   c * 16 + kg * 8);
                             }
@@ -235,7 +250,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
 #pragma unroll
                         for (int u = 0; u < kUnroll; ++u) {
                             const int j = j0 + u * 128 + ptid;
-                            if (j < kTasks) *reinterpret_cast<uint4 *>(As + 16 * j) = v[u];
+                            if (j < kTasks) {
+                                const int kg = j & 1, px = (j >> 1) % kPitch, row = (j >> 1) / kPitch;
+                                *reinterpret_cast<uint4 *>(As + kg * C::kKg +
+                                                           (row * kPitch + px) * 16) = v[u];
+                            }
                         }
                     }
                     tc::fence_proxy_async();
@@ -264,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         // -------------------------------------------------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(128, N);
-            constexpr uint32_t kLboA = (TR + 2) * kPitch * 16, kLboB = N * 16;
+            constexpr uint32_t kLboA = C::kKg, kLboB = N * 16;
             uint32_t it = 0, tl = 0;
             bool ok = true, pending = false;
             if (RES && ntiles > static_cast<int>(blockIdx.x) &&
