@@ -432,7 +432,7 @@ density_grad_kernel(const float *__restrict__ d, const float *__restrict__ g, lo
 }
 
 ToneArgs tone_args_bwd(const spp_tonemap *tm) {
-    ToneArgs t{1.0f, 1.0f, 0.0f, 0.5f, 0.5f};
+    ToneArgs t{1.0f, 1.0f, 0.0f, 0.5f, 0.5f, 2.0f, 2.0f};
     if (tm) {
         t.alpha = tm->alpha;
         t.beta = tm->beta;
@@ -440,6 +440,8 @@ ToneArgs tone_args_bwd(const spp_tonemap *tm) {
         t.s = tm->shadow;
         t.h = tm->highlight;
     }
+    t.inv_s = 1.0f / t.s;
+    t.inv_h = 1.0f / t.h;
     return t;
 }
 

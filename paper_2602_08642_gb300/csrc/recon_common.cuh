@@ -7,6 +7,7 @@ namespace spp {
 
 struct ToneArgs {
     float alpha, beta, k, s, h;
+    float inv_s, inv_h;  // 1/s and 1/h, computed once on the host
 };
 
 constexpr float kLog2e = 1.4426950408889634f;
@@ -21,13 +22,23 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// 1/x on the SFU (about 1 ulp), for the softmax normalisation.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // tau of Sec. 5: exponential toe below s-1, linear middle, exponential
 // shoulder above 1-h.
 // Branch-free: one exponential serves whichever tail the argument is in.
-__device__ __forceinline__ float tau_curve(float x, float s, float h) {
+// The tails divide by s and by h, uniform over the frame: multiplying by the
+// host-computed reciprocals costs one rounding more than a division
+// (relative 2^-24), far inside the output tolerance.
+__device__ __forceinline__ float tau_curve(float x, float s, float h, float inv_s, float inv_h) {
     const bool toe = x < s - 1.0f;
     const bool mid = !toe && x < 1.0f - h;
-    const float arg = toe ? __fdiv_rn(x + 1.0f - s, s) : __fdiv_rn(-(x + h - 1.0f), h);
+    const float arg = toe ? (x + 1.0f - s) * inv_s : -(x + h - 1.0f) * inv_h;
     const float ex = __expf(fminf(arg, 0.0f));
     const float tail = toe ? 0.5f * s * ex : 1.0f - 0.5f * h * ex;
     return mid ? 0.5f * (1.0f + x) : tail;
@@ -46,9 +57,12 @@ __device__ __forceinline__ void tone_map(float o0, float o1, float o2, const Ton
     const float l1 = __logf(fmaxf(o1, 0x1p-24f));
     const float l2 = __logf(fmaxf(o2, 0x1p-24f));
     const float mean = (l0 + l1 + l2) * (1.0f / 3.0f);
-    r = srgb(tau_curve(tm.alpha * (mean + tm.beta * (l0 - mean) + tm.k), tm.s, tm.h));
-    g = srgb(tau_curve(tm.alpha * (mean + tm.beta * (l1 - mean) + tm.k), tm.s, tm.h));
-    b = srgb(tau_curve(tm.alpha * (mean + tm.beta * (l2 - mean) + tm.k), tm.s, tm.h));
+    r = srgb(tau_curve(tm.alpha * (mean + tm.beta * (l0 - mean) + tm.k), tm.s, tm.h, tm.inv_s,
+                       tm.inv_h));
+    g = srgb(tau_curve(tm.alpha * (mean + tm.beta * (l1 - mean) + tm.k), tm.s, tm.h, tm.inv_s,
+                       tm.inv_h));
+    b = srgb(tau_curve(tm.alpha * (mean + tm.beta * (l2 - mean) + tm.k), tm.s, tm.h, tm.inv_s,
+                       tm.inv_h));
 }
 
 // Launches the TMA-pipelined reconstruction of one level when the level's

@@ -131,7 +131,7 @@ recon_kernel(const float *__restrict__ noisy, const float *__restrict__ logits,
                 a2 = fmaf(e, sW[2][ty + j][tx + i], a2);
             }
     }
-    const float inv = __frcp_rn(wsum);
+    const float inv = rcp_approx(wsum);
     const float o0 = a0 * inv, o1 = a1 * inv, o2 = a2 * inv;
     if (!inside) return;
     const long long op = static_cast<long long>(y) * Wl + x;
@@ -175,7 +175,7 @@ __global__ void tonemap_image_kernel(const float *__restrict__ hdr, int64_t n,
 }
 
 ToneArgs tone_args(const spp_tonemap *tm) {
-    ToneArgs t{1.0f, 1.0f, 0.0f, 0.5f, 0.5f};
+    ToneArgs t{1.0f, 1.0f, 0.0f, 0.5f, 0.5f, 2.0f, 2.0f};
     if (tm) {
         t.alpha = tm->alpha;
         t.beta = tm->beta;
@@ -183,6 +183,8 @@ ToneArgs tone_args(const spp_tonemap *tm) {
         t.s = tm->shadow;
         t.h = tm->highlight;
     }
+    t.inv_s = 1.0f / t.s;
+    t.inv_h = 1.0f / t.h;
     return t;
 }
 

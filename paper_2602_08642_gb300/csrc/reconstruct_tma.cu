@@ -384,7 +384,7 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
             const float m1 = pk[p], w1 = pk[kPixels + p];
             const float M = fmaxf(m, m1);
             const float s0 = ex2_approx((m - M) * kLog2e), s1 = ex2_approx((m1 - M) * kLog2e);
-            const float inv = __frcp_rn(wsum * s0 + w1 * s1);
+            const float inv = rcp_approx(wsum * s0 + w1 * s1);
             const float o0 = (a0 * s0 + pk[2 * kPixels + p] * s1) * inv;
             const float o1 = (a1 * s0 + pk[3 * kPixels + p] * s1) * inv;
             const float o2 = (a2 * s0 + pk[4 * kPixels + p] * s1) * inv;
