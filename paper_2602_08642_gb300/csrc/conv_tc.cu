@@ -66,19 +66,32 @@ struct Cfg {
     static constexpr int kStage = RES ? kA : kA + kB;
     static constexpr int kWRegion = RES ? kResidentMax : 0;
     static constexpr int kEpiBytes = RES ? 2 * 16 * kTileX * 4 : 0;
-    static constexpr int kNS0 = (kSmemBudget - kHeader - kWRegion - kEpiBytes) / kStage;
+    static constexpr int kBiasOff = kHeader;                     // FP32 bias [N]
+    static constexpr int kZeroOff = kBiasOff + 1024;             // zero operand (stacked)
+    static constexpr int kZeroBytes = (N == 32) ? 4096 : 0;
+    static constexpr int kWOff = kZeroOff + kZeroBytes;          // resident weights
+    static constexpr int kStagesOff = kWOff + kWRegion;
+    static constexpr int kNS0 = (kSmemBudget - kStagesOff - kEpiBytes) / kStage;
     static constexpr int kNS = kNS0 > 8 ? 8 : kNS0;
     // a stage is published kLag stages after its copies were issued; kLag <=
     // kNS - 2 lets the MMAs of one stage run while the next is published
     static constexpr int kLag = kNS - 2;
-    static constexpr int kCols = tc::pow2_cols(2 * TR * N);
+    // N = 32: the three dy taps of a halo row are one MMA of N = 96 whose
+    // output spans three neighbouring output rows; each accumulator then holds
+    // TR + 4 row slots (two spare slots at each end); one 0 x 0 MMA with
+    // accumulate off resets the TR real slots at the start of a tile, after
+    // which every MMA accumulates (the spare slots are never read)
+    static constexpr bool kStack = (N == 32);
+    static constexpr int kRowOff = kStack ? 2 : 0;
+    static constexpr int kAccCols = (kStack ? TR + 4 : TR) * N;
+    static constexpr int kCols = tc::pow2_cols(2 * kAccCols);
+    static_assert(2 * kAccCols <= 512, "accumulators exceed TMEM");
     // FP32 planar outputs leave through two 8 KB staging buffers ([16 ch][128 px])
     // and TMA tensor stores (resident-weight variants; the heads are)
-    static constexpr int kEpiOff = (kHeader + kWRegion + kNS * kStage + 127) / 128 * 128;
+    static constexpr int kEpiOff = (kStagesOff + kNS * kStage + 127) / 128 * 128;
     static constexpr int kSmem = kEpiOff + kEpiBytes + 128;  // + alignment slack
     static_assert(kSmem <= kSmemLimit, "shared memory over the per-CTA limit");
     static_assert(kNS >= 2, "stage does not fit twice");
-    static_assert(2 * TR * N <= 512, "accumulators exceed TMEM");
 };
 
 struct Bars {
@@ -122,8 +135,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     Bars &bars = *reinterpret_cast<Bars *>(base);
-    unsigned char *wres = base + kHeader;              // resident weights (RES)
-    unsigned char *stages = base + kHeader + C::kWRegion;
+    unsigned char *wres = base + C::kWOff;              // resident weights (RES)
+    unsigned char *stages = base + C::kStagesOff;
+    float *sbias = reinterpret_cast<float *>(base + C::kBiasOff);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const int tiles_x = (a.W + kTileX - 1) / kTileX;
@@ -145,6 +159,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         tc::mbar_init(&bars.drain, 1);
         bars.abort = 0;
         tc::fence_mbar_init();
+    }
+    for (int i = tid; i < N; i += kThreads) sbias[i] = (a.bias && i < a.cout) ? a.bias[i] : 0.f;
+    if (C::kStack) {
+        // the zero operand that resets an accumulator (0 x 0 with accumulate off)
+        for (int i = tid; i < C::kZeroBytes / 16; i += kThreads)
+            reinterpret_cast<uint4 *>(base + C::kZeroOff)[i] = make_uint4(0, 0, 0, 0);
+        tc::fence_proxy_async();
     }
     if (warp == 8) tc::tmem_alloc(&bars.tmem_base, C::kCols);
     tc::tc_fence_before();
@@ -299,7 +320,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     break;
                 }
                 tc::tc_fence_after();
-                const uint32_t d0 = tmem + acc * TR * N;
+                const uint32_t d0 = tmem + acc * C::kAccCols;
+                if (C::kStack) {
+                    // reset the TR real row slots (the spare slots are never read)
+                    const uint64_t zd =
+                        tc::smem_desc(tc::smem_u32(base + C::kZeroOff), 2048, 128);
+                    tc::mma_bf16(d0 + C::kRowOff * N, zd, zd, tc::idesc_bf16_f32(128, TR * N), 0u);
+                }
                 for (int c = 0; c < kchunks; ++c, ++it) {
                     const int s = static_cast<int>(it % NS);
                     const uint32_t ph = (it / NS) & 1u;
@@ -313,15 +340,33 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     const uint32_t a_base = tc::smem_u32(stages + s * C::kStage);
                     const uint32_t b_base =
                         RES ? tc::smem_u32(wres + c * C::kB) : a_base + C::kA;
+                    if (C::kStack) {
+                        // halo row h feeds output rows h-2, h-1, h through the
+                        // stacked weights [dy = 2; dy = 1; dy = 0] of its dx tap
+                        constexpr uint32_t idesc3 = tc::idesc_bf16_f32(128, 3 * N);
 #pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;
-                        const uint64_t bd = tc::smem_desc(b_base + tap * 2 * N * 16, kLboB, 128);
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint64_t bd =
+                                tc::smem_desc(b_base + dx * 2 * 3 * N * 16, 3 * N * 16, 128);
 #pragma unroll
-                        for (int r = 0; r < TR; ++r) {
-                            const uint64_t ad = tc::smem_desc(
-                                a_base + ((r + dy) * kPitch + dx) * 16, kLboA, 128);
-                            tc::mma_bf16(d0 + r * N, ad, bd, idesc, (c | tap) != 0);
+                            for (int h = 0; h < TR + 2; ++h) {
+                                const uint64_t ad = tc::smem_desc(
+                                    a_base + (h * kPitch + dx) * 16, kLboA, 128);
+                                tc::mma_bf16(d0 + h * N, ad, bd, idesc3, 1u);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const int dy = tap / 3, dx = tap % 3;
+                            const uint64_t bd =
+                                tc::smem_desc(b_base + tap * 2 * N * 16, kLboB, 128);
+#pragma unroll
+                            for (int r = 0; r < TR; ++r) {
+                                const uint64_t ad = tc::smem_desc(
+                                    a_base + ((r + dy) * kPitch + dx) * 16, kLboA, 128);
+                                tc::mma_bf16(d0 + r * N, ad, bd, idesc, (c | tap) != 0);
+                            }
                         }
                     }
                     pending = true;
@@ -350,7 +395,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             tc::tc_fence_after();
             const int b = t / per_img, rr = t - b * per_img;
             const int y0 = (rr / tiles_x) * TR, x = (rr % tiles_x) * kTileX + warp * 32 + lane;
-            const uint32_t abase = tmem + lane_base + acc * TR * N;
+            const uint32_t abase = tmem + lane_base + acc * C::kAccCols + C::kRowOff * N;
+            // hands the accumulator back to the MMA warp
+            auto release_acc = [&]() {
+                tc::tc_fence_before();
+                tc::mbar_arrive(&bars.acce[acc]);
+            };
             // BF16 NHWC store of 16 channels [j, j+16) of one pixel
             auto store16 = [&](__nv_bfloat16 *dst, const float *f) {
                 uint4 *o = reinterpret_cast<uint4 *>(dst);
@@ -387,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             float f0[16], f1[16], sum[16];
 #pragma unroll
                             for (int e = 0; e < 16; ++e) {
-                                const float bb = a.bias ? __ldg(a.bias + j + e) : 0.f;
+                                const float bb = sbias[j + e];
                                 f0[e] = __bfloat162float(__float2bfloat16_rn(
                                     fmaxf(__uint_as_float(v0[16 * q + e]) + bb, 0.f)));
                                 f1[e] = __bfloat162float(__float2bfloat16_rn(
@@ -409,13 +459,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                         }
                     }
                 }
-                tc::tc_fence_before();
-                tc::mbar_arrive(&bars.acce[acc]);
+                release_acc();
                 continue;
             }
             if (RES && a.epi_mode == kEpiF32Planar && a.tma_out) {
                 // stage 16 output planes of the row in shared memory, store them
-                // with one TMA tensor store (clipped at W and at cout)
+                // with one TMA tensor store of 128 pixels (clipped at W and at
+                // cout); 128-pixel rows store faster than per-warp 32-pixel ones
                 float *ebuf = reinterpret_cast<float *>(base + C::kEpiOff);
                 const int px = warp * 32 + lane;
                 const int x0 = (rr % tiles_x) * kTileX;
@@ -429,22 +479,22 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                         tc::tmem_wait_ld();
                         if (j0 >= a.cout) continue;  // padding columns
                         float *buf = ebuf + (eblk & 1) * (16 * kTileX);
+                        // bias into registers before the barrier, whose memory
+                        // clobber would otherwise serialise these reads
+                        float bb[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) bb[e] = sbias[j0 + e];
                         if (tid == 0) tma_store_wait_read<1>();
                         named_bar_epilogue();
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int n = j0 + e;
-                            buf[e * kTileX + px] =
-                                __uint_as_float(v[e]) + ((a.bias && n < a.cout) ? __ldg(a.bias + n) : 0.f);
-                        }
+                        for (int e = 0; e < 16; ++e) buf[e * kTileX + px] = __uint_as_float(v[e]) + bb[e];
                         tc::fence_proxy_async();
                         named_bar_epilogue();
                         if (tid == 0 && y < a.H) tma_store_planes(&omap, buf, x0, y, j0, b);
                         ++eblk;
                     }
                 }
-                tc::tc_fence_before();
-                tc::mbar_arrive(&bars.acce[acc]);
+                release_acc();
                 continue;
             }
             // one row at a time, up to 32 columns per TMEM round trip
@@ -476,16 +526,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
 #pragma unroll
                             for (int e = 0; e < 16; ++e) {
                                 const int n = j + e;
-                                if (n < a.cout)
-                                    __stcs(o + n * plane, f[e] + (a.bias ? __ldg(a.bias + n) : 0.f));
+                                if (n < a.cout) __stcs(o + n * plane, f[e] + sbias[n]);
                             }
                             continue;
                         }
                         if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
-                            if (a.bias) {
 #pragma unroll
-                                for (int e = 0; e < 16; ++e) f[e] += __ldg(a.bias + j + e);
-                            }
+                            for (int e = 0; e < 16; ++e) f[e] += sbias[j + e];
                             if (a.epi_mode == kEpiReluBF16) {
 #pragma unroll
                                 for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
@@ -508,8 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     }
                 }
             }
-            tc::tc_fence_before();
-            tc::mbar_arrive(&bars.acce[acc]);
+            release_acc();
         }
         if (tid == 0 && eblk) tma_store_wait_all();
     }
@@ -528,12 +574,25 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, int cin, int co
     for (int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; idx < total;
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int e = static_cast<int>(idx % 8);
-        const int o = static_cast<int>((idx / 8) % n);
-        const int kg = static_cast<int>((idx / (8 * n)) % 2);
-        const int tap = static_cast<int>((idx / (16 * n)) % 9);
-        const int c = static_cast<int>(idx / (144 * static_cast<int64_t>(n)));
+        int o, kg, c, dy, dx;
+        if (n == 32) {
+            // stacked: [chunk][dx][kg][96 = (dy = 2, 1, 0) x 32][8]
+            const int n3 = static_cast<int>((idx / 8) % 96);
+            kg = static_cast<int>((idx / 768) % 2);
+            dx = static_cast<int>((idx / 1536) % 3);
+            c = static_cast<int>(idx / 4608);
+            o = n3 % 32;
+            dy = 2 - n3 / 32;
+        } else {
+            // [chunk][tap][kg][n][8]
+            o = static_cast<int>((idx / 8) % n);
+            kg = static_cast<int>((idx / (8 * n)) % 2);
+            const int tap = static_cast<int>((idx / (16 * n)) % 9);
+            c = static_cast<int>(idx / (144 * static_cast<int64_t>(n)));
+            dy = tap / 3;
+            dx = tap % 3;
+        }
         const int k = c * 16 + kg * 8 + e;  // input channel of this convolution
-        const int dy = tap / 3, dx = tap % 3;
         float v = 0.f;
         if (!transpose) {
             if (o < cout && k < cin) v = w[((static_cast<int64_t>(o) * cin + k) * 3 + dy) * 3 + dx];

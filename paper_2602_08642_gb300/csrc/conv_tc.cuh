@@ -52,7 +52,9 @@ struct ConvArgs {
 };
 
 // Bytes of a packed weight operand for a convolution with cin_pad input and n
-// output channels: BF16 [cin_pad/16][9 taps][2][n][8].
+// output channels: BF16 [cin_pad/16][9 taps][2][n][8]; for n = 32 the taps of
+// one dx are stacked along N instead: [cin_pad/16][3 dx][2][96 = dy 2,1,0 x 32][8]
+// (the same size).
 inline size_t packed_bytes(int cin_pad, int n) {
     return static_cast<size_t>(cin_pad / 16) * 9 * 2 * n * 8 * 2;
 }
