@@ -307,6 +307,19 @@ int spp_tonemap_backward(const float *hdr, int W, int H, const spp_tonemap *tm,
 int spp_l1_loss(const float *ldr, const float *ref, int64_t n, float *loss, float *grad_ldr,
                 cudaStream_t stream);
 
+/* Combined training loss of Sec. 6.3 (Eq. loss_spatial with the mask m = 1,
+ * Eq. loss_temporal, Eq. loss_combined) over n elements of tone-mapped sRGB:
+ *   *loss (device float, OVERWRITTEN) = mean of max(wt |dI - dI_ref|, ws |I - I_ref|)
+ * with dI = ldr - prev_warped and dI_ref = ref - ref_prev_warped (the previous
+ * output and reference, warped to this frame, e.g. by spp_warp_previous),
+ * wt = temporal_weight, ws = spatial_weight (the paper: 1.25 and 1; ws = 0
+ * gives the temporal error alone); the maximum is taken per element, ties go
+ * to the spatial term.  grad_ldr (nullable, OVERWRITTEN) = d loss / d ldr
+ * with the previous frame held constant. */
+int spp_combined_loss(const float *ldr, const float *ref, const float *prev_warped,
+                      const float *ref_prev_warped, int64_t n, float temporal_weight,
+                      float spatial_weight, float *loss, float *grad_ldr, cudaStream_t stream);
+
 /* Evaluation metric: *mse (device double, OVERWRITTEN) = mean over the n
  * elements of (a - b)^2, accumulated in FP64.  PSNR = -10 log10(mse) for
  * images in [0, 1]. */

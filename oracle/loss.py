@@ -21,18 +21,21 @@ from __future__ import annotations
 import numpy as np
 
 
-def combined_loss(ldr, ref, prev_warped, ref_prev_warped, temporal_weight: float = 1.25):
-    """(L, dL/d ldr) in FP64."""
+def combined_loss(ldr, ref, prev_warped, ref_prev_warped, temporal_weight: float = 1.25,
+                  spatial_weight: float = 1.0):
+    """(L, dL/d ldr) in FP64 of mean max(w_t T, w_s S); the paper's weights
+    are w_t = 1.25, w_s = 1 (w_s = 0 gives the temporal error alone)."""
     I = np.asarray(ldr, np.float64)
     R = np.asarray(ref, np.float64)
     dI = I - np.asarray(prev_warped, np.float64)
     dR = R - np.asarray(ref_prev_warped, np.float64)
-    s = np.abs(I - R)
+    s = spatial_weight * np.abs(I - R)
     t = temporal_weight * np.abs(dI - dR)
     n = I.size
     temporal = t > s
     loss = float(np.where(temporal, t, s).sum() / n)
-    grad = np.where(temporal, temporal_weight * np.sign(dI - dR), np.sign(I - R)) / n
+    grad = np.where(temporal, temporal_weight * np.sign(dI - dR),
+                    spatial_weight * np.sign(I - R)) / n
     return loss, grad
 
 

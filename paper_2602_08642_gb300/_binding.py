@@ -108,6 +108,8 @@ _SIGS = {
                             ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "spp_tonemap_image": (_I, [_P, _I, _I, ctypes.POINTER(spp_tonemap), _P, _P]),
     "spp_mse": (_I, [_P, _P, _I64, _P, _P]),
+    "spp_combined_loss": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, _P, _P,
+                               _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -415,3 +417,12 @@ def spp_tonemap_image(hdr, W, H, tm, ldr, stream=None) -> int:
 def spp_mse(a, b, n, out, stream=None) -> int:
     f = torch.float32
     return lib.spp_mse(_dev(a, f), _dev(b, f), int(n), _dev(out, torch.float64), _stream(stream))
+
+
+def spp_combined_loss(ldr, ref, prev_warped, ref_prev_warped, n, temporal_weight, spatial_weight,
+                      loss, grad_ldr, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_combined_loss(_dev(ldr, f), _dev(ref, f), _dev(prev_warped, f),
+                                 _dev(ref_prev_warped, f), int(n), float(temporal_weight),
+                                 float(spatial_weight), _dev(loss, f), _dev(grad_ldr, f),
+                                 _stream(stream))

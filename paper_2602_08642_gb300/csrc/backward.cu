@@ -303,6 +303,39 @@ l1_loss_kernel(const float *__restrict__ a, const float *__restrict__ b, long lo
     }
 }
 
+// Eq. loss_combined: mean over elements of max(wt |dI - dI_ref|, ws |I - I_ref|)
+// with dI = I - Wprev, dI_ref = I_ref - Wref (warped previous frames), and
+// its gradient with respect to I (ties go to the spatial term).
+__global__ void combined_loss_kernel(const float *__restrict__ I, const float *__restrict__ R,
+                                     const float *__restrict__ P, const float *__restrict__ Q,
+                                     long long n, float w, float ws,
+                                     float *__restrict__ loss, float *__restrict__ grad) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    float v = 0.0f;
+    if (i < n) {
+        const float ds = I[i] - R[i];
+        const float dt = (I[i] - P[i]) - (R[i] - Q[i]);
+        const float s = ws * fabsf(ds), t = w * fabsf(dt);
+        const bool temporal = t > s;
+        v = temporal ? t : s;
+        if (grad) {
+            const float sg = temporal ? (dt > 0.0f ? w : (dt < 0.0f ? -w : 0.0f))
+                                      : (ds > 0.0f ? ws : (ds < 0.0f ? -ws : 0.0f));
+            grad[i] = sg / static_cast<float>(n);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    __shared__ float part[8];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += part[k];
+        atomicAdd(loss, t / static_cast<float>(n));
+    }
+}
+
 // Mean squared difference (for PSNR); partial sums in FP64, one atomic per block.
 __global__ void sq_err_kernel(const float *__restrict__ a, const float *__restrict__ b, long long n,
                               double *__restrict__ out) {
@@ -523,6 +556,23 @@ int spp_l1_loss(const float *ldr, const float *ref, int64_t n, float *loss, floa
     if (n == 0) return SPP_OK;
     l1_loss_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
         ldr, ref, static_cast<long long>(n), loss, grad_ldr);
+    count_launch();
+    return launch_status();
+}
+
+int spp_combined_loss(const float *ldr, const float *ref, const float *prev_warped,
+                      const float *ref_prev_warped, int64_t n, float temporal_weight,
+                      float spatial_weight, float *loss, float *grad_ldr, cudaStream_t stream) {
+    using namespace spp;
+    if (n < 0 || !ldr || !ref || !prev_warped || !ref_prev_warped || !loss) return SPP_ERR_ARG;
+    if (!aligned16(ldr) || !aligned16(ref) || !aligned16(prev_warped) ||
+        !aligned16(ref_prev_warped) || !aligned16(loss) || (grad_ldr && !aligned16(grad_ldr)))
+        return SPP_ERR_ALIGN;
+    if (cudaMemsetAsync(loss, 0, sizeof(float), stream) != cudaSuccess) return SPP_ERR_CUDA;
+    if (n == 0) return SPP_OK;
+    combined_loss_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
+        ldr, ref, prev_warped, ref_prev_warped, static_cast<long long>(n), temporal_weight,
+        spatial_weight, loss, grad_ldr);
     count_launch();
     return launch_status();
 }

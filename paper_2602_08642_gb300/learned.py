@@ -103,10 +103,12 @@ class Predictor:
                                     *self.g_logits, self.grad, self.bws, self.status),
                 "spp_unet_backward")
 
-    def adamw(self, lr: float, weight_decay: float = 1e-4, grad_scale: float = 1.0):
+    def adamw(self, lr: float, weight_decay: float = 1e-4, grad_scale: float = 1.0,
+              betas=(0.9, 0.999)):
         self.step_count += 1
         B.check(B.spp_adamw_step(self.theta, self.grad, self.m, self.v, self.step_count, lr=lr,
-                                 weight_decay=weight_decay, grad_scale=grad_scale), "adamw")
+                                 beta1=betas[0], beta2=betas[1], weight_decay=weight_decay,
+                                 grad_scale=grad_scale), "adamw")
         self.pack()
 
     def frame_logits(self, b: int, temporal: bool):
@@ -151,6 +153,12 @@ class Renderer:
         self.mse = torch.zeros(2, dtype=torch.float64, device="cuda")[:1]
         self.dws = Predictor._aligned(B.spp_density_backward_workspace_bytes())
         self.cur_params = [None] * B_
+        # temporal term of the objective: previous tone-mapped output and
+        # reference, warped to the current frame
+        self.ldr_prev = [_zeros(3, H, W) for _ in range(B_)]
+        self.wldr_prev = [_zeros(3, H, W) for _ in range(B_)]
+        self.wref_prev = [_zeros(3, H, W) for _ in range(B_)]
+        self.tmp = _zeros(3, H, W)
 
     def params(self, frame: int, seed: int):
         return B.make_params(self.budget, uniform_fraction=PHI, seed=seed, frame=frame)
@@ -163,6 +171,7 @@ class Renderer:
         fr.splat()
         out = fr.reconstruct(logits, tm=self.tm)
         self.hdr_prev[b].copy_(out)
+        self.ldr_prev[b].copy_(fr.ldr)
 
     def warp_previous(self, b: int, mv):
         B.check(B.spp_warp_previous(self.hdr_prev[b], mv, self.W, self.H, self.warped[b]), "warp")
@@ -190,12 +199,27 @@ class Renderer:
     def reference(self, b: int, clean):
         B.check(B.spp_tonemap_image(clean, self.W, self.H, self.tm, self.ref[b]), "tonemap")
 
-    def backward(self, b: int, d, logits, g_logits):
-        """L1 loss of sample b and its gradient into g_logits (level 0 planes
-        0..53 and the density plane 54, levels 1 and 2)."""
+    def temporal_references(self, b: int, clean_prev, mv):
+        """W(I_{t-1}) and W(I_ref,{t-1}) of Eq. loss_temporal: the previous
+        tone-mapped output and reference warped to frame t."""
+        B.check(B.spp_warp_previous(self.ldr_prev[b], mv, self.W, self.H, self.wldr_prev[b]),
+                "warp")
+        B.check(B.spp_tonemap_image(clean_prev, self.W, self.H, self.tm, self.tmp), "tonemap")
+        B.check(B.spp_warp_previous(self.tmp, mv, self.W, self.H, self.wref_prev[b]), "warp")
+
+    def backward(self, b: int, d, logits, g_logits, objective: str = "l1"):
+        """Loss of sample b and its gradient into g_logits (level 0 planes
+        0..53 and the density plane 54, levels 1 and 2).  objective "l1" is
+        Eq. loss_spatial with m = 1; "combined" is Eq. loss_combined (needs
+        temporal_references first)."""
         fr = self.frames[b]
         n = 3 * self.W * self.H
-        B.check(B.spp_l1_loss(self.ldr[b], self.ref[b], n, self.loss[b], self.g_ldr), "l1")
+        if objective == "combined":
+            B.check(B.spp_combined_loss(self.ldr[b], self.ref[b], self.wldr_prev[b],
+                                        self.wref_prev[b], n, 1.25, 1.0, self.loss[b], self.g_ldr),
+                    "combined loss")
+        else:
+            B.check(B.spp_l1_loss(self.ldr[b], self.ref[b], n, self.loss[b], self.g_ldr), "l1")
         g = self.g_hdr[0]
         g.zero_()
         B.check(B.spp_tonemap_backward(self.hdr[b], self.W, self.H, self.tm, self.g_ldr, g),
@@ -228,21 +252,50 @@ class Renderer:
         return -10.0 * math.log10(max(m, 1e-30))
 
 
+def random_tonemap(rng) -> "B.spp_tonemap":
+    """A tone map of the training family (Sec. 5): contrast and saturation in
+    [0.8, 1.2], exposure in [-1, 1], shadow and highlight in [0.2, 0.9]."""
+    return B.make_tonemap(alpha=float(rng.uniform(0.8, 1.2)), beta=float(rng.uniform(0.8, 1.2)),
+                          exposure=float(rng.uniform(-1.0, 1.0)),
+                          shadow=float(rng.uniform(0.2, 0.9)),
+                          highlight=float(rng.uniform(0.2, 0.9)))
+
+
 class Trainer:
-    """Trains the predictor on batches of two-frame samples."""
+    """Trains the predictor on batches of two-frame samples.
+
+    objective "l1" (Eq. loss_spatial, m = 1) or "combined" (Eq.
+    loss_combined with the temporal term); random_tmo draws a tone map of
+    the training family per step; total_steps enables cosine annealing of
+    the learning rate; betas and weight_decay are AdamW's (the paper uses
+    (0.8, 0.985) and 0.02)."""
 
     def __init__(self, theta: torch.Tensor, batch: int, size: int, budget: float = 0.25,
-                 lr: float = 1e-3, weight_decay: float = 1e-4):
+                 lr: float = 1e-3, weight_decay: float = 1e-4, objective: str = "l1",
+                 betas=(0.9, 0.999), random_tmo: bool = False, total_steps: int | None = None,
+                 seed: int = 0):
+        import numpy as np
         self.net = Predictor(theta, batch, size, size, train=True)
         self.rnd = Renderer(batch, size, size, budget)
         self.lr, self.wd = lr, weight_decay
+        self.objective, self.betas, self.random_tmo = objective, betas, random_tmo
+        self.total_steps = total_steps
+        self.rng = np.random.default_rng(seed)
         self.step_index = 0
+
+    def current_lr(self) -> float:
+        if not self.total_steps:
+            return self.lr
+        k = min(self.step_index, self.total_steps)
+        return 0.5 * self.lr * (1.0 + math.cos(math.pi * k / self.total_steps))
 
     def step(self, samples: list[FrameData], seed: int) -> float:
         """One optimisation step on len(samples) == batch samples; returns
         the mean loss (reading it synchronises)."""
         net, rnd = self.net, self.rnd
         f_prev, f_cur = 2 * self.step_index, 2 * self.step_index + 1
+        if self.random_tmo:
+            rnd.tm = random_tonemap(self.rng)
         for b, s in enumerate(samples):
             net.features(b, s.gprev["albedo"], s.gprev["normal"], s.gprev["depth"], s.mv, None)
         net.forward()
@@ -256,20 +309,25 @@ class Trainer:
             logits = net.frame_logits(b, True)
             rnd.current_frame(b, net.density[b], logits, s.clean, seed + b, f_cur)
             rnd.reference(b, s.clean)
+            if self.objective == "combined":
+                rnd.temporal_references(b, s.clean_prev, s.mv)
             gl = [net.g_logits[0][b, :54], net.g_logits[1][b], net.g_logits[2][b],
                   net.g_logits[0][b, 54]]
-            rnd.backward(b, net.density[b], logits, gl)
+            rnd.backward(b, net.density[b], logits, gl, self.objective)
         net.backward()
-        net.adamw(self.lr, self.wd, grad_scale=1.0 / len(samples))
+        net.adamw(self.current_lr(), self.wd, grad_scale=1.0 / len(samples), betas=self.betas)
         self.step_index += 1
         return float(sum(l.item() for l in rnd.loss)) / len(samples)
 
 
 def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None,
-             fixed_logits: list[torch.Tensor] | None = None, seed: int = 99) -> list[float]:
+             fixed_logits: list[torch.Tensor] | None = None, seed: int = 99,
+             temporal: list | None = None) -> list[float]:
     """PSNR (tone-mapped sRGB against the tone-mapped clean image) of frame
     t of each sample.  theta None runs the plain method: uniform density
-    d = 1 and the fixed logits (54 / 29 / 25 channels)."""
+    d = 1 and the fixed logits (54 / 29 / 25 channels).  If ``temporal`` is
+    a list, the temporal error mean |dI - dI_ref| of Eq. loss_temporal of
+    each sample is appended to it."""
     W, H = samples[0].W, samples[0].H
     rnd = Renderer(1, W, H, budget)
     net = Predictor(theta, 1, W, H) if theta is not None else None
@@ -293,4 +351,11 @@ def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None
         rnd.current_frame(0, d, lg, s.clean, seed + i, 1)
         rnd.reference(0, s.clean)
         out.append(rnd.psnr(0))
+        if temporal is not None:
+            # mean |dI - dI_ref|: the combined loss with the spatial weight 0
+            rnd.temporal_references(0, s.clean_prev, s.mv)
+            B.check(B.spp_combined_loss(rnd.ldr[0], rnd.ref[0], rnd.wldr_prev[0],
+                                        rnd.wref_prev[0], 3 * W * H, 1.0, 0.0, rnd.loss[0], None),
+                    "temporal error")
+            temporal.append(float(rnd.loss[0].item()))
     return out

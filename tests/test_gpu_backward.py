@@ -243,3 +243,25 @@ def test_autograd_chain_matches_oracle_chain(spp):
     for l in range(L):
         assert_grad(host(lgt[l].grad), g_logits[l], f"grad logits {l}", rtol=3e-4, afrac=3e-5)
     assert_grad(host(zt.grad), gz, "grad z", rtol=1e-3, afrac=1e-4)
+
+
+@pytest.mark.parametrize("ws", [1.0, 0.0])
+def test_combined_loss_parity(spp, ws):
+    """Eq. loss_combined (and, with ws = 0, the temporal error alone) and its
+    gradient against the FP64 oracle."""
+    import oracle.loss as OL
+    rng = np.random.default_rng(14 + int(ws))
+    n = 3 * 77 * 53
+    I, R, P, Q = (rng.random(n).astype(np.float32) for _ in range(4))
+    loss = torch.zeros(4, device="cuda")[:1]
+    grad = torch.empty(n, device="cuda")
+    spp.check(spp.binding.spp_combined_loss(dev(I), dev(R), dev(P), dev(Q), n, 1.25, ws, loss,
+                                            grad))
+    v, g = OL.combined_loss(I, R, P, Q, 1.25, ws)
+    assert abs(float(loss.item()) - v) <= 1e-5 * v
+    got = host(grad)
+    # the branch taken may differ where the two terms are within FP32 rounding
+    s = ws * np.abs(I.astype(np.float64) - R)
+    t = 1.25 * np.abs((I.astype(np.float64) - P) - (R.astype(np.float64) - Q))
+    clear = np.abs(t - s) > 1e-6
+    assert np.allclose(got[clear], g[clear], rtol=1e-6, atol=0)

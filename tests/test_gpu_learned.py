@@ -50,3 +50,36 @@ def test_trained_network_beats_plain_method(spp):
     learned = float(np.mean(Lm.evaluate(held, budget, tr.net.theta, None)))
     print(f"held-out PSNR: plain {plain:.2f} dB, learned {learned:.2f} dB")
     assert learned > plain + 1.0
+
+
+def test_full_objective_training(spp):
+    """Training with the paper's full objective (Eq. loss_combined), a random
+    tone map of the training family per step, AdamW with the paper's betas and
+    weight decay and a cosine schedule: the loss falls, the network beats the
+    plain method in PSNR and at least halves its temporal error |dI - dI_ref|
+    (measured: 3.5x lower, +0.5 dB)."""
+    from paper_2602_08642_gb300 import learned as Lm
+    size, budget, steps = 64, 0.25, 200
+    train = [Lm.FrameData(inp.training_pair(size, seed=100 + i)) for i in range(24)]
+    held = [Lm.FrameData(inp.training_pair(size, seed=900 + i)) for i in range(8)]
+    theta = torch.from_numpy(inp.unet_params(U.LAYERS, seed=5, head_bias=inp.fixed_head_bias()))
+    fixed = [torch.from_numpy(a).cuda() for a in inp.fixed_logits(size, size, 3, True)]
+    t_plain = []
+    plain = float(np.mean(Lm.evaluate(held, budget, None, fixed, temporal=t_plain)))
+    tr = Lm.Trainer(theta, 8, size, budget, lr=2e-3, weight_decay=0.02, objective="combined",
+                    betas=(0.8, 0.985), random_tmo=True, total_steps=steps, seed=1)
+    rng = np.random.default_rng(0)
+    losses = []
+    for k in range(steps):
+        idx = rng.choice(len(train), 8, replace=False)
+        losses.append(tr.step([train[i] for i in idx], seed=1000 + 17 * k))
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    t_learned = []
+    learned = float(np.mean(Lm.evaluate(held, budget, tr.net.theta, None, temporal=t_learned)))
+    print(f"full objective: PSNR plain {plain:.2f} learned {learned:.2f} dB; temporal error "
+          f"plain {np.mean(t_plain):.4f} learned {np.mean(t_learned):.4f}")
+    # the temporal term trades spatial error for stability: a smaller PSNR gain
+    # than the L1-trained network, a much smaller temporal error
+    assert learned > plain + 0.25
+    assert np.mean(t_learned) < 0.5 * np.mean(t_plain)

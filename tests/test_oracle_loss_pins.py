@@ -49,3 +49,10 @@ def test_cosine_schedule_endpoints():
     assert L.cosine_lr(0, 100, 1e-3) == 1e-3
     assert abs(L.cosine_lr(50, 100, 1e-3) - 0.5e-3) < 1e-18
     assert abs(L.cosine_lr(100, 100, 1e-3, 1e-5) - 1e-5) < 1e-18
+
+
+def test_zero_spatial_weight_gives_temporal_l1():
+    rng = np.random.default_rng(4)
+    I, R, P, Q = (rng.random(30) for _ in range(4))
+    loss, _ = L.combined_loss(I, R, P, Q, temporal_weight=1.0, spatial_weight=0.0)
+    assert abs(loss - np.abs((I - P) - (R - Q)).mean()) < 1e-15
