@@ -72,6 +72,7 @@ def _load():
             "orc_budget_coeffs": (_I, [_P, _I64, _D, _D, _P, _P, _P]),
             "orc_assign_one": (None, [_D, _D, _D, _I, _P, _P, _P]),
             "orc_alloc": (_I, [_P, _I64, _D, _D, _D, _I, _U64, _U32, _P, _P, _P, _P, _P, _P]),
+            "orc_alloc_u48": (_I, [_P, _I64, _D, _D, _D, _I, _P, _P, _P, _P, _P, _P, _P]),
             "orc_sample_list": (None, [_P, _I64, _P]),
             "orc_sample_noise": (_D, [_U64, _U32, _U64, _U64]),
             "orc_render": (None, [_P, _P, _I64, _U64, _U32, _P]),
@@ -168,7 +169,10 @@ class Alloc:
 
 
 def alloc(d, B: float, phi: float = 0.125, lam: float = 10.0, hard: bool = False,
-          seed: int = 0x5EED, frame: int = 0) -> Alloc:
+          seed: int = 0x5EED, frame: int = 0, u48=None) -> Alloc:
+    """Sec. 3 and 4.2-4.3.  u48 (optional, uint64 per pixel) replaces the
+    counter-based uniforms by explicit ones, u = u48 2^-48 (the blue-noise
+    dither, oracle.bluenoise.uniform48)."""
     d = _c(d, np.float32).ravel()
     N = d.size
     s = np.empty(N, np.float64)
@@ -177,9 +181,17 @@ def alloc(d, B: float, phi: float = 0.125, lam: float = 10.0, hard: bool = False
     w = np.empty(N, np.float64)
     extra = np.empty(N, np.int32)
     coeffs = np.empty(3, np.float64)
-    rc = _load().orc_alloc(_ptr(d), N, B, phi, lam, int(hard), seed & 0xFFFFFFFFFFFFFFFF,
-                           frame, _ptr(s), _ptr(counts), _ptr(offsets), _ptr(w), _ptr(extra),
-                           _ptr(coeffs))
+    if u48 is not None:
+        u = np.ascontiguousarray(np.asarray(u48, np.uint64).ravel())
+        if u.size != N:
+            raise ValueError("u48 must have one value per pixel")
+        rc = _load().orc_alloc_u48(_ptr(d), N, B, phi, lam, int(hard), _ptr(u), _ptr(s),
+                                   _ptr(counts), _ptr(offsets), _ptr(w), _ptr(extra),
+                                   _ptr(coeffs))
+    else:
+        rc = _load().orc_alloc(_ptr(d), N, B, phi, lam, int(hard), seed & 0xFFFFFFFFFFFFFFFF,
+                               frame, _ptr(s), _ptr(counts), _ptr(offsets), _ptr(w),
+                               _ptr(extra), _ptr(coeffs))
     if rc != OK:
         return Alloc(rc=rc)
     T = int(offsets[N])

@@ -242,6 +242,33 @@ int orc_alloc(const float *d, int64_t N, double B, double phi, double lambda, in
     return ORC_OK;
 }
 
+/* a1-a2 with explicit uniforms: u_i = u48[i] 2^-48 (the blue-noise dither of
+ * Sec. 6.3 instead of the counter-based white noise); otherwise orc_alloc. */
+int orc_alloc_u48(const float *d, int64_t N, double B, double phi, double lambda, int hard,
+                  const uint64_t *u48, double *s_out, int64_t *counts, int64_t *offsets,
+                  double *w_out, int32_t *extra_out, double *coeffs_out) {
+    double S, a, c;
+    int rc = orc_budget_coeffs(d, N, B, phi, &S, &a, &c);
+    if (rc != ORC_OK) return rc;
+    if (coeffs_out) { coeffs_out[0] = S; coeffs_out[1] = a; coeffs_out[2] = c; }
+    int64_t run = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        double m = c * (double)d[i];
+        double s = a + m;
+        double u = (double)u48[i] * 0x1p-48;
+        int64_t n; double w; int extra;
+        orc_assign_one(s, u, lambda, hard, &n, &w, &extra);
+        s_out[i] = s;
+        counts[i] = n;
+        w_out[i] = w;
+        if (extra_out) extra_out[i] = extra;
+        offsets[i] = run;
+        run += n;
+    }
+    offsets[N] = run;
+    return ORC_OK;
+}
+
 /* a3: the sample list, pixel index of every slot. */
 void orc_sample_list(const int64_t *offsets, int64_t N, int32_t *sample_pixel) {
     for (int64_t i = 0; i < N; ++i)
