@@ -94,6 +94,17 @@ int spp_get_status(const int32_t *status, cudaStream_t stream);
 int spp_clear_status(int32_t *status, cudaStream_t stream);
 
 /* ---------------------------------------------------- a1-a3: allocation */
+/* Blue-noise dithering (Sec. 6.3 dithers the discretisation with blue
+ * noise, after Ulichney's void-and-cluster method).  spp_blue_noise_mask
+ * writes a T x T rank matrix (T a power of two in [4, 256], a permutation of
+ * 0 .. T^2-1) to HOST memory `rank`: void-and-cluster on a torus with a
+ * Gaussian filter of sigma 1.5 whose weights are the integers
+ * round(2^20 exp(-r^2 / 4.5)), ties broken by the smallest index, the start
+ * pattern of floor(T^2/10) pixels drawn by SplitMix64(seed).  SPP_ERR_ARG for
+ * a bad T or a null pointer.  Upload the result to use it with
+ * spp_alloc_sample_map_dithered. */
+int spp_blue_noise_mask(int T, uint64_t seed, uint16_t *rank);
+
 /* Workspace bytes spp_alloc_sample_map needs for a W x H frame. */
 size_t spp_alloc_workspace_bytes(int W, int H);
 
@@ -134,6 +145,24 @@ int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p,
                          int32_t *counts, int32_t *offsets, int32_t *sample_pixel,
                          int64_t capacity, float *s_out, float *holdout_w, int64_t *total,
                          int32_t *status, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* spp_alloc_sample_map with the uniforms taken from a blue-noise mask
+ * (device, uint16 [T][T], from spp_blue_noise_mask) tiled over the frame
+ * instead of the counter-based white noise: for pixel (x, y) of frame
+ * p->frame,
+ *   u = ((rank[y mod T][x mod T] 2^(48-2k) + 2^(47-2k) + off) mod 2^48) 2^-48,
+ *   T = 2^k, off = (frame G + (mix(seed) >> 16)) mod 2^48,
+ * G = 0x9E3779B97F4A (the golden-ratio gamma's top 48 bits), mix the
+ * SplitMix64 finaliser.  Within a tile the uniforms of a frame are the
+ * stratified values (r + 1/2)/T^2 in blue-noise order, so a constant density
+ * receives its budget to within one sample per tile; the golden-ratio step
+ * moves each pixel's threshold from frame to frame.  Other arguments and
+ * errors as spp_alloc_sample_map. */
+int spp_alloc_sample_map_dithered(const float *d, int W, int H, const spp_params *p,
+                                  const uint16_t *mask, int T, int32_t *counts, int32_t *offsets,
+                                  int32_t *sample_pixel, int64_t capacity, float *s_out,
+                                  float *holdout_w, int64_t *total, int32_t *status, void *ws,
+                                  size_t ws_bytes, cudaStream_t stream);
 
 /*
  * Allocation-free variant of spp_alloc_sample_map.  The paper has no

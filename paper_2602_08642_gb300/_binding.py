@@ -108,6 +108,9 @@ _SIGS = {
                             ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _P]),
     "spp_tonemap_image": (_I, [_P, _I, _I, ctypes.POINTER(spp_tonemap), _P, _P]),
     "spp_mse": (_I, [_P, _P, _I64, _P, _P]),
+    "spp_blue_noise_mask": (_I, [_I, _U64, _P]),
+    "spp_alloc_sample_map_dithered": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _I, _P,
+                                           _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "spp_combined_loss": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, _P, _P,
                                _P]),
 }
@@ -426,3 +429,24 @@ def spp_combined_loss(ldr, ref, prev_warped, ref_prev_warped, n, temporal_weight
                                  _dev(ref_prev_warped, f), int(n), float(temporal_weight),
                                  float(spatial_weight), _dev(loss, f), _dev(grad_ldr, f),
                                  _stream(stream))
+
+
+# ------------------------------------------------------ blue-noise dithering
+def spp_blue_noise_mask(T: int, seed: int):
+    """The T x T rank matrix as a host numpy uint16 array."""
+    import numpy as np
+    out = np.empty((T, T), np.uint16)
+    check(lib.spp_blue_noise_mask(T, seed & 0xFFFFFFFFFFFFFFFF,
+                                  ctypes.c_void_p(out.ctypes.data)), "spp_blue_noise_mask")
+    return out
+
+
+def spp_alloc_sample_map_dithered(d, W, H, params: spp_params, mask, counts, offsets,
+                                  sample_pixel, capacity, s_out, holdout_w, total, status, ws,
+                                  stream=None) -> int:
+    return lib.spp_alloc_sample_map_dithered(
+        _dev(d, torch.float32), W, H, ctypes.byref(params), _dev(mask, torch.int16),
+        mask.shape[0], _dev(counts, torch.int32), _dev(offsets, torch.int32),
+        _dev(sample_pixel, torch.int32), int(capacity), _dev(s_out, torch.float32),
+        _dev(holdout_w, torch.float32), _dev(total, torch.int64), _dev(status, torch.int32),
+        _dev(ws), _nbytes(ws), _stream(stream))

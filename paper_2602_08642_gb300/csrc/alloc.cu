@@ -394,10 +394,29 @@ __device__ __forceinline__ void st_state(unsigned long long *p, unsigned long lo
     atomicExch(p, v);
 }
 
+// Source of the uniforms u_i: the counter-based white noise (mask == null),
+// or a tiled T x T blue-noise rank mask (Sec. 6.3):
+//   u48 = (rank[y mod T][x mod T] 2^(48 - 2 log2 T) + 2^(47 - 2 log2 T) + off48) mod 2^48
+// with off48 = t G48 + (mix(seed) >> 16) mod 2^48 set by the host.
+struct Dither {
+    const uint16_t *mask = nullptr;
+    int W = 0, log2T = 0;
+    uint64_t off48 = 0;
+};
+
+__device__ __forceinline__ uint64_t dither_bits(const Dither &dt, long long i) {
+    const int y = static_cast<int>(i / dt.W), x = static_cast<int>(i - static_cast<long long>(y) * dt.W);
+    const int T = 1 << dt.log2T;
+    const uint64_t r = __ldg(dt.mask + ((y & (T - 1)) << dt.log2T) + (x & (T - 1)));
+    const uint64_t u48 = ((r << (48 - 2 * dt.log2T)) + (1ull << (47 - 2 * dt.log2T)) + dt.off48) &
+                         0xFFFFFFFFFFFFull;
+    return u48 << 16;
+}
+
 __global__ void __launch_bounds__(kScanThreads, 4)
 assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *hdr_c,
-                   AllocHeader *hdr, unsigned long long *tile_state, uint64_t key, int hard,
-                   int stall_tile1,
+                   AllocHeader *hdr, unsigned long long *tile_state, uint64_t key, Dither dither,
+                   int hard, int stall_tile1,
                    int32_t *__restrict__ counts, int32_t *__restrict__ offsets,
                    int32_t *__restrict__ sample_pixel, long long capacity, float *__restrict__ s_out,
                    float *__restrict__ w_out, long long *total, int32_t *status, int num_tiles) {
@@ -447,7 +466,8 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
         wv[q] = 1.0f;
         sv[q] = 1.0f;
         if (i < N && valid) {
-            const uint64_t bits = stream_bits(key, static_cast<uint64_t>(i));
+            const uint64_t bits = dither.mask ? dither_bits(dither, i)
+                                              : stream_bits(key, static_cast<uint64_t>(i));
             int nq = 0;
             float wq = 1.0f, sq = 1.0f;
             bool done = false;
@@ -605,11 +625,14 @@ size_t spp_alloc_workspace_bytes(int W, int H) {
     return spp::kHeaderBytes + spp::alloc_tiles(N) * sizeof(unsigned long long);
 }
 
-int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int32_t *counts,
-                         int32_t *offsets, int32_t *sample_pixel, int64_t capacity, float *s_out,
-                         float *holdout_w, int64_t *total, int32_t *status, void *ws,
-                         size_t ws_bytes, cudaStream_t stream) {
-    using namespace spp;
+}  // extern "C"
+
+namespace spp {
+namespace {
+int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &dither,
+               int32_t *counts, int32_t *offsets, int32_t *sample_pixel, int64_t capacity,
+               float *s_out, float *holdout_w, int64_t *total, int32_t *status, void *ws,
+               size_t ws_bytes, cudaStream_t stream) {
     if (!p || W < 0 || H < 0 || capacity < 0) return SPP_ERR_ARG;
     if (static_cast<long long>(W) * H == 0) {  // empty frame: T = 0, offsets[0] = 0
         if (!offsets || !total) return SPP_ERR_ARG;
@@ -657,13 +680,46 @@ int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int3
     budget_sum_kernel<<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(d, N, hdr, args,
                                                                              status);
     const int num_tiles = static_cast<int>(alloc_tiles(N));
+    Dither dt = dither;
+    dt.W = W;
     assign_scan_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
-        d, N, hdr, hdr, tiles, stream_key(p->seed, p->frame), args.hard,
+        d, N, hdr, hdr, tiles, stream_key(p->seed, p->frame), dt, args.hard,
         (p->flags & SPP_FLAG_TEST_STALL_TILE1) ? 1 : 0, counts, offsets,
         sample_pixel, capacity, s_out, holdout_w, reinterpret_cast<long long *>(total), status,
         num_tiles);
     count_launch(2);
     return launch_status();
+}
+}  // namespace
+}  // namespace spp
+
+extern "C" {
+
+int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int32_t *counts,
+                         int32_t *offsets, int32_t *sample_pixel, int64_t capacity, float *s_out,
+                         float *holdout_w, int64_t *total, int32_t *status, void *ws,
+                         size_t ws_bytes, cudaStream_t stream) {
+    return spp::alloc_impl(d, W, H, p, spp::Dither{}, counts, offsets, sample_pixel, capacity,
+                           s_out, holdout_w, total, status, ws, ws_bytes, stream);
+}
+
+int spp_alloc_sample_map_dithered(const float *d, int W, int H, const spp_params *p,
+                                  const uint16_t *mask, int T, int32_t *counts, int32_t *offsets,
+                                  int32_t *sample_pixel, int64_t capacity, float *s_out,
+                                  float *holdout_w, int64_t *total, int32_t *status, void *ws,
+                                  size_t ws_bytes, cudaStream_t stream) {
+    using namespace spp;
+    if (!mask || !p) return SPP_ERR_ARG;
+    if (T < 4 || T > 256 || (T & (T - 1))) return SPP_ERR_ARG;
+    if (!aligned16(mask)) return SPP_ERR_ALIGN;
+    Dither dt;
+    dt.mask = mask;
+    dt.log2T = 0;
+    while ((1 << dt.log2T) < T) ++dt.log2T;
+    dt.off48 = (static_cast<uint64_t>(p->frame) * (kGamma >> 16) + (mix64(p->seed) >> 16)) &
+               0xFFFFFFFFFFFFull;
+    return alloc_impl(d, W, H, p, dt, counts, offsets, sample_pixel, capacity, s_out, holdout_w,
+                      total, status, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

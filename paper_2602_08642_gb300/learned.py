@@ -132,8 +132,10 @@ class FrameData:
 class Renderer:
     """Per-frame sampling / reconstruction state for B frames of W x H."""
 
-    def __init__(self, B_: int, W: int, H: int, budget: float):
+    def __init__(self, B_: int, W: int, H: int, budget: float, dither_mask=None):
         self.B, self.W, self.H, self.budget = B_, W, H, budget
+        # blue-noise rank mask (device int16 [T][T]) or None for white noise
+        self.mask = dither_mask
         self.frames = [Frame(W, H, LEVELS, max_budget=budget) for _ in range(B_)]
         self.tm = B.make_tonemap()
         self.hdr_prev = [_zeros(3, H, W) for _ in range(B_)]
@@ -160,13 +162,19 @@ class Renderer:
         self.wref_prev = [_zeros(3, H, W) for _ in range(B_)]
         self.tmp = _zeros(3, H, W)
 
+    def _alloc(self, fr, d, params):
+        if self.mask is not None:
+            fr.alloc_dithered(d, params, self.mask)
+        else:
+            fr.alloc(d, params)
+
     def params(self, frame: int, seed: int):
         return B.make_params(self.budget, uniform_fraction=PHI, seed=seed, frame=frame)
 
     def previous_frame(self, b: int, d, logits, clean, seed: int, frame: int):
         """Frame t-1 of sample b (no temporal term); its output goes to hdr_prev[b]."""
         fr = self.frames[b]
-        fr.alloc(d, self.params(frame, seed))
+        self._alloc(fr, d, self.params(frame, seed))
         fr.render(clean, seed ^ 0xC0FFEE, frame)
         fr.splat()
         out = fr.reconstruct(logits, tm=self.tm)
@@ -183,7 +191,7 @@ class Renderer:
         for the backward), with the temporal term over warped[b]."""
         fr = self.frames[b]
         self.cur_params[b] = self.params(frame, seed)
-        fr.alloc(d, self.cur_params[b])
+        self._alloc(fr, d, self.cur_params[b])
         fr.render(clean, seed ^ 0xC0FFEE, frame)
         fr.splat()
         hats = self.hats[b]
@@ -273,10 +281,10 @@ class Trainer:
     def __init__(self, theta: torch.Tensor, batch: int, size: int, budget: float = 0.25,
                  lr: float = 1e-3, weight_decay: float = 1e-4, objective: str = "l1",
                  betas=(0.9, 0.999), random_tmo: bool = False, total_steps: int | None = None,
-                 seed: int = 0):
+                 seed: int = 0, dither_mask=None):
         import numpy as np
         self.net = Predictor(theta, batch, size, size, train=True)
-        self.rnd = Renderer(batch, size, size, budget)
+        self.rnd = Renderer(batch, size, size, budget, dither_mask)
         self.lr, self.wd = lr, weight_decay
         self.objective, self.betas, self.random_tmo = objective, betas, random_tmo
         self.total_steps = total_steps
@@ -322,14 +330,14 @@ class Trainer:
 
 def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None,
              fixed_logits: list[torch.Tensor] | None = None, seed: int = 99,
-             temporal: list | None = None) -> list[float]:
+             temporal: list | None = None, dither_mask=None) -> list[float]:
     """PSNR (tone-mapped sRGB against the tone-mapped clean image) of frame
     t of each sample.  theta None runs the plain method: uniform density
     d = 1 and the fixed logits (54 / 29 / 25 channels).  If ``temporal`` is
     a list, the temporal error mean |dI - dI_ref| of Eq. loss_temporal of
     each sample is appended to it."""
     W, H = samples[0].W, samples[0].H
-    rnd = Renderer(1, W, H, budget)
+    rnd = Renderer(1, W, H, budget, dither_mask)
     net = Predictor(theta, 1, W, H) if theta is not None else None
     ones = torch.ones(H, W, device="cuda")
     out = []

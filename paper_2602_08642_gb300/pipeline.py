@@ -66,6 +66,16 @@ class Frame:
                                        self.total, self.status, self.alloc_ws, stream),
                 "spp_alloc_sample_map")
 
+    def alloc_dithered(self, d: torch.Tensor, params: B.spp_params, mask: torch.Tensor,
+                       stream=None):
+        """alloc with the uniforms from a blue-noise rank mask (device int16
+        view of spp_blue_noise_mask's uint16 [T][T])."""
+        B.check(B.spp_alloc_sample_map_dithered(d, self.W, self.H, params, mask, self.counts,
+                                                self.offsets, self.sample_pixel, self.capacity,
+                                                self.s, self.holdout_w, self.total, self.status,
+                                                self.alloc_ws, stream),
+                "spp_alloc_sample_map_dithered")
+
     def render(self, clean: torch.Tensor, seed: int, frame: int, stream=None):
         B.check(B.spp_render_synthetic(clean, self.offsets, self.sample_pixel, self.total,
                                        self.capacity, self.W, self.H, seed, frame, self.rgb,

@@ -388,6 +388,12 @@ def test_frame_parity_4k_low_budget(spp):
     _frame_parity(spp, 3840, 2160, 3, 0.125, temporal=True, frame_index=2, seed=3)
 
 
+def test_frame_parity_1440p_five_levels(spp):
+    """The paper's five-level pyramid (Sec. 6.1, App. A) at 2560 x 1440 with
+    the temporal term (1440 / 16 = 90, so every level is whole)."""
+    _frame_parity(spp, 2560, 1440, 5, 0.25, temporal=True, frame_index=3, seed=4)
+
+
 def test_two_frame_sequence_feeds_back(spp):
     """Frame t+1 reprojects frame t's HDR output (red loop of Sec. 3): each
     side feeds back its own output."""
@@ -404,3 +410,45 @@ def test_two_frame_sequence_feeds_back(spp):
         torch.cuda.synchronize()
         assert_rel(host(out), ref["hdr"], rtol=2e-5 if t else RTOL, what=f"frame {t}")
         prev_gpu, prev_ref = out, ref["hdr"]
+
+
+# ---------------------------------------------------------------------------
+# Blue-noise dithered discretisation (Sec. 6.3)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("W,H,B,T", [(128, 128, 0.25, 64), (1000, 700, 0.37, 64),
+                                     (97, 61, 1.6, 16), (1920, 1080, 0.25, 64)])
+def test_alloc_dithered_bit_exact(spp, W, H, B, T):
+    import oracle.bluenoise as BN
+    d = inp.density_lognormal(W, H, seed=31)
+    mask = spp.binding.spp_blue_noise_mask(T, 0xB1)
+    params = spp.make_params(B, seed=0x5EED, frame=5)
+    fr = spp.Frame(W, H, 2, max_budget=B)
+    fr.clear_status()
+    mdev = torch.from_numpy(mask.view(np.int16)).cuda()
+    spp.check(spp.binding.spp_alloc_sample_map_dithered(
+        dev(d), W, H, params, mdev, fr.counts, fr.offsets, fr.sample_pixel, fr.capacity, fr.s,
+        fr.holdout_w, fr.total, fr.status, fr.alloc_ws))
+    torch.cuda.synchronize()
+    assert fr.check_status() == 0
+    u48 = BN.uniform48(BN.mask(T, 0xB1), W, H, seed=0x5EED, frame=5)
+    ref = oracle.alloc(d, B, u48=u48)
+    assert np.array_equal(host(fr.counts), ref.counts)
+    assert np.array_equal(host(fr.offsets)[:W * H + 1], ref.offsets)
+    assert int(fr.total.item()) == ref.T
+
+
+def test_alloc_dithered_constant_density_budget(spp):
+    """A constant density over whole tiles receives its budget to within one
+    sample per tile, frame after frame (white noise: hundreds off)."""
+    import oracle.bluenoise as BN
+    W = H = 256
+    T = 64
+    mask = torch.from_numpy(spp.binding.spp_blue_noise_mask(T, 3).view(np.int16)).cuda()
+    d = torch.ones(H, W, device="cuda")
+    fr = spp.Frame(W, H, 2, max_budget=0.5)
+    for frame in range(6):
+        params = spp.make_params(0.3, frame=frame)
+        spp.check(spp.binding.spp_alloc_sample_map_dithered(
+            d, W, H, params, mask, fr.counts, fr.offsets, fr.sample_pixel, fr.capacity, fr.s,
+            fr.holdout_w, fr.total, fr.status, fr.alloc_ws))
+        assert abs(int(fr.total.item()) - 0.3 * W * H) <= (W // T) * (H // T)
