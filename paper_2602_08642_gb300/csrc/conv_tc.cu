@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 #include "conv_src.cuh"
@@ -58,9 +59,9 @@ template <int N, bool RES>
 struct Cfg {
     static constexpr int TR = N <= 64 ? 4 : N <= 128 ? 2 : 1;  // rows per tile
     // bytes between the two 8-channel groups of a stage (the A operand's LBO):
-    // at least one group, and 64 mod 128 so that the two 16-byte halves of a
-    // pixel's 32 bytes, written by neighbouring threads, hit different banks
-    static constexpr int kKg = ((TR + 2) * kPitch * 16 - 64 + 127) / 128 * 128 + 64;
+    // one group rounded up to 128 bytes, so that each group's TMA box starts
+    // on a 128-byte boundary
+    static constexpr int kKg = ((TR + 2) * kPitch * 16 + 127) / 128 * 128;
     static constexpr int kA = 2 * kKg;                          // halo bytes per stage
     static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per K chunk
     static constexpr int kStage = RES ? kA : kA + kB;
@@ -108,6 +109,18 @@ static_assert(sizeof(Bars) <= kHeader, "header");
 
 __device__ __forceinline__ void named_bar_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+// TMA load of an NHWC halo box [1 group][TR+2 rows][130 px][8 ch] (5-D map:
+// channel-in-group, x, y, group, image) into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_halo(const CUtensorMap *map, void *dst, uint64_t *bar,
+                                              int x, int y, int g, int b) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(tc::smem_u32(bar)), "r"(0), "r"(x), "r"(y),
+        "r"(g), "r"(b)
+        : "memory");
+}
+
 // TMA tensor store of a [16][1][128] FP32 box from shared memory at (x, y, c, b).
 __device__ __forceinline__ void tma_store_planes(const CUtensorMap *map, const void *src, int x,
                                                  int y, int c, int b) {
@@ -129,7 +142,8 @@ __device__ __forceinline__ void tma_store_wait_all() {
 
 template <int N, bool RES>
 __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
-                                                             const __grid_constant__ CUtensorMap omap) {
+                                                             const __grid_constant__ CUtensorMap omap,
+                                                             const __grid_constant__ CUtensorMap imap) {
     using C = Cfg<N, RES>;
     constexpr int TR = C::TR, NS = C::kNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
-            tc::mbar_init(&bars.full[s], 128);
+            tc::mbar_init(&bars.full[s], a.tma_in ? 1 : 128);
             tc::mbar_init(&bars.wfull[s], 1);
             tc::mbar_init(&bars.empty[s], 1);
         }
@@ -234,7 +248,19 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 }
                 // task j -> 8-channel group j & 1 (fastest), then pixel, then row;
                 // shared-memory offset kg * kKg + (row * kPitch + px) * 16
-                if (async_src) {
+                if (a.tma_in) {
+                    // the halo of both 8-channel groups as two TMA boxes (zero fill
+                    // outside the image and beyond the channels)
+                    if (ptid == 0) {
+                        tc::mbar_arrive_expect_tx(&bars.full[s], 2 * 8 * kPitch * (TR + 2) * 2);
+#pragma unroll
+                        for (int kg = 0; kg < 2; ++kg)
+                            tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
+                                          2 * c + kg, b);
+                    }
+                    ++it;
+                    ++published;
+                } else if (async_src) {
                     const uint32_t sbase = tc::smem_u32(As);
 #pragma unroll
                     for (int u = 0; u < kPer; ++u) {
@@ -292,6 +318,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         for (; published < it; ++published) tc::mbar_arrive(&bars.full[published % NS]);
         if (!ok && ptid == 0) {
             // wait (bounded, ignoring the abort flag) for the copies still in flight
+            if (a.tma_in) {
+                const uint32_t first = it > NS ? it - NS : 0;
+                for (uint32_t k = first; k < it; ++k)
+                    (void)tc::mbar_wait(&bars.full[k % NS], (k / NS) & 1u, nullptr);
+            }
             if (RES) {
                 if (issued) (void)tc::mbar_wait(&bars.wfull[0], 0, nullptr);
             } else {
@@ -604,6 +635,16 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, int cin, int co
     }
 }
 
+// SPP_CONV_NO_TMA_IN=1 selects the cp.async halo producers instead of TMA
+// (comparison and fallback).
+bool getenv_disable_tma_in() {
+    static const bool off = [] {
+        const char *v = getenv("SPP_CONV_NO_TMA_IN");
+        return v && v[0] == '1';
+    }();
+    return off;
+}
+
 template <int N, bool RES>
 int launch_variant(const ConvArgs &a, cudaStream_t stream) {
     using C = Cfg<N, RES>;
@@ -641,7 +682,29 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             b.tma_out = 1;
     }
-    conv3x3_kernel<N, RES><<<grid, kThreads, C::kSmem, stream>>>(b, omap);
+    CUtensorMap imap;
+    memset(&imap, 0, sizeof(imap));
+    b.tma_in = 0;
+    if (a.src_mode == kSrcNHWC && a.c0 % 8 == 0 && !getenv_disable_tma_in()) {
+        // NHWC BF16 [B][H][W][c0] as 5-D (channel in group, x, y, group, image);
+        // box 8 x 130 x (TR+2) x 1 x 1 = one 8-channel group of the halo
+        auto enc = tensor_map_encoder();
+        const int groups = a.c0 / 8;
+        cuuint64_t dims[5] = {8, static_cast<cuuint64_t>(a.W), static_cast<cuuint64_t>(a.H),
+                              static_cast<cuuint64_t>(groups), static_cast<cuuint64_t>(a.B)};
+        cuuint64_t strides[4] = {static_cast<cuuint64_t>(a.c0) * 2,
+                                 static_cast<cuuint64_t>(a.W) * a.c0 * 2, 16,
+                                 static_cast<cuuint64_t>(a.H) * a.W * a.c0 * 2};
+        cuuint32_t box[5] = {8, static_cast<cuuint32_t>(kPitch), static_cast<cuuint32_t>(C::TR + 2),
+                             1, 1};
+        cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        if (enc && enc(&imap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(a.src0),
+                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            b.tma_in = 1;
+    }
+    conv3x3_kernel<N, RES><<<grid, kThreads, C::kSmem, stream>>>(b, omap, imap);
     count_launch();
     return launch_status();
 }
