@@ -135,7 +135,7 @@ class Renderer:
     def __init__(self, B_: int, W: int, H: int, budget: float, dither_mask=None):
         self.B, self.W, self.H, self.budget = B_, W, H, budget
         # blue-noise rank mask (device int16 [T][T]) or None for white noise
-        self.mask = dither_mask
+        self.dither = dither_mask
         self.frames = [Frame(W, H, LEVELS, max_budget=budget) for _ in range(B_)]
         self.tm = B.make_tonemap()
         self.hdr_prev = [_zeros(3, H, W) for _ in range(B_)]
@@ -163,8 +163,8 @@ class Renderer:
         self.tmp = _zeros(3, H, W)
 
     def _alloc(self, fr, d, params):
-        if self.mask is not None:
-            fr.alloc_dithered(d, params, self.mask)
+        if self.dither is not None:
+            fr.alloc_dithered(d, params, self.dither)
         else:
             fr.alloc(d, params)
 
