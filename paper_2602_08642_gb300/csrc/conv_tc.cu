@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
-            tc::mbar_init(&bars.full[s], a.tma_in ? 1 : 128);
+            tc::mbar_init(&bars.full[s], a.tma_in == 1 ? 1 : 128);
             tc::mbar_init(&bars.wfull[s], 1);
             tc::mbar_init(&bars.empty[s], 1);
         }
@@ -216,6 +216,14 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         const bool async_src = a.src_mode == kSrcNHWC || a.src_mode == kSrcConcatUp;
         constexpr uint32_t kLag = C::kLag;
         uint32_t published = 0;
+        // arrival for a cp.async stage whose copies have landed (TMA stages of
+        // an upsampling layer arrived when they were issued)
+        auto publish_lagged = [&](uint32_t k) {
+            const int ck = static_cast<int>(k % static_cast<uint32_t>(kchunks));
+            if (a.tma_in == 2 && ck * 16 < a.c0) return;
+            tc::fence_proxy_async();
+            tc::mbar_arrive(&bars.full[k % NS]);
+        };
         if (RES && ptid == 0) {
             // the whole packed weight operand, once
             tc::mbar_arrive_expect_tx(&bars.wfull[0], static_cast<uint32_t>(kchunks * C::kB));
@@ -248,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 }
                 // task j -> 8-channel group j & 1 (fastest), then pixel, then row;
                 // shared-memory offset kg * kKg + (row * kPitch + px) * 16
-                if (a.tma_in) {
+                if (a.tma_in == 1) {
                     // the halo of both 8-channel groups as two TMA boxes (zero fill
                     // outside the image and beyond the channels)
                     if (ptid == 0) {
@@ -260,6 +268,26 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     }
                     ++it;
                     ++published;
+                } else if (a.tma_in == 2 && c * 16 < a.c0) {
+                    // upsampling layer, skip-connection chunk: TMA as above, every
+                    // producer arrives now; an empty copy group keeps the count of
+                    // groups equal to the count of stages for the lagged ones
+                    if (ptid == 0) {
+                        tc::mbar_arrive_expect_tx(&bars.full[s], 2 * 8 * kPitch * (TR + 2) * 2);
+#pragma unroll
+                        for (int kg = 0; kg < 2; ++kg)
+                            tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
+                                          2 * c + kg, b);
+                    } else {
+                        tc::mbar_arrive(&bars.full[s]);
+                    }
+                    cp_async_commit();
+                    ++it;
+                    if (it > kLag) {
+                        cp_async_wait<kLag>();
+                        publish_lagged(published);
+                        ++published;
+                    }
                 } else if (async_src) {
                     const uint32_t sbase = tc::smem_u32(As);
 #pragma unroll
@@ -275,8 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     ++it;
                     if (it > kLag) {
                         cp_async_wait<kLag>();
-                        tc::fence_proxy_async();
-                        tc::mbar_arrive(&bars.full[published % NS]);
+                        publish_lagged(published);
                         ++published;
                     }
                 } else {
@@ -314,11 +341,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         // publish the stages still in flight (also on the abort path, where the
         // copies must land before the CTA exits)
         cp_async_wait<0>();
-        tc::fence_proxy_async();
-        for (; published < it; ++published) tc::mbar_arrive(&bars.full[published % NS]);
+        for (; published < it; ++published) publish_lagged(published);
         if (!ok && ptid == 0) {
             // wait (bounded, ignoring the abort flag) for the copies still in flight
-            if (a.tma_in) {
+            if (a.tma_in == 1) {
                 const uint32_t first = it > NS ? it - NS : 0;
                 for (uint32_t k = first; k < it; ++k)
                     (void)tc::mbar_wait(&bars.full[k % NS], (k / NS) & 1u, nullptr);
@@ -685,7 +711,8 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
     CUtensorMap imap;
     memset(&imap, 0, sizeof(imap));
     b.tma_in = 0;
-    if (a.src_mode == kSrcNHWC && a.c0 % 8 == 0 && !getenv_disable_tma_in()) {
+    if ((a.src_mode == kSrcNHWC || (a.src_mode == kSrcConcatUp && a.c0 % 16 == 0)) &&
+        a.c0 % 8 == 0 && !getenv_disable_tma_in()) {
         // NHWC BF16 [B][H][W][c0] as 5-D (channel in group, x, y, group, image);
         // box 8 x 130 x (TR+2) x 1 x 1 = one 8-channel group of the halo
         auto enc = tensor_map_encoder();
@@ -702,7 +729,7 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-            b.tma_in = 1;
+            b.tma_in = a.src_mode == kSrcNHWC ? 1 : 2;
     }
     conv3x3_kernel<N, RES><<<grid, kThreads, C::kSmem, stream>>>(b, omap, imap);
     count_launch();

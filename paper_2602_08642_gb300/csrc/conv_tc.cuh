@@ -48,7 +48,8 @@ struct ConvArgs {
     // to pool_out [B][H/2][W/2][n] (H and W even)
     __nv_bfloat16 *pool_out = nullptr;
     int tma_out = 0;  // set by the launcher: FP32 planar output through TMA stores
-    int tma_in = 0;   // set by the launcher: NHWC halo through TMA loads
+    int tma_in = 0;   // set by the launcher: NHWC halo through TMA loads (1), or only the
+                      // skip-connection chunks of an upsampling layer (2)
     int32_t *status = nullptr;
 };
 
