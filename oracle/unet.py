@@ -53,34 +53,61 @@ import math
 
 import numpy as np
 
-# (name, cin, cout, relu)
-LAYERS = [
-    ("e0a", 12, 32, True), ("e0b", 32, 32, True),
-    ("e1a", 32, 64, True), ("e1b", 64, 64, True),
-    ("e2a", 64, 128, True), ("e2b", 128, 128, True),
-    ("h2", 128, 25, False),
-    ("d1a", 192, 64, True), ("d1b", 64, 64, True),
-    ("h1", 64, 29, False),
-    ("d0a", 96, 32, True), ("d0b", 32, 32, True),
-    ("h0", 32, 55, False),
-]
+# Network specifications: input channels and the output channels of the
+# three heads (h0 at level 0, h1 at level 1, h2 at level 2; 0 = absent).
+#   joint     the single predictor of density and kernels (12 inputs; h0 =
+#             54 logits + density logit)
+#   sampler   the first stage of the two-stage pipeline (Sec. 3): G-buffer,
+#             warped previous output and warped latents -> density logit
+#   denoiser  the second stage: noisy radiance, s and n, G-buffer, warped
+#             previous HDR output and latents -> 54 logits, 3 demodulation
+#             channels (Sec. 6.2) and 7 latent channels at level 0; 29 and 25
+#             logits at levels 1 and 2
+N_LATENT = 7
+SPECS = {
+    "joint": (12, (55, 29, 25)),
+    "sampler": (12 + N_LATENT, (1, 0, 0)),
+    "denoiser": (17 + N_LATENT, (64, 29, 25)),
+}
+DEMOD_CHANNELS = slice(54, 57)
+LATENT_CHANNELS = slice(57, 57 + N_LATENT)
+DEMOD_CLAMP = 8.0
+
+
+def layers(spec: str = "joint"):
+    """[(name, cin, cout, relu)] of a network specification (absent heads
+    are left out; the order is the parameter order)."""
+    cin, (c0, c1, c2) = SPECS[spec]
+    out = [("e0a", cin, 32, True), ("e0b", 32, 32, True),
+           ("e1a", 32, 64, True), ("e1b", 64, 64, True),
+           ("e2a", 64, 128, True), ("e2b", 128, 128, True)]
+    if c2:
+        out.append(("h2", 128, c2, False))
+    out += [("d1a", 192, 64, True), ("d1b", 64, 64, True)]
+    if c1:
+        out.append(("h1", 64, c1, False))
+    out += [("d0a", 96, 32, True), ("d0b", 32, 32, True), ("h0", 32, c0, False)]
+    return out
+
+
+LAYERS = layers("joint")
 N_FEATURES = 12
 DENSITY_CHANNEL = 54
 
 
-def param_offsets():
+def param_offsets(spec: str = "joint"):
     """[(name, cin, cout, w_offset, b_offset)], total parameter count."""
     out, off = [], 0
-    for name, cin, cout, _ in LAYERS:
+    for name, cin, cout, _ in layers(spec):
         out.append((name, cin, cout, off, off + cout * cin * 9))
         off += cout * cin * 9 + cout
     return out, off
 
 
-def unpack(theta):
+def unpack(theta, spec: str = "joint"):
     """dict name -> (W [cout][cin][3][3] FP64, b [cout] FP64)."""
     theta = np.asarray(theta, np.float64)
-    table, total = param_offsets()
+    table, total = param_offsets(spec)
     assert theta.size == total
     return {name: (theta[wo:bo].reshape(cout, cin, 3, 3), theta[bo:bo + cout])
             for name, cin, cout, wo, bo in table}
@@ -154,12 +181,13 @@ def up2_backward(g):
 
 
 # ---------------------------------------------------------------- network
-def forward(theta, x, round_bf16_acts: bool = False):
-    """Forward pass on one image x [12][H][W] (H, W divisible by 4).
+def forward(theta, x, round_bf16_acts: bool = False, spec: str = "joint"):
+    """Forward pass on one image x [cin][H][W] (H, W divisible by 4).
 
-    Returns a dict with z [H][W], logits [l0 [54][H][W], l1 [29][H/2][W/2],
-    l2 [25][H/4][W/4]] and the cache needed by :func:`backward`."""
-    P = unpack(theta)
+    Returns a dict with heads [h0 [c0][H][W], h1 [c1][H/2][W/2] or None,
+    h2 [c2][H/4][W/4] or None] and the cache needed by :func:`backward`;
+    for the joint network also z [H][W] and logits [l0 [54][H][W], l1, l2]."""
+    P = unpack(theta, spec)
     rnd = round_bf16 if round_bf16_acts else (lambda a: a)
     if round_bf16_acts:
         P = {k: (round_bf16(w), b) for k, (w, b) in P.items()}
@@ -175,22 +203,26 @@ def forward(theta, x, round_bf16_acts: bool = False):
         return y
 
     x = rnd(np.asarray(x, np.float64))
+    assert x.shape[0] == SPECS[spec][0]
     s0 = layer("e0b", layer("e0a", x))
     s1 = layer("e1b", layer("e1a", rnd(pool2(s0))))
     bt = layer("e2b", layer("e2a", rnd(pool2(s1))))
-    l2 = layer("h2", bt, relu=False)
+    l2 = layer("h2", bt, relu=False) if "h2" in P else None
     t1 = layer("d1b", layer("d1a", np.concatenate([s1, up2(bt)])))
-    l1 = layer("h1", t1, relu=False)
+    l1 = layer("h1", t1, relu=False) if "h1" in P else None
     t0 = layer("d0b", layer("d0a", np.concatenate([s0, up2(t1)])))
     h0 = layer("h0", t0, relu=False)
-    return dict(z=h0[DENSITY_CHANNEL], logits=[h0[:DENSITY_CHANNEL], l1, l2], cache=cache,
-                params=P)
+    out = dict(heads=[h0, l1, l2], cache=cache, params=P, spec=spec)
+    if spec == "joint":
+        out.update(z=h0[DENSITY_CHANNEL], logits=[h0[:DENSITY_CHANNEL], l1, l2])
+    return out
 
 
-def backward(fwd, g_logits, g_z):
-    """Gradient of sum_l <g_logits[l], logits[l]> + <g_z, z> with respect to
-    theta (flat, the layout of :func:`param_offsets`), in FP64."""
-    P, cache = fwd["params"], fwd["cache"]
+def backward_heads(fwd, g_heads, input_grad: bool = False):
+    """Gradient of sum_k <g_heads[k], heads[k]> with respect to theta (flat,
+    the layout of :func:`param_offsets`), in FP64; with input_grad also the
+    gradient with respect to the input x (returned as (g_theta, g_x))."""
+    P, cache, spec = fwd["params"], fwd["cache"], fwd["spec"]
     grads = {}
 
     def back(name, g_out, relu=True):
@@ -200,27 +232,37 @@ def backward(fwd, g_logits, g_z):
         grads[name] = (gw, gb)
         return gx
 
-    g_h0 = np.concatenate([np.asarray(g_logits[0], np.float64),
-                           np.asarray(g_z, np.float64)[None]])
-    g_t0 = back("h0", g_h0, relu=False)
+    g_t0 = back("h0", np.asarray(g_heads[0], np.float64), relu=False)
     g_cat0 = back("d0a", back("d0b", g_t0))
     c_s0 = cache["e0b.out"].shape[0]
     g_s0 = g_cat0[:c_s0]
-    g_t1 = up2_backward(g_cat0[c_s0:]) + back("h1", np.asarray(g_logits[1], np.float64), relu=False)
+    g_t1 = up2_backward(g_cat0[c_s0:])
+    if "h1" in P:
+        g_t1 = g_t1 + back("h1", np.asarray(g_heads[1], np.float64), relu=False)
     g_cat1 = back("d1a", back("d1b", g_t1))
     c_s1 = cache["e1b.out"].shape[0]
     g_s1 = g_cat1[:c_s1]
-    g_b = up2_backward(g_cat1[c_s1:]) + back("h2", np.asarray(g_logits[2], np.float64), relu=False)
+    g_b = up2_backward(g_cat1[c_s1:])
+    if "h2" in P:
+        g_b = g_b + back("h2", np.asarray(g_heads[2], np.float64), relu=False)
     g_s1 = g_s1 + pool2_backward(back("e2a", back("e2b", g_b)))
     g_s0 = g_s0 + pool2_backward(back("e1a", back("e1b", g_s1)))
-    back("e0a", back("e0b", g_s0))
-    table, total = param_offsets()
+    g_x = back("e0a", back("e0b", g_s0))
+    table, total = param_offsets(spec)
     out = np.empty(total)
     for name, cin, cout, wo, bo in table:
         gw, gb = grads[name]
         out[wo:bo] = gw.ravel()
         out[bo:bo + cout] = gb
-    return out
+    return (out, g_x) if input_grad else out
+
+
+def backward(fwd, g_logits, g_z):
+    """Joint network: gradient of sum_l <g_logits[l], logits[l]> + <g_z, z>
+    with respect to theta."""
+    g_h0 = np.concatenate([np.asarray(g_logits[0], np.float64),
+                           np.asarray(g_z, np.float64)[None]])
+    return backward_heads(fwd, [g_h0, g_logits[1], g_logits[2]])
 
 
 def density(z):
