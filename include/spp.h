@@ -523,6 +523,135 @@ int spp_adamw_step(float *theta, const float *grad, float *m, float *v, int64_t 
                    float lr, float beta1, float beta2, float eps, float weight_decay,
                    float grad_scale, cudaStream_t stream);
 
+/* ------------------------- f1: two-stage pipeline (sampler + denoiser) */
+/*
+ * The paper's full pipeline (Sec. 3, Sec. 6.2 "Learned Demodulation",
+ * Sec. 6.3): a sampler network predicts the density before rendering; after
+ * rendering a denoiser network sees the noisy radiance, the sample maps, the
+ * G-buffer, the previous HDR output and latent features, and predicts the
+ * gather-kernel logits, a 3-channel demodulation map and the latents that
+ * both networks read (warped) in the next frame.  The paper prints neither
+ * layer tables nor input encodings; this library's reading:
+ *
+ * Networks (same U-Net trunk as the joint predictor above, layer slots
+ * 0..12 of spp_unet_layer; a network without h1 / h2 leaves those slots
+ * empty, cout = 0, and has no parameters for them):
+ *   SPP_NET_JOINT     12 inputs; h0 55 (54 logits + density logit), h1 29, h2 25
+ *   SPP_NET_SAMPLER   19 inputs: the 12 joint features, then the 7 warped
+ *                     latents; h0 = 1 (density logit z)
+ *   SPP_NET_DENOISER  24 inputs: ln(1+L^0) [3], ln(1+s), ln(1+n), albedo [3],
+ *                     normal [3], ln(depth)/ln(100), motion/8 [2],
+ *                     ln(1 + W_t L_{t-1}) [3], warped latents [7];
+ *                     h0 = 64 planes: 54 kernel logits, 3 raw demodulation
+ *                     channels c (planes 54..56), 7 raw latents (57..63);
+ *                     h1 29, h2 25
+ * Demodulation map m = exp(clamp(c, -8, 8)); latents passed on = tanh of
+ * their raw planes.  Frame with demodulation:
+ *   hdr = m * R(pyramid(L^0 / m), W_t L_{t-1} / m, kernel logits)
+ * where R is the gather pyramid (spp_reconstruct_level, levels L-1 .. 0).
+ */
+#define SPP_NET_JOINT 0
+#define SPP_NET_SAMPLER 1
+#define SPP_NET_DENOISER 2
+#define SPP_LATENT_CHANNELS 7
+#define SPP_DEMOD_PLANE 54
+#define SPP_LATENT_PLANE 57
+
+/* Input channels and head widths (0 = absent) of network `net`. */
+int spp_net_spec(int net, int *cin, int *head0, int *head1, int *head2);
+/* Shape of layer slot i (0..12) of network `net` (cout 0: absent head). */
+int spp_net_layer(int net, int i, int *cin, int *cout, int *relu);
+/* FP32 parameters of network `net` (-1 for an unknown net). */
+int64_t spp_net_param_count(int net);
+/* Packed blob bytes / packing, as spp_unet_packed_bytes / spp_unet_pack. */
+size_t spp_net_packed_bytes(int net, int with_backward);
+int spp_net_pack(int net, const float *theta, int with_backward, void *packed,
+                 size_t packed_bytes, cudaStream_t stream);
+/* Forward workspace bytes (activations kept for the backward). */
+size_t spp_net_workspace_bytes(int net, int B, int W, int H);
+/* Forward on B frames (W, H divisible by 4): in [B][cin][H][W] FP32;
+ * head0 [B][h0][H][W], head1 [B][h1][H/2][W/2], head2 [B][h2][H/4][W/4]
+ * FP32 planar (NULL allowed for an absent head). */
+int spp_net_forward(int net, const void *packed, const float *in, int B, int W, int H,
+                    float *head0, float *head1, float *head2, void *ws, size_t ws_bytes,
+                    int32_t *status, cudaStream_t stream);
+size_t spp_net_backward_workspace_bytes(int net, int B, int W, int H);
+/* Backward of spp_net_forward: grad_theta (OVERWRITTEN) from the head
+ * gradients (same shapes as the heads); if grad_in is not NULL also the
+ * gradient with respect to the input, [B][cin][H][W] FP32 (OVERWRITTEN; the
+ * BF16 rounding of the input counts as the identity).  fwd_ws: the
+ * workspace of the forward call. */
+int spp_net_backward(int net, const void *packed, int B, int W, int H, const void *fwd_ws,
+                     size_t fwd_ws_bytes, const float *grad_head0, const float *grad_head1,
+                     const float *grad_head2, float *grad_theta, float *grad_in, void *ws,
+                     size_t ws_bytes, int32_t *status, cudaStream_t stream);
+
+/* Unnormalised spatial softmax of a density logit plane per frame:
+ * density[b][i] = exp(z[b * batch_stride + i] - max_i z[b * batch_stride + i])
+ * (Sec. 3); ws holds B words. */
+size_t spp_density_softmax_workspace_bytes(int B);
+int spp_density_softmax(const float *z, int B, int W, int H, int64_t batch_stride,
+                        float *density, void *ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Latents of frame t-1 for frame t: out[k] = W_t tanh(raw[k]) for the 7
+ * raw latent planes of the previous denoiser (raw [7][H][W], usually head0
+ * + 57 planes), bilinear along mv like spp_warp_previous. */
+int spp_warp_latent(const float *raw, const float *mv, int W, int H, float *out,
+                    cudaStream_t stream);
+
+/* Sampler input in19 [19][H][W]: the 12 channels of spp_assemble_features,
+ * then warped_latent [7][H][W] (NULL: zeros, the first frame). */
+int spp_assemble_sampler_features(const float *albedo, const float *normal, const float *depth,
+                                  const float *mv, const float *warped_prev_ldr,
+                                  const float *warped_latent, int W, int H, float *in19,
+                                  cudaStream_t stream);
+
+/* Denoiser input in24 [24][H][W] from the splatted radiance L0 [3][H][W],
+ * the sample map s [H][W] and counts [H][W] (spp_alloc_sample_map), the
+ * G-buffer, mv, the previous HDR output warped to this frame
+ * (warped_prev_hdr [3][H][W], NULL: zeros) and the warped latents (NULL:
+ * zeros), in the channel order given above. */
+int spp_assemble_denoiser_features(const float *L0, const float *s, const int32_t *counts,
+                                   const float *albedo, const float *normal, const float *depth,
+                                   const float *mv, const float *warped_prev_hdr,
+                                   const float *warped_latent, int W, int H, float *in24,
+                                   cudaStream_t stream);
+
+/* Adds the gradient reaching L0 and s through the denoiser input:
+ * grad_L0 += grad_in24[0..2] / (1 + L0), grad_s += grad_in24[3] / (1 + s);
+ * either output may be NULL (skipped), so that the L0 part can be added
+ * before spp_splat_backward (which overwrites grad_s) and the s part after. */
+int spp_denoiser_features_backward(const float *L0, const float *s, const float *grad_in24,
+                                   int W, int H, float *grad_L0, float *grad_s,
+                                   cudaStream_t stream);
+
+/* Demodulation (Sec. 6.2): m = exp(clamp(c, -8, 8)) ([3][H][W], written to
+ * m), layers[0] = L0 / m and layers[l] (l < L) the 2^l x 2^l block means of
+ * layers[0] (Eq. app-pyramid); if warped is not NULL, warped_out = warped /
+ * m.  W, H divisible by 2^(L-1), 1 <= L <= 5. */
+int spp_demodulate(const float *L0, const float *c, const float *warped, int W, int H, int L,
+                   float *m, float *const *layers, float *warped_out, cudaStream_t stream);
+
+/* Remodulation and tone map: out_hdr = m * R ([3][H][W]), out_ldr =
+ * tau-sRGB of out_hdr (tm as spp_reconstruct_level; out_ldr may be NULL). */
+int spp_remodulate_tonemap(const float *R, const float *m, int W, int H, const spp_tonemap *tm,
+                           float *out_hdr, float *out_ldr, cudaStream_t stream);
+
+/* Backward of the remodulation into the reconstruction: grad_R = grad_out * m. */
+int spp_remodulate_backward(const float *grad_out, const float *m, int W, int H, float *grad_R,
+                            cudaStream_t stream);
+
+/* Backward of the demodulation: from grad_out (w.r.t. out_hdr), grad_L0d
+ * (w.r.t. layers[0], after spp_pyramid_backward folded the coarser levels
+ * in) and grad_Wd (w.r.t. warped_out; NULL with Wd NULL), writes
+ *   grad_L0 = grad_L0d / m
+ *   grad_c  = (grad_out out_hdr - grad_L0d L0d - grad_Wd Wd) [|c| < 8]
+ * (both OVERWRITTEN). */
+int spp_demodulate_backward(const float *out_hdr, const float *grad_out, const float *L0d,
+                            const float *grad_L0d, const float *Wd, const float *grad_Wd,
+                            const float *c, const float *m, int W, int H, float *grad_L0,
+                            float *grad_c, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

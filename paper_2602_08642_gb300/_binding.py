@@ -113,6 +113,28 @@ _SIGS = {
                                            _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "spp_combined_loss": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float, _P, _P,
                                _P]),
+    "spp_net_spec": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                          ctypes.POINTER(_I)]),
+    "spp_net_layer": (_I, [_I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "spp_net_param_count": (_I64, [_I]),
+    "spp_net_packed_bytes": (_SZ, [_I, _I]),
+    "spp_net_pack": (_I, [_I, _P, _I, _P, _SZ, _P]),
+    "spp_net_workspace_bytes": (_SZ, [_I, _I, _I, _I]),
+    "spp_net_forward": (_I, [_I, _P, _P, _I, _I, _I, _P, _P, _P, _P, _SZ, _P, _P]),
+    "spp_net_backward_workspace_bytes": (_SZ, [_I, _I, _I, _I]),
+    "spp_net_backward": (_I, [_I, _P, _I, _I, _I, _P, _SZ, _P, _P, _P, _P, _P, _P, _SZ, _P,
+                              _P]),
+    "spp_density_softmax_workspace_bytes": (_SZ, [_I]),
+    "spp_density_softmax": (_I, [_P, _I, _I, _I, _I64, _P, _P, _SZ, _P]),
+    "spp_warp_latent": (_I, [_P, _P, _I, _I, _P, _P]),
+    "spp_assemble_sampler_features": (_I, [_P, _P, _P, _P, _P, _P, _I, _I, _P, _P]),
+    "spp_assemble_denoiser_features": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P,
+                                            _P]),
+    "spp_denoiser_features_backward": (_I, [_P, _P, _P, _I, _I, _P, _P, _P]),
+    "spp_demodulate": (_I, [_P, _P, _P, _I, _I, _I, _P, _P, _P, _P]),
+    "spp_remodulate_tonemap": (_I, [_P, _P, _I, _I, ctypes.POINTER(spp_tonemap), _P, _P, _P]),
+    "spp_remodulate_backward": (_I, [_P, _P, _I, _I, _P, _P]),
+    "spp_demodulate_backward": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -450,3 +472,131 @@ def spp_alloc_sample_map_dithered(d, W, H, params: spp_params, mask, counts, off
         _dev(sample_pixel, torch.int32), int(capacity), _dev(s_out, torch.float32),
         _dev(holdout_w, torch.float32), _dev(total, torch.int64), _dev(status, torch.int32),
         _dev(ws), _nbytes(ws), _stream(stream))
+
+
+# ------------------------------------------- f1: two-stage pipeline
+SPP_NET_JOINT = 0
+SPP_NET_SAMPLER = 1
+SPP_NET_DENOISER = 2
+SPP_LATENT_CHANNELS = 7
+SPP_DEMOD_PLANE = 54
+SPP_LATENT_PLANE = 57
+
+
+def spp_net_spec(net: int):
+    """(cin, (h0, h1, h2)) of network `net`."""
+    a, b, c, d = _I(), _I(), _I(), _I()
+    check(lib.spp_net_spec(net, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                           ctypes.byref(d)), "spp_net_spec")
+    return a.value, (b.value, c.value, d.value)
+
+
+def spp_net_layer(net: int, i: int):
+    a, b, c = _I(), _I(), _I()
+    check(lib.spp_net_layer(net, i, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "spp_net_layer")
+    return a.value, b.value, c.value
+
+
+def spp_net_param_count(net: int) -> int:
+    return int(lib.spp_net_param_count(net))
+
+
+def spp_net_packed_bytes(net: int, with_backward: bool) -> int:
+    return int(lib.spp_net_packed_bytes(net, int(with_backward)))
+
+
+def spp_net_pack(net, theta, with_backward, packed, stream=None) -> int:
+    return lib.spp_net_pack(net, _dev(theta, torch.float32), int(with_backward), _dev(packed),
+                            _nbytes(packed), _stream(stream))
+
+
+def spp_net_workspace_bytes(net: int, B: int, W: int, H: int) -> int:
+    return int(lib.spp_net_workspace_bytes(net, B, W, H))
+
+
+def spp_net_forward(net, packed, x, B, W, H, head0, head1, head2, ws, status, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_net_forward(net, _dev(packed), _dev(x, f), B, W, H, _dev(head0, f),
+                               _dev(head1, f), _dev(head2, f), _dev(ws), _nbytes(ws),
+                               _dev(status, torch.int32), _stream(stream))
+
+
+def spp_net_backward_workspace_bytes(net: int, B: int, W: int, H: int) -> int:
+    return int(lib.spp_net_backward_workspace_bytes(net, B, W, H))
+
+
+def spp_net_backward(net, packed, B, W, H, fwd_ws, g0, g1, g2, grad_theta, grad_in, ws, status,
+                     stream=None) -> int:
+    f = torch.float32
+    return lib.spp_net_backward(net, _dev(packed), B, W, H, _dev(fwd_ws), _nbytes(fwd_ws),
+                                _dev(g0, f), _dev(g1, f), _dev(g2, f), _dev(grad_theta, f),
+                                _dev(grad_in, f), _dev(ws), _nbytes(ws), _dev(status, torch.int32),
+                                _stream(stream))
+
+
+def spp_density_softmax_workspace_bytes(B: int) -> int:
+    return int(lib.spp_density_softmax_workspace_bytes(B))
+
+
+def spp_density_softmax(z, B, W, H, batch_stride, density, ws, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_density_softmax(_dev(z, f), B, W, H, int(batch_stride), _dev(density, f),
+                                   _dev(ws), _nbytes(ws), _stream(stream))
+
+
+def spp_warp_latent(raw, mv, W, H, out, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_warp_latent(_dev(raw, f), _dev(mv, f), W, H, _dev(out, f), _stream(stream))
+
+
+def spp_assemble_sampler_features(albedo, normal, depth, mv, warped_prev_ldr, warped_latent, W, H,
+                                  in19, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_assemble_sampler_features(_dev(albedo, f), _dev(normal, f), _dev(depth, f),
+                                             _dev(mv, f), _dev(warped_prev_ldr, f),
+                                             _dev(warped_latent, f), W, H, _dev(in19, f),
+                                             _stream(stream))
+
+
+def spp_assemble_denoiser_features(L0, s, counts, albedo, normal, depth, mv, warped_prev_hdr,
+                                   warped_latent, W, H, in24, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_assemble_denoiser_features(
+        _dev(L0, f), _dev(s, f), _dev(counts, torch.int32), _dev(albedo, f), _dev(normal, f),
+        _dev(depth, f), _dev(mv, f), _dev(warped_prev_hdr, f), _dev(warped_latent, f), W, H,
+        _dev(in24, f), _stream(stream))
+
+
+def spp_denoiser_features_backward(L0, s, grad_in24, W, H, grad_L0, grad_s, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_denoiser_features_backward(_dev(L0, f), _dev(s, f), _dev(grad_in24, f), W, H,
+                                              _dev(grad_L0, f), _dev(grad_s, f), _stream(stream))
+
+
+def spp_demodulate(L0, c, warped, W, H, L, m, layers, warped_out, stream=None) -> int:
+    f = torch.float32
+    arr = _ptr_array(layers[:L], f)
+    return lib.spp_demodulate(_dev(L0, f), _dev(c, f), _dev(warped, f), W, H, L, _dev(m, f),
+                              ctypes.cast(arr, _P), _dev(warped_out, f), _stream(stream))
+
+
+def spp_remodulate_tonemap(R, m, W, H, tm, out_hdr, out_ldr, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_remodulate_tonemap(_dev(R, f), _dev(m, f), W, H, ctypes.byref(tm),
+                                      _dev(out_hdr, f), _dev(out_ldr, f), _stream(stream))
+
+
+def spp_remodulate_backward(grad_out, m, W, H, grad_R, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_remodulate_backward(_dev(grad_out, f), _dev(m, f), W, H, _dev(grad_R, f),
+                                       _stream(stream))
+
+
+def spp_demodulate_backward(out_hdr, grad_out, L0d, grad_L0d, Wd, grad_Wd, c, m, W, H, grad_L0,
+                            grad_c, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_demodulate_backward(_dev(out_hdr, f), _dev(grad_out, f), _dev(L0d, f),
+                                       _dev(grad_L0d, f), _dev(Wd, f), _dev(grad_Wd, f),
+                                       _dev(c, f), _dev(m, f), W, H, _dev(grad_L0, f),
+                                       _dev(grad_c, f), _stream(stream))

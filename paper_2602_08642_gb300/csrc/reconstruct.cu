@@ -174,6 +174,12 @@ __global__ void tonemap_image_kernel(const float *__restrict__ hdr, int64_t n,
     }
 }
 
+size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
+
+}  // namespace
+
+// Tone-map arguments of a call (defaults when tm is NULL) and their check;
+// also used by the two-stage pipeline's remodulation.
 ToneArgs tone_args(const spp_tonemap *tm) {
     ToneArgs t{1.0f, 1.0f, 0.0f, 0.5f, 0.5f, 2.0f, 2.0f};
     if (tm) {
@@ -193,9 +199,6 @@ bool tone_ok(const ToneArgs &t) {
            t.beta == t.beta && t.k == t.k;
 }
 
-size_t align256(size_t v) { return (v + 255) & ~static_cast<size_t>(255); }
-
-}  // namespace
 }  // namespace spp
 
 extern "C" {

@@ -14,46 +14,81 @@
 namespace spp {
 namespace unet {
 
-const Layer kLayers[kNumLayers] = {
-    {12, 32, 1},  {32, 32, 1},  {32, 64, 1}, {64, 64, 1}, {64, 128, 1},
-    {128, 128, 1}, {128, 25, 0}, {192, 64, 1}, {64, 64, 1}, {64, 29, 0},
-    {96, 32, 1},  {32, 32, 1},  {32, 55, 0},
+const NetSpec kNets[kNumNets] = {
+    {12, {55, 29, 25}},  // joint predictor
+    {19, {1, 0, 0}},     // sampler
+    {24, {64, 29, 25}},  // denoiser
 };
+
+Layer layer(int net, int i) {
+    static const Layer trunk[kNumLayers] = {
+        {0, 32, 1},    {32, 32, 1}, {32, 64, 1}, {64, 64, 1}, {64, 128, 1},
+        {128, 128, 1}, {128, 0, 0}, {192, 64, 1}, {64, 64, 1}, {64, 0, 0},
+        {96, 32, 1},   {32, 32, 1}, {32, 0, 0},
+    };
+    Layer l = trunk[i];
+    const NetSpec &n = kNets[net];
+    if (i == E0A) l.cin = n.cin;
+    if (i == H0) l.cout = n.heads[0];
+    if (i == H1) l.cout = n.heads[1];
+    if (i == H2) l.cout = n.heads[2];
+    return l;
+}
+
+int level_of(int i) {
+    return (i == E1A || i == E1B || i == D1A || i == D1B || i == H1) ? 1
+           : (i == E2A || i == E2B || i == H2)                       ? 2
+                                                                     : 0;
+}
 
 int round16(int c) { return (c + 15) / 16 * 16; }
 
+int input_channels_padded(int net) { return round16(kNets[net].cin); }
+
 // MMA width of a layer's forward convolution (its output channels, padded).
-int fwd_n(int i) { return kLayers[i].relu ? kLayers[i].cout : (kLayers[i].cout <= 32 ? 32 : 64); }
+int fwd_n(int net, int i) {
+    const Layer l = layer(net, i);
+    return l.relu ? l.cout : (l.cout <= 32 ? 32 : 64);
+}
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-PackedLayout packed_layout(int with_backward) {
+PackedLayout packed_layout(int net, int with_backward) {
     PackedLayout L{};
     size_t off = 0;
     int64_t toff = 0;
     for (int i = 0; i < kNumLayers; ++i) {
-        const Layer &l = kLayers[i];
+        const Layer l = layer(net, i);
+        if (l.cout == 0) {
+            L.theta_w[i] = L.theta_b[i] = toff;
+            L.fwd[i] = L.bias[i] = 0;
+            continue;
+        }
         L.theta_w[i] = toff;
         L.theta_b[i] = toff + static_cast<int64_t>(l.cout) * l.cin * 9;
         toff = L.theta_b[i] + l.cout;
         L.fwd[i] = off;
-        off = align256(off + conv::packed_bytes(round16(l.cin), fwd_n(i)));
+        off = align256(off + conv::packed_bytes(round16(l.cin), fwd_n(net, i)));
         L.bias[i] = off;
-        off = align256(off + sizeof(float) * fwd_n(i));
+        off = align256(off + sizeof(float) * fwd_n(net, i));
     }
     L.param_count = toff;
     for (int i = 0; i < kNumLayers; ++i) {
+        const Layer l = layer(net, i);
         L.bwd[i] = 0;
-        if (with_backward && i > 0) {  // no data gradient is needed for the input layer
+        if (with_backward && l.cout > 0) {
+            // data-gradient operand: input channels = this layer's outputs,
+            // MMA width = its inputs (the input layer's padded to 16 / 32)
             L.bwd[i] = off;
-            off = align256(off + conv::packed_bytes(round16(kLayers[i].cout), kLayers[i].cin));
+            off = align256(off + conv::packed_bytes(round16(l.cout),
+                                                    i == E0A ? round16(l.cin) : l.cin));
         }
     }
     L.total = off;
     return L;
 }
 
-ActLayout act_layout(int B, int W, int H) {
+ActLayout act_layout(int net, int B, int W, int H) {
     ActLayout A{};
     const size_t p0 = static_cast<size_t>(B) * H * W, p1 = p0 / 4, p2 = p0 / 16;
     size_t off = 0;
@@ -62,7 +97,8 @@ ActLayout act_layout(int B, int W, int H) {
         off = align256(off + elems * sizeof(__nv_bfloat16));
         return o;
     };
-    A.x16 = take(p0 * 16);
+    A.xin_c = input_channels_padded(net);
+    A.xin = take(p0 * A.xin_c);
     A.e0a = take(p0 * 32);
     A.s0 = take(p0 * 32);
     A.p0 = take(p1 * 32);
@@ -126,6 +162,27 @@ __global__ void features_nhwc16_kernel(const float *__restrict__ in12, int64_t n
     }
 }
 
+// in [B][C][H][W] FP32 -> BF16 [B][H][W][CP] (CP = 32; channels C..CP-1 zero).
+__global__ void features_nhwc32_kernel(const float *__restrict__ in, int C, int64_t n, int64_t hw,
+                                       __nv_bfloat16 *__restrict__ out) {
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t b = p / hw, i = p - b * hw;
+        const float *src = in + b * C * hw + i;
+        uint32_t w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float lo = 2 * k < C ? __ldg(src + (2 * k) * hw) : 0.f;
+            const float hi = 2 * k + 1 < C ? __ldg(src + (2 * k + 1) * hw) : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+            w[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(out + p * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    }
+}
+
 __global__ void copy_bias_kernel(const float *__restrict__ b, int cout, int n, float *__restrict__ dst) {
     const int i = threadIdx.x;
     if (i < n) dst[i] = i < cout ? b[i] : 0.f;
@@ -140,11 +197,11 @@ __device__ __forceinline__ float unordered(uint32_t u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
 }
 
-// zmax[b] = max over the frame of z = logits0[b][54]
-__global__ void zmax_kernel(const float *__restrict__ logits0, int64_t hw, int B,
+// zmax[b] = max over the frame of z[b * stride + i]
+__global__ void zmax_kernel(const float *__restrict__ zplane, int64_t hw, int64_t stride,
                             uint32_t *__restrict__ zmax) {
     const int b = blockIdx.y;
-    const float *z = logits0 + (static_cast<int64_t>(b) * 55 + kDensityChannel) * hw;
+    const float *z = zplane + static_cast<int64_t>(b) * stride;
     float m = -INFINITY;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < hw;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -162,10 +219,10 @@ __global__ void zmax_kernel(const float *__restrict__ logits0, int64_t hw, int B
     }
 }
 
-__global__ void density_kernel(const float *__restrict__ logits0, int64_t hw,
+__global__ void density_kernel(const float *__restrict__ zplane, int64_t hw, int64_t stride,
                                const uint32_t *__restrict__ zmax, float *__restrict__ d) {
     const int b = blockIdx.y;
-    const float *z = logits0 + (static_cast<int64_t>(b) * 55 + kDensityChannel) * hw;
+    const float *z = zplane + static_cast<int64_t>(b) * stride;
     const float m = unordered(zmax[b]);
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < hw;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -174,21 +231,18 @@ __global__ void density_kernel(const float *__restrict__ logits0, int64_t hw,
 
 }  // namespace
 
-conv::ConvArgs layer_input(int i, int B, int W, int H, const float * /*in12*/,
-                           const unsigned char *ws) {
-    const ActLayout A = act_layout(B, W, H);
+conv::ConvArgs layer_input(int net, int i, int B, int W, int H, const unsigned char *ws) {
+    const ActLayout A = act_layout(net, B, W, H);
     auto act = [&](size_t off) { return reinterpret_cast<const __nv_bfloat16 *>(ws + off); };
     conv::ConvArgs a;
-    const int level = (i == E1A || i == E1B || i == D1A || i == D1B || i == H1)   ? 1
-                      : (i == E2A || i == E2B || i == H2) ? 2
-                                                          : 0;
+    const int level = level_of(i);
     a.B = B;
     a.W = W >> level;
     a.H = H >> level;
-    a.cin_pad = round16(kLayers[i].cin);
+    a.cin_pad = i == E0A ? A.xin_c : round16(layer(net, i).cin);
     a.src_mode = conv::kSrcNHWC;
     switch (i) {
-        case E0A: a.src0 = act(A.x16); a.c0 = 16; break;
+        case E0A: a.src0 = act(A.xin); a.c0 = A.xin_c; break;
         case E0B: a.src0 = act(A.e0a); a.c0 = 32; break;
         case E1A: a.src0 = act(A.p0); a.c0 = 32; break;
         case E1B: a.src0 = act(A.e1a); a.c0 = 64; break;
@@ -217,20 +271,34 @@ size_t layer_output(int i, const ActLayout &A) {
     return idx[i] < 0 ? static_cast<size_t>(-1) : offs[idx[i]];
 }
 
-int forward(const unsigned char *packed, const float *in12, int B, int W, int H, float *density,
-            float *logits0, float *logits1, float *logits2, unsigned char *ws, int32_t *status,
-            cudaStream_t stream) {
-    const PackedLayout P = packed_layout(0);
-    const ActLayout A = act_layout(B, W, H);
+int density_softmax(const float *z, int B, int64_t hw, int64_t batch_stride, float *d,
+                    uint32_t *zmax, cudaStream_t stream) {
+    if (cudaMemsetAsync(zmax, 0, sizeof(uint32_t) * B, stream) != cudaSuccess) return SPP_ERR_CUDA;
+    const int gx = static_cast<int>(std::min<int64_t>((hw + 255) / 256, 2 * sm_count()));
+    zmax_kernel<<<dim3(gx, B), 256, 0, stream>>>(z, hw, batch_stride, zmax);
+    density_kernel<<<dim3(gx, B), 256, 0, stream>>>(z, hw, batch_stride, zmax, d);
+    count_launch(2);
+    return launch_status();
+}
+
+int forward(int net, const unsigned char *packed, const float *in, int B, int W, int H,
+            float *density, float *head0, float *head1, float *head2, unsigned char *ws,
+            int32_t *status, cudaStream_t stream) {
+    const PackedLayout P = packed_layout(net, 0);
+    const ActLayout A = act_layout(net, B, W, H);
     float *heads[kNumLayers] = {};
-    heads[H0] = logits0;
-    heads[H1] = logits1;
-    heads[H2] = logits2;
+    heads[H0] = head0;
+    heads[H1] = head1;
+    heads[H2] = head2;
     {
         const int64_t n = static_cast<int64_t>(B) * W * H;
         const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 8 * sm_count()));
-        features_nhwc16_kernel<<<grid, 256, 0, stream>>>(
-            in12, n, static_cast<int64_t>(W) * H, reinterpret_cast<__nv_bfloat16 *>(ws + A.x16));
+        auto *x = reinterpret_cast<__nv_bfloat16 *>(ws + A.xin);
+        if (A.xin_c == 16)
+            features_nhwc16_kernel<<<grid, 256, 0, stream>>>(in, n, static_cast<int64_t>(W) * H, x);
+        else
+            features_nhwc32_kernel<<<grid, 256, 0, stream>>>(in, kNets[net].cin, n,
+                                                             static_cast<int64_t>(W) * H, x);
         count_launch();
         if (launch_status() != SPP_OK) return SPP_ERR_CUDA;
     }
@@ -238,13 +306,15 @@ int forward(const unsigned char *packed, const float *in12, int B, int W, int H,
                                           D1A, D1B, H1,  D0A, D0B, H0};
     for (int k = 0; k < kNumLayers; ++k) {
         const int i = order[k];
-        conv::ConvArgs a = layer_input(i, B, W, H, in12, ws);
-        a.n = fwd_n(i);
-        a.cout = kLayers[i].cout;
+        const Layer l = layer(net, i);
+        if (l.cout == 0) continue;
+        conv::ConvArgs a = layer_input(net, i, B, W, H, ws);
+        a.n = fwd_n(net, i);
+        a.cout = l.cout;
         a.wpack = reinterpret_cast<const __nv_bfloat16 *>(packed + P.fwd[i]);
         a.bias = reinterpret_cast<const float *>(packed + P.bias[i]);
         a.status = status;
-        if (kLayers[i].relu) {
+        if (l.relu) {
             a.epi_mode = conv::kEpiReluBF16;
             a.out = reinterpret_cast<__nv_bfloat16 *>(ws + layer_output(i, A));
             if (i == E0B) a.pool_out = reinterpret_cast<__nv_bfloat16 *>(ws + A.p0);
@@ -256,28 +326,30 @@ int forward(const unsigned char *packed, const float *in12, int B, int W, int H,
         const int rc = conv::conv3x3(a, stream);
         if (rc != SPP_OK) return rc;
     }
-    uint32_t *zmax = reinterpret_cast<uint32_t *>(ws + A.zmax);
-    if (cudaMemsetAsync(zmax, 0, sizeof(uint32_t) * B, stream) != cudaSuccess) return SPP_ERR_CUDA;
-    const int64_t hw = static_cast<int64_t>(W) * H;
-    const int gx = static_cast<int>(std::min<int64_t>((hw + 255) / 256, 2 * sm_count()));
-    zmax_kernel<<<dim3(gx, B), 256, 0, stream>>>(logits0, hw, B, zmax);
-    density_kernel<<<dim3(gx, B), 256, 0, stream>>>(logits0, hw, zmax, density);
-    count_launch(2);
+    if (net == kNetJoint && density) {
+        const int64_t hw = static_cast<int64_t>(W) * H;
+        return density_softmax(head0 + kDensityChannel * hw, B, hw, 55 * hw, density,
+                               reinterpret_cast<uint32_t *>(ws + A.zmax), stream);
+    }
     return launch_status();
 }
 
-int pack(const float *theta, int with_backward, unsigned char *packed, cudaStream_t stream) {
-    const PackedLayout P = packed_layout(with_backward);
+int pack(int net, const float *theta, int with_backward, unsigned char *packed,
+         cudaStream_t stream) {
+    const PackedLayout P = packed_layout(net, with_backward);
     for (int i = 0; i < kNumLayers; ++i) {
-        const Layer &l = kLayers[i];
-        int rc = conv::pack_weights(theta + P.theta_w[i], l.cin, l.cout, 0, round16(l.cin), fwd_n(i),
+        const Layer l = layer(net, i);
+        if (l.cout == 0) continue;
+        int rc = conv::pack_weights(theta + P.theta_w[i], l.cin, l.cout, 0, round16(l.cin),
+                                    fwd_n(net, i),
                                     reinterpret_cast<__nv_bfloat16 *>(packed + P.fwd[i]), stream);
         if (rc != SPP_OK) return rc;
-        copy_bias_kernel<<<1, 256, 0, stream>>>(theta + P.theta_b[i], l.cout, fwd_n(i),
+        copy_bias_kernel<<<1, 256, 0, stream>>>(theta + P.theta_b[i], l.cout, fwd_n(net, i),
                                                 reinterpret_cast<float *>(packed + P.bias[i]));
         count_launch();
-        if (with_backward && i > 0) {
-            rc = conv::pack_weights(theta + P.theta_w[i], l.cin, l.cout, 1, round16(l.cout), l.cin,
+        if (with_backward) {
+            rc = conv::pack_weights(theta + P.theta_w[i], l.cin, l.cout, 1, round16(l.cout),
+                                    i == E0A ? round16(l.cin) : l.cin,
                                     reinterpret_cast<__nv_bfloat16 *>(packed + P.bwd[i]), stream);
             if (rc != SPP_OK) return rc;
         }
@@ -301,26 +373,101 @@ int assemble(const float *albedo, const float *normal, const float *depth, const
 // ------------------------------------------------------------------ C ABI
 using spp::aligned16;
 
-extern "C" int spp_unet_layer(int i, int *cin, int *cout, int *relu) {
-    if (i < 0 || i >= spp::unet::kNumLayers || !cin || !cout || !relu) return SPP_ERR_ARG;
-    *cin = spp::unet::kLayers[i].cin;
-    *cout = spp::unet::kLayers[i].cout;
-    *relu = spp::unet::kLayers[i].relu;
+namespace {
+bool valid_net(int net) { return net >= 0 && net < spp::unet::kNumNets; }
+bool aligned256(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; }
+}  // namespace
+
+extern "C" int spp_net_spec(int net, int *cin, int *head0, int *head1, int *head2) {
+    if (!valid_net(net) || !cin || !head0 || !head1 || !head2) return SPP_ERR_ARG;
+    const spp::unet::NetSpec &n = spp::unet::kNets[net];
+    *cin = n.cin;
+    *head0 = n.heads[0];
+    *head1 = n.heads[1];
+    *head2 = n.heads[2];
     return SPP_OK;
 }
 
-extern "C" int64_t spp_unet_param_count(void) { return spp::unet::packed_layout(0).param_count; }
+extern "C" int spp_net_layer(int net, int i, int *cin, int *cout, int *relu) {
+    if (!valid_net(net) || i < 0 || i >= spp::unet::kNumLayers || !cin || !cout || !relu)
+        return SPP_ERR_ARG;
+    const spp::unet::Layer l = spp::unet::layer(net, i);
+    *cin = l.cin;
+    *cout = l.cout;
+    *relu = l.relu;
+    return SPP_OK;
+}
+
+extern "C" int64_t spp_net_param_count(int net) {
+    return valid_net(net) ? spp::unet::packed_layout(net, 0).param_count : -1;
+}
+
+extern "C" size_t spp_net_packed_bytes(int net, int with_backward) {
+    return valid_net(net) ? spp::unet::packed_layout(net, with_backward).total : 0;
+}
+
+extern "C" int spp_net_pack(int net, const float *theta, int with_backward, void *packed,
+                            size_t packed_bytes, cudaStream_t stream) {
+    if (!valid_net(net) || !theta || !packed) return SPP_ERR_ARG;
+    if (!aligned16(theta) || !aligned256(packed)) return SPP_ERR_ALIGN;
+    if (packed_bytes < spp::unet::packed_layout(net, with_backward).total) return SPP_ERR_WORKSPACE;
+    return spp::unet::pack(net, theta, with_backward, static_cast<unsigned char *>(packed), stream);
+}
+
+extern "C" size_t spp_net_workspace_bytes(int net, int B, int W, int H) {
+    if (!valid_net(net) || B < 0 || W < 0 || H < 0) return 0;
+    return spp::unet::act_layout(net, B, W, H).total;
+}
+
+extern "C" int spp_net_forward(int net, const void *packed, const float *in, int B, int W, int H,
+                               float *head0, float *head1, float *head2, void *ws,
+                               size_t ws_bytes, int32_t *status, cudaStream_t stream) {
+    if (!valid_net(net) || B < 0 || W < 0 || H < 0 || !packed || !in || !head0 || !ws)
+        return SPP_ERR_ARG;
+    const spp::unet::NetSpec &n = spp::unet::kNets[net];
+    if ((n.heads[1] && !head1) || (n.heads[2] && !head2)) return SPP_ERR_ARG;
+    if (W % 4 || H % 4) return SPP_ERR_SHAPE;
+    if (!aligned256(packed) || !aligned256(ws) || !aligned16(in) || !aligned16(head0) ||
+        (n.heads[1] && !aligned16(head1)) || (n.heads[2] && !aligned16(head2)))
+        return SPP_ERR_ALIGN;
+    if (ws_bytes < spp::unet::act_layout(net, B, W, H).total) return SPP_ERR_WORKSPACE;
+    if (static_cast<int64_t>(B) * W * H == 0) return SPP_OK;
+    return spp::unet::forward(net, static_cast<const unsigned char *>(packed), in, B, W, H, nullptr,
+                              head0, head1, head2, static_cast<unsigned char *>(ws), status,
+                              stream);
+}
+
+extern "C" size_t spp_density_softmax_workspace_bytes(int B) {
+    return B < 0 ? 0 : static_cast<size_t>(std::max(B, 1)) * sizeof(uint32_t);
+}
+
+extern "C" int spp_density_softmax(const float *z, int B, int W, int H, int64_t batch_stride,
+                                   float *density, void *ws, size_t ws_bytes,
+                                   cudaStream_t stream) {
+    if (!z || !density || !ws || B < 0 || W < 0 || H < 0 ||
+        batch_stride < static_cast<int64_t>(W) * H)
+        return SPP_ERR_ARG;
+    if (!aligned16(z) || !aligned16(density) || !aligned16(ws)) return SPP_ERR_ALIGN;
+    if (ws_bytes < static_cast<size_t>(std::max(B, 1)) * sizeof(uint32_t)) return SPP_ERR_WORKSPACE;
+    if (static_cast<int64_t>(B) * W * H == 0) return SPP_OK;
+    return spp::unet::density_softmax(z, B, static_cast<int64_t>(W) * H, batch_stride, density,
+                                      static_cast<uint32_t *>(ws), stream);
+}
+
+// The joint predictor (network 0) under its original names.
+extern "C" int spp_unet_layer(int i, int *cin, int *cout, int *relu) {
+    return spp_net_layer(spp::unet::kNetJoint, i, cin, cout, relu);
+}
+
+extern "C" int64_t spp_unet_param_count(void) { return spp_net_param_count(spp::unet::kNetJoint); }
 
 extern "C" size_t spp_unet_packed_bytes(int with_backward) {
-    return spp::unet::packed_layout(with_backward).total;
+    return spp_net_packed_bytes(spp::unet::kNetJoint, with_backward);
 }
 
 extern "C" int spp_unet_pack(const float *theta, int with_backward, void *packed,
                              size_t packed_bytes, cudaStream_t stream) {
-    if (!theta || !packed) return SPP_ERR_ARG;
-    if (!aligned16(theta) || (reinterpret_cast<uintptr_t>(packed) & 255u)) return SPP_ERR_ALIGN;
-    if (packed_bytes < spp::unet::packed_layout(with_backward).total) return SPP_ERR_WORKSPACE;
-    return spp::unet::pack(theta, with_backward, static_cast<unsigned char *>(packed), stream);
+    return spp_net_pack(spp::unet::kNetJoint, theta, with_backward, packed, packed_bytes, stream);
 }
 
 extern "C" int spp_assemble_features(const float *albedo, const float *normal, const float *depth,
@@ -334,8 +481,7 @@ extern "C" int spp_assemble_features(const float *albedo, const float *normal, c
 }
 
 extern "C" size_t spp_predict_workspace_bytes(int B, int W, int H) {
-    if (B < 0 || W < 0 || H < 0) return 0;
-    return spp::unet::act_layout(B, W, H).total;
+    return spp_net_workspace_bytes(spp::unet::kNetJoint, B, W, H);
 }
 
 extern "C" int spp_predict_density_and_kernels(const void *packed, const float *in12, int B, int W,
@@ -347,15 +493,15 @@ extern "C" int spp_predict_density_and_kernels(const void *packed, const float *
         !logits2 || !ws)
         return SPP_ERR_ARG;
     if (W % 4 || H % 4) return SPP_ERR_SHAPE;
-    if ((reinterpret_cast<uintptr_t>(packed) & 255u) || (reinterpret_cast<uintptr_t>(ws) & 255u) ||
-        !aligned16(in12) || !aligned16(density) || !aligned16(logits0) || !aligned16(logits1) ||
-        !aligned16(logits2))
+    if (!aligned256(packed) || !aligned256(ws) || !aligned16(in12) || !aligned16(density) ||
+        !aligned16(logits0) || !aligned16(logits1) || !aligned16(logits2))
         return SPP_ERR_ALIGN;
-    if (ws_bytes < spp::unet::act_layout(B, W, H).total) return SPP_ERR_WORKSPACE;
+    if (ws_bytes < spp::unet::act_layout(spp::unet::kNetJoint, B, W, H).total)
+        return SPP_ERR_WORKSPACE;
     if (static_cast<int64_t>(B) * W * H == 0) return SPP_OK;
-    return spp::unet::forward(static_cast<const unsigned char *>(packed), in12, B, W, H, density,
-                              logits0, logits1, logits2, static_cast<unsigned char *>(ws), status,
-                              stream);
+    return spp::unet::forward(spp::unet::kNetJoint, static_cast<const unsigned char *>(packed),
+                              in12, B, W, H, density, logits0, logits1, logits2,
+                              static_cast<unsigned char *>(ws), status, stream);
 }
 
 // ----------------------------------------------------- single conv layers

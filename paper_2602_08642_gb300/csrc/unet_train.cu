@@ -21,14 +21,14 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // BF16 NHWC gradient buffers of the backward.
 struct GradLayout {
-    size_t d0b, d0a, cat0, e0b, e0a;               // level 0
+    size_t d0b, d0a, cat0, e0b, e0a, gin;          // level 0 (gin: input gradient)
     size_t t1h, d1b, d1a, cat1, e1b, e1a, pool0;   // level 1
     size_t bth, e2b, e2a, pool1;                   // level 2
     size_t wg;                                     // weight-gradient scratch
     size_t total;
 };
 
-GradLayout grad_layout(int B, int W, int H) {
+GradLayout grad_layout(int net, int B, int W, int H) {
     GradLayout G{};
     const size_t p0 = static_cast<size_t>(B) * H * W, p1 = p0 / 4, p2 = p0 / 16;
     size_t off = 0;
@@ -42,6 +42,7 @@ GradLayout grad_layout(int B, int W, int H) {
     G.cat0 = take(p0 * 96);
     G.e0b = take(p0 * 32);
     G.e0a = take(p0 * 32);
+    G.gin = take(p0 * input_channels_padded(net));
     G.t1h = take(p1 * 64);
     G.d1b = take(p1 * 64);
     G.d1a = take(p1 * 64);
@@ -56,11 +57,11 @@ GradLayout grad_layout(int B, int W, int H) {
     G.wg = off;
     size_t wg = 0;
     for (int i = 0; i < kNumLayers; ++i) {
-        const int level = (i == E1A || i == E1B || i == D1A || i == D1B || i == H1)   ? 1
-                          : (i == E2A || i == E2B || i == H2) ? 2
-                                                              : 0;
-        wg = std::max(wg, conv::wgrad_workspace_bytes(B, W >> level, H >> level,
-                                                      round16(kLayers[i].cin), fwd_n(i)));
+        if (!present(net, i)) continue;
+        const int level = level_of(i);
+        const int cin_pad = i == E0A ? input_channels_padded(net) : round16(layer(net, i).cin);
+        wg = std::max(wg, conv::wgrad_workspace_bytes(B, W >> level, H >> level, cin_pad,
+                                                      fwd_n(net, i)));
     }
     G.total = align256(off + wg);
     return G;
@@ -139,6 +140,18 @@ __global__ void adamw_kernel(float *__restrict__ theta, const float *__restrict_
     }
 }
 
+// BF16 NHWC [B][H][W][CP] -> FP32 planar [B][C][H][W] (the first C channels).
+__global__ void nhwc_to_planar_kernel(const __nv_bfloat16 *__restrict__ src, int CP, int C,
+                                      int64_t n, int64_t hw, float *__restrict__ dst) {
+    for (int64_t p = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t b = p / hw, i = p - b * hw;
+        const __nv_bfloat16 *s = src + p * CP;
+        float *d = dst + b * C * hw + i;
+        for (int c = 0; c < C; ++c) d[c * hw] = __bfloat162float(s[c]);
+    }
+}
+
 int launch_junction(int B, int H, int W, int C, const __nv_bfloat16 *act, const __nv_bfloat16 *A,
                     int a_c, int a_off, const __nv_bfloat16 *F, int f_c, int f_off,
                     const __nv_bfloat16 *Cq, int c_c, __nv_bfloat16 *out, cudaStream_t stream) {
@@ -153,20 +166,23 @@ int launch_junction(int B, int H, int W, int C, const __nv_bfloat16 *act, const 
 
 }  // namespace
 
-size_t backward_workspace_bytes(int B, int W, int H) { return grad_layout(B, W, H).total; }
+size_t backward_workspace_bytes(int net, int B, int W, int H) {
+    return grad_layout(net, B, W, H).total;
+}
 
-int backward(const unsigned char *packed, const float *in12, int B, int W, int H,
-             const unsigned char *fws, const float *g0, const float *g1, const float *g2,
-             float *grad_theta, unsigned char *bws, int32_t *status, cudaStream_t stream) {
-    const PackedLayout P = packed_layout(1);
-    const ActLayout A = act_layout(B, W, H);
-    const GradLayout G = grad_layout(B, W, H);
+int backward(int net, const unsigned char *packed, int B, int W, int H, const unsigned char *fws,
+             const float *g0, const float *g1, const float *g2, float *grad_theta, float *grad_in,
+             unsigned char *bws, int32_t *status, cudaStream_t stream) {
+    const PackedLayout P = packed_layout(net, 1);
+    const ActLayout A = act_layout(net, B, W, H);
+    const GradLayout G = grad_layout(net, B, W, H);
     auto act = [&](size_t off) { return reinterpret_cast<const __nv_bfloat16 *>(fws + off); };
     auto gb = [&](size_t off) { return reinterpret_cast<__nv_bfloat16 *>(bws + off); };
     const float *gheads[kNumLayers] = {};
     gheads[H0] = g0;
     gheads[H1] = g1;
     gheads[H2] = g2;
+    const bool has_h1 = present(net, H1), has_h2 = present(net, H2);
     // gradient with respect to each layer's pre-activation output
     size_t gpre[kNumLayers] = {G.e0a, G.e0b, G.e1a, G.e1b, G.e2a, G.e2b, 0,
                                G.d1a, G.d1b, 0,     G.d0a, G.d0b, 0};
@@ -177,42 +193,41 @@ int backward(const unsigned char *packed, const float *in12, int B, int W, int H
         g.B = B;
         g.W = W >> level;
         g.H = H >> level;
-        if (!kLayers[i].relu) {
+        const Layer l = layer(net, i);
+        if (!l.relu) {
             g.src_mode = conv::kSrcPlanarF32;
             g.srcf = gheads[i];
-            g.cf = kLayers[i].cout;
+            g.cf = l.cout;
         } else {
             g.src_mode = conv::kSrcNHWC;
             g.src0 = gb(gpre[i]);
-            g.c0 = kLayers[i].cout;
+            g.c0 = l.cout;
         }
         return g;
     };
-    auto level_of = [](int i) {
-        return (i == E1A || i == E1B || i == D1A || i == D1B || i == H1) ? 1
-               : (i == E2A || i == E2B || i == H2)                       ? 2
-                                                                         : 0;
-    };
     auto wgrad_layer = [&](int i) {
-        if (rc != SPP_OK) return;
+        if (rc != SPP_OK || !present(net, i)) return;
+        const Layer l = layer(net, i);
         conv::WgradArgs w;
-        w.x = layer_input(i, B, W, H, in12, fws);
+        w.x = layer_input(net, i, B, W, H, fws);
         w.g = gsrc(i, level_of(i));
-        w.cin = kLayers[i].cin;
-        w.cout = kLayers[i].cout;
-        w.n = fwd_n(i);
+        w.cin = l.cin;
+        w.cout = l.cout;
+        w.n = fwd_n(net, i);
         w.status = status;
         rc = conv::wgrad(w, grad_theta + P.theta_w[i], grad_theta + P.theta_b[i], bws + G.wg,
                          stream);
     };
-    // data gradient of layer i into `out` (channels cin), masked by `mask`
+    // data gradient of layer i into `out` (channels cin, the input layer's
+    // padded), masked by `mask`
     auto dgrad_layer = [&](int i, __nv_bfloat16 *out, const __nv_bfloat16 *mask) {
-        if (rc != SPP_OK) return;
+        if (rc != SPP_OK || !present(net, i)) return;
+        const Layer l = layer(net, i);
         const int level = level_of(i);
         conv::ConvArgs a = gsrc(i, level);
-        a.cin_pad = round16(kLayers[i].cout);
-        a.n = kLayers[i].cin;
-        a.cout = kLayers[i].cin;
+        a.cin_pad = round16(l.cout);
+        a.n = i == E0A ? input_channels_padded(net) : l.cin;
+        a.cout = a.n;
         a.wpack = reinterpret_cast<const __nv_bfloat16 *>(packed + P.bwd[i]);
         a.epi_mode = mask ? conv::kEpiMaskBF16 : conv::kEpiBF16;
         a.act = mask;
@@ -238,7 +253,8 @@ int backward(const unsigned char *packed, const float *in12, int B, int W, int H
     // decoder, level 1
     wgrad_layer(H1);
     dgrad_layer(H1, gb(G.t1h), nullptr);
-    junction(1, 64, act(A.t1), gb(G.t1h), 64, 0, gb(G.cat0), 96, 32, nullptr, 0, gb(G.d1b));
+    junction(1, 64, act(A.t1), has_h1 ? gb(G.t1h) : nullptr, 64, 0, gb(G.cat0), 96, 32, nullptr,
+             0, gb(G.d1b));
     wgrad_layer(D1B);
     dgrad_layer(D1B, gb(G.d1a), act(A.d1a));
     wgrad_layer(D1A);
@@ -246,7 +262,8 @@ int backward(const unsigned char *packed, const float *in12, int B, int W, int H
     // bottleneck, level 2
     wgrad_layer(H2);
     dgrad_layer(H2, gb(G.bth), nullptr);
-    junction(2, 128, act(A.bt), gb(G.bth), 128, 0, gb(G.cat1), 192, 64, nullptr, 0, gb(G.e2b));
+    junction(2, 128, act(A.bt), has_h2 ? gb(G.bth) : nullptr, 128, 0, gb(G.cat1), 192, 64,
+             nullptr, 0, gb(G.e2b));
     wgrad_layer(E2B);
     dgrad_layer(E2B, gb(G.e2a), act(A.e2a));
     wgrad_layer(E2A);
@@ -262,6 +279,16 @@ int backward(const unsigned char *packed, const float *in12, int B, int W, int H
     wgrad_layer(E0B);
     dgrad_layer(E0B, gb(G.e0a), act(A.e0a));
     wgrad_layer(E0A);
+    if (grad_in && rc == SPP_OK) {
+        dgrad_layer(E0A, gb(G.gin), nullptr);
+        if (rc != SPP_OK) return rc;
+        const int64_t n = static_cast<int64_t>(B) * W * H;
+        const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 8 * sm_count()));
+        nhwc_to_planar_kernel<<<grid, 256, 0, stream>>>(gb(G.gin), A.xin_c, kNets[net].cin, n,
+                                                        static_cast<int64_t>(W) * H, grad_in);
+        count_launch();
+        rc = launch_status();
+    }
     return rc;
 }
 
@@ -283,9 +310,38 @@ int adamw(float *theta, const float *grad, float *m, float *v, int64_t n, int st
 // ------------------------------------------------------------------ C ABI
 using spp::aligned16;
 
+extern "C" size_t spp_net_backward_workspace_bytes(int net, int B, int W, int H) {
+    if (net < 0 || net >= spp::unet::kNumNets || B < 0 || W < 0 || H < 0) return 0;
+    return spp::unet::backward_workspace_bytes(net, B, W, H);
+}
+
+extern "C" int spp_net_backward(int net, const void *packed, int B, int W, int H,
+                                const void *fwd_ws, size_t fwd_ws_bytes, const float *grad_head0,
+                                const float *grad_head1, const float *grad_head2,
+                                float *grad_theta, float *grad_in, void *ws, size_t ws_bytes,
+                                int32_t *status, cudaStream_t stream) {
+    if (net < 0 || net >= spp::unet::kNumNets || B < 0 || W < 0 || H < 0 || !packed || !fwd_ws ||
+        !grad_head0 || !grad_theta || !ws)
+        return SPP_ERR_ARG;
+    const spp::unet::NetSpec &n = spp::unet::kNets[net];
+    if ((n.heads[1] && !grad_head1) || (n.heads[2] && !grad_head2)) return SPP_ERR_ARG;
+    if (W % 4 || H % 4) return SPP_ERR_SHAPE;
+    auto a256 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 255u) == 0; };
+    if (!a256(packed) || !a256(fwd_ws) || !a256(ws) || !aligned16(grad_head0) ||
+        (n.heads[1] && !aligned16(grad_head1)) || (n.heads[2] && !aligned16(grad_head2)) ||
+        !aligned16(grad_theta) || (grad_in && !aligned16(grad_in)))
+        return SPP_ERR_ALIGN;
+    if (fwd_ws_bytes < spp::unet::act_layout(net, B, W, H).total ||
+        ws_bytes < spp::unet::backward_workspace_bytes(net, B, W, H))
+        return SPP_ERR_WORKSPACE;
+    return spp::unet::backward(net, static_cast<const unsigned char *>(packed), B, W, H,
+                               static_cast<const unsigned char *>(fwd_ws), grad_head0, grad_head1,
+                               grad_head2, grad_theta, grad_in, static_cast<unsigned char *>(ws),
+                               status, stream);
+}
+
 extern "C" size_t spp_unet_backward_workspace_bytes(int B, int W, int H) {
-    if (B < 0 || W < 0 || H < 0) return 0;
-    return spp::unet::backward_workspace_bytes(B, W, H);
+    return spp_net_backward_workspace_bytes(spp::unet::kNetJoint, B, W, H);
 }
 
 extern "C" int spp_unet_backward(const void *packed, const float *in12, int B, int W, int H,
@@ -293,21 +349,11 @@ extern "C" int spp_unet_backward(const void *packed, const float *in12, int B, i
                                  const float *grad_logits1, const float *grad_logits2,
                                  float *grad_theta, void *ws, size_t ws_bytes, int32_t *status,
                                  cudaStream_t stream) {
-    if (B < 0 || W < 0 || H < 0 || !packed || !in12 || !fwd_ws || !grad_logits0 ||
-        !grad_logits1 || !grad_logits2 || !grad_theta || !ws)
-        return SPP_ERR_ARG;
-    if (W % 4 || H % 4) return SPP_ERR_SHAPE;
-    if ((reinterpret_cast<uintptr_t>(packed) & 255u) || (reinterpret_cast<uintptr_t>(fwd_ws) & 255u) ||
-        (reinterpret_cast<uintptr_t>(ws) & 255u) || !aligned16(in12) || !aligned16(grad_logits0) ||
-        !aligned16(grad_logits1) || !aligned16(grad_logits2) || !aligned16(grad_theta))
-        return SPP_ERR_ALIGN;
-    if (fwd_ws_bytes < spp::unet::act_layout(B, W, H).total ||
-        ws_bytes < spp::unet::backward_workspace_bytes(B, W, H))
-        return SPP_ERR_WORKSPACE;
-    return spp::unet::backward(static_cast<const unsigned char *>(packed), in12, B, W, H,
-                               static_cast<const unsigned char *>(fwd_ws), grad_logits0,
-                               grad_logits1, grad_logits2, grad_theta,
-                               static_cast<unsigned char *>(ws), status, stream);
+    if (!in12) return SPP_ERR_ARG;
+    if (!aligned16(in12)) return SPP_ERR_ALIGN;
+    return spp_net_backward(spp::unet::kNetJoint, packed, B, W, H, fwd_ws, fwd_ws_bytes,
+                            grad_logits0, grad_logits1, grad_logits2, grad_theta, nullptr, ws,
+                            ws_bytes, status, stream);
 }
 
 extern "C" int spp_adamw_step(float *theta, const float *grad, float *m, float *v, int64_t n,

@@ -55,30 +55,49 @@ def _zeros(*shape, dtype=torch.float32):
 
 
 class Predictor:
-    """Device state of the network for batches of B frames of W x H."""
+    """Device state of one network (the joint predictor by default; the
+    sampler or the denoiser of the two-stage pipeline with ``net``) for
+    batches of B frames of W x H."""
 
-    def __init__(self, theta: torch.Tensor, B_: int, W: int, H: int, train: bool = False):
+    def __init__(self, theta: torch.Tensor, B_: int, W: int, H: int, train: bool = False,
+                 net: int = B.SPP_NET_JOINT, input_grad: bool = False):
         if W % 4 or H % 4:
             raise ValueError("W and H must be divisible by 4")
-        self.B, self.W, self.H, self.train = B_, W, H, train
+        self.B, self.W, self.H, self.train, self.net = B_, W, H, train, net
+        self.cin, self.head_ch = B.spp_net_spec(net)
         self.theta = theta.detach().to("cuda", torch.float32).contiguous().clone()
-        if self.theta.numel() != B.spp_unet_param_count():
+        if self.theta.numel() != B.spp_net_param_count(net):
             raise ValueError("theta has the wrong size")
-        self.packed = self._aligned(B.spp_unet_packed_bytes(train))
-        self.fws = self._aligned(B.spp_predict_workspace_bytes(B_, W, H))
-        self.in12 = _zeros(B_, 12, H, W)
+        self.packed = self._aligned(B.spp_net_packed_bytes(net, train))
+        self.fws = self._aligned(B.spp_net_workspace_bytes(net, B_, W, H))
+        self.x = _zeros(B_, self.cin, H, W)
+        self.heads = [None if c == 0 else _zeros(B_, c, H >> l, W >> l)
+                      for l, c in enumerate(self.head_ch)]
         self.density = _zeros(B_, H, W)
-        self.logits = [_zeros(B_, 55, H, W), _zeros(B_, 29, H // 2, W // 2),
-                       _zeros(B_, 25, H // 4, W // 4)]
+        self.dws = self._aligned(B.spp_density_softmax_workspace_bytes(B_))
         self.status = _zeros(4, dtype=torch.int32)[:1]
         if train:
-            self.bws = self._aligned(B.spp_unet_backward_workspace_bytes(B_, W, H))
+            self.bws = self._aligned(B.spp_net_backward_workspace_bytes(net, B_, W, H))
             self.grad = _zeros(self.theta.numel())
             self.m = _zeros(self.theta.numel())
             self.v = _zeros(self.theta.numel())
-            self.g_logits = [torch.zeros_like(t) for t in self.logits]
+            self.g_heads = [None if t is None else torch.zeros_like(t) for t in self.heads]
+            self.g_x = torch.zeros_like(self.x) if input_grad else None
             self.step_count = 0
         self.pack()
+
+    # the joint network's names
+    @property
+    def in12(self):
+        return self.x
+
+    @property
+    def logits(self):
+        return self.heads
+
+    @property
+    def g_logits(self):
+        return self.g_heads
 
     @staticmethod
     def _aligned(n: int) -> torch.Tensor:
@@ -87,21 +106,29 @@ class Predictor:
         return buf[off:off + int(n)]
 
     def pack(self):
-        B.check(B.spp_unet_pack(self.theta, self.train, self.packed), "spp_unet_pack")
+        B.check(B.spp_net_pack(self.net, self.theta, self.train, self.packed), "spp_net_pack")
 
     def features(self, b: int, albedo, normal, depth, mv, prev_ldr=None):
         B.check(B.spp_assemble_features(albedo, normal, depth, mv, prev_ldr, self.W, self.H,
-                                        self.in12[b]), "spp_assemble_features")
+                                        self.x[b]), "spp_assemble_features")
 
     def forward(self):
-        B.check(B.spp_predict_density_and_kernels(self.packed, self.in12, self.B, self.W, self.H,
-                                                  self.density, *self.logits, self.fws,
-                                                  self.status), "spp_predict")
+        if self.net == B.SPP_NET_JOINT:
+            B.check(B.spp_predict_density_and_kernels(self.packed, self.x, self.B, self.W, self.H,
+                                                      self.density, *self.heads, self.fws,
+                                                      self.status), "spp_predict")
+            return
+        B.check(B.spp_net_forward(self.net, self.packed, self.x, self.B, self.W, self.H,
+                                  *self.heads, self.fws, self.status), "spp_net_forward")
+        if self.net == B.SPP_NET_SAMPLER:
+            hw = self.W * self.H
+            B.check(B.spp_density_softmax(self.heads[0], self.B, self.W, self.H, hw, self.density,
+                                          self.dws), "spp_density_softmax")
 
     def backward(self):
-        B.check(B.spp_unet_backward(self.packed, self.in12, self.B, self.W, self.H, self.fws,
-                                    *self.g_logits, self.grad, self.bws, self.status),
-                "spp_unet_backward")
+        B.check(B.spp_net_backward(self.net, self.packed, self.B, self.W, self.H, self.fws,
+                                   *self.g_heads, self.grad, self.g_x, self.bws, self.status),
+                "spp_net_backward")
 
     def adamw(self, lr: float, weight_decay: float = 1e-4, grad_scale: float = 1.0,
               betas=(0.9, 0.999)):
@@ -112,8 +139,8 @@ class Predictor:
         self.pack()
 
     def frame_logits(self, b: int, temporal: bool):
-        l0 = self.logits[0][b, :54] if temporal else self.logits[0][b, :29]
-        return [l0, self.logits[1][b], self.logits[2][b]]
+        l0 = self.heads[0][b, :54] if temporal else self.heads[0][b, :29]
+        return [l0, self.heads[1][b], self.heads[2][b]]
 
 
 class FrameData:

@@ -1,0 +1,381 @@
+"""Parity of the two-stage pipeline (sampler, denoiser, latents, learned
+demodulation) with its FP64 oracle (oracle/two_stage.py, oracle/unet.py),
+and a training check of the whole pipeline on the GPU.
+
+Tolerances
+* Networks: as the joint predictor's (tests/test_gpu_unet.py): BF16
+  weights and activations, FP32 accumulation; max error below 8 % and RMS
+  error below 1.5 % of each head's RMS against the oracle with the same
+  BF16 roundings, below 2 % against the exact FP64 network.  Gradients:
+  relative L2 error per layer below 3 %, in a parameter regime where the
+  ReLU masks do not depend on rounding (see _theta_stable).
+* Feature assembly, latent warp, demodulation, pyramid, remodulation: FP32
+  arithmetic on FP32 inputs, 2e-6 relative (+ 1e-6 absolute for the logs
+  and the tone-mapped output).
+* Demodulated reconstruction and its backward: as the plain
+  reconstruction's (1e-5 relative) and backward (1e-4 relative + 1e-5 of
+  the largest magnitude).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle.two_stage as TS
+import oracle.unet as U
+import spp_inputs as inp
+from test_gpu_backward import assert_grad
+
+pytestmark = pytest.mark.gpu
+
+NETS = {"sampler": 1, "denoiser": 2}
+
+
+@pytest.fixture(scope="module")
+def spp():
+    from conftest import build_spp_lib
+    build_spp_lib()
+    import paper_2602_08642_gb300 as spp
+    torch.cuda.set_device(0)
+    oracle.build()
+    return spp
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def _theta(spec, seed=21):
+    table, _ = U.param_offsets(spec)
+    theta = inp.unet_params(U.layers(spec), seed=seed, head_scale=1.0).astype(np.float64)
+    rng = np.random.default_rng(seed + 1)
+    for name, cin, cout, wo, bo in table:
+        theta[bo:bo + cout] = 0.05 * rng.standard_normal(cout)
+    return theta.astype(np.float32)
+
+
+def _gbuf(W, H, seed):
+    clean, gb = inp.scene(W, H, seed=seed)
+    mv = inp.motion_affine(W, H, seed=seed)
+    return clean, gb, mv
+
+
+def _inputs(spec, B, W, H, seed):
+    xs = []
+    rng = np.random.default_rng(seed)
+    for b in range(B):
+        clean, gb, mv = _gbuf(W, H, seed + b)
+        lat = rng.uniform(-1, 1, (TS.N_LATENT, H, W))
+        prev = rng.random((3, H, W)) * 2
+        if spec in ("sampler", "joint"):
+            xs.append(TS.sampler_features(gb["albedo"], gb["normal"], gb["depth"], mv,
+                                          np.clip(prev / 2, 0, 1), lat))
+            if spec == "joint":
+                xs[-1] = xs[-1][:12]
+        else:
+            L0 = clean * np.exp(0.8 * rng.standard_normal((3, H, W)) - 0.32)
+            L0[:, rng.random((H, W)) < 0.6] = 0
+            s = rng.uniform(0.03, 2.0, (H, W))
+            n = rng.integers(0, 3, (H, W))
+            xs.append(TS.denoiser_features(L0, s, n, gb["albedo"], gb["normal"], gb["depth"], mv,
+                                           prev, lat))
+    return np.stack(xs).astype(np.float32)
+
+
+def _run_net(spp, net, theta, x, B, W, H, train=False):
+    bnd = spp.binding
+    cin, heads = bnd.spp_net_spec(net)
+    packed = _aligned(bnd.spp_net_packed_bytes(net, train))
+    bnd.check(bnd.spp_net_pack(net, dev(theta), train, packed))
+    ws = _aligned(bnd.spp_net_workspace_bytes(net, B, W, H))
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")[:1]
+    outs = [None if c == 0 else torch.empty(B, c, H >> l, W >> l, device="cuda")
+            for l, c in enumerate(heads)]
+    xin = dev(x)
+    bnd.check(bnd.spp_net_forward(net, packed, xin, B, W, H, *outs, ws, st))
+    assert bnd.spp_get_status(st) == 0
+    return outs, dict(packed=packed, ws=ws, st=st, x=xin)
+
+
+def _aligned(n):
+    buf = torch.empty(int(n) + 256, dtype=torch.uint8, device="cuda")
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + int(n)]
+
+
+@pytest.mark.parametrize("regime", ["he", "stable"])
+@pytest.mark.parametrize("spec", ["sampler", "denoiser"])
+@pytest.mark.parametrize("B,W,H", [(2, 48, 32), (1, 136, 20), (8, 64, 64)])
+def test_net_forward_parity(spp, spec, B, W, H, regime):
+    theta = _theta(spec) if regime == "he" else _theta_stable(spec)
+    x = _inputs(spec, B, W, H, seed=30)
+    outs, _ = _run_net(spp, NETS[spec], theta, x, B, W, H)
+    report = []
+    for b in range(B):
+        ref = U.forward(theta, x[b], round_bf16_acts=True, spec=spec)["heads"]
+        exact = U.forward(theta, x[b], round_bf16_acts=False, spec=spec)["heads"]
+        for k, (o, r, e) in enumerate(zip(outs, ref, exact)):
+            if o is None:
+                assert r is None
+                continue
+            g = host(o[b])
+            scale = np.sqrt(np.mean(r * r))
+            report.append((b, k, round(float(np.abs(g - r).max() / scale), 4),
+                           round(float(np.sqrt(np.mean((g - r) ** 2)) / scale), 5),
+                           round(float(np.sqrt(np.mean((g - e) ** 2)) / scale), 5)))
+    print(spec, regime, "(image, head, max/rms, rms/rms vs bf16 oracle, rms/rms vs exact):", report)
+    # against the exact FP64 network the BF16 error of a head is 0.2-1.5 %
+    # RMS (the sampler's single plane is the noisiest); against the oracle
+    # with the same roundings below 1 %
+    for b, k, emax, erms, eexact in report:
+        assert emax < 8e-2 and erms < 1.5e-2 and eexact < 2e-2, (spec, b, k)
+
+
+def test_sampler_density_softmax(spp):
+    B, W, H = 2, 40, 24
+    theta = _theta("sampler")
+    x = _inputs("sampler", B, W, H, seed=33)
+    outs, _ = _run_net(spp, 1, theta, x, B, W, H)
+    bnd = spp.binding
+    d = torch.empty(B, H, W, device="cuda")
+    ws = torch.empty(bnd.spp_density_softmax_workspace_bytes(B), dtype=torch.uint8, device="cuda")
+    bnd.check(bnd.spp_density_softmax(outs[0], B, W, H, W * H, d, ws))
+    z = host(outs[0])[:, 0]
+    for b in range(B):
+        ref = np.exp(z[b] - z[b].max())
+        assert np.allclose(host(d[b]), ref, rtol=2e-6, atol=1e-7)
+
+
+def _theta_stable(spec, seed=21):
+    """Hidden weights scaled by 1/4 and hidden biases around +0.3: no
+    pre-activation comes near zero, so no ReLU mask depends on rounding.
+    With He-scale weights and small biases the hidden-layer gradients of a
+    BF16 network are not determined to better than about 10 % (a 1e-4
+    relative change of one bias moves the FP64 oracle's own gradients by
+    7-17 %: about 0.4 % of the masks flip); here that spread is below
+    1.3 %."""
+    table, _ = U.param_offsets(spec)
+    theta = inp.unet_params(U.layers(spec), seed=seed, head_scale=1.0).astype(np.float64)
+    rng = np.random.default_rng(seed + 1)
+    for name, cin, cout, wo, bo in table:
+        hidden = not name.startswith("h")
+        if hidden:
+            theta[wo:bo] *= 0.25
+        theta[bo:bo + cout] = (0.3 if hidden else 0.0) + 0.05 * rng.standard_normal(cout)
+    return theta.astype(np.float32)
+
+
+@pytest.mark.parametrize("spec", ["joint", "sampler", "denoiser"])
+@pytest.mark.parametrize("B,W,H", [(2, 48, 32), (8, 64, 64)])
+def test_net_backward_parity(spp, spec, B, W, H):
+    """Parameter and input gradients of every network (absent heads, padded
+    input channels, the input layer's data gradient) against the FP64
+    oracle, in the regime where they are well determined: 3 % relative L2
+    per layer."""
+    net = {"joint": 0, **NETS}[spec]
+    theta = _theta_stable(spec)
+    x = _inputs(spec, B, W, H, seed=40)
+    outs, st = _run_net(spp, net, theta, x, B, W, H, train=True)
+    rng = np.random.default_rng(41)
+    gh = [None if o is None else rng.standard_normal(tuple(o.shape)).astype(np.float32)
+          for o in outs]
+    bnd = spp.binding
+    bws = _aligned(bnd.spp_net_backward_workspace_bytes(net, B, W, H))
+    grad = torch.empty(theta.size, device="cuda")
+    g_in = torch.empty(B, x.shape[1], H, W, device="cuda")
+    bnd.check(bnd.spp_net_backward(net, st["packed"], B, W, H, st["ws"],
+                                   *[None if g is None else dev(g) for g in gh], grad, g_in, bws,
+                                   st["st"]))
+    assert bnd.spp_get_status(st["st"]) == 0
+    ref = np.zeros(theta.size)
+    ref_x = np.zeros(x.shape)
+    for b in range(B):
+        f = U.forward(theta, x[b], round_bf16_acts=True, spec=spec)
+        r, rx = U.backward_heads(f, [None if g is None else g[b] for g in gh], input_grad=True)
+        ref += r
+        ref_x[b] = rx
+    got = host(grad)
+    errs = {}
+    table, _ = U.param_offsets(spec)
+    for name, cin, cout, wo, bo in table:
+        for part, sl in (("w", slice(wo, bo)), ("b", slice(bo, bo + cout))):
+            errs[name + "." + part] = float(np.linalg.norm(got[sl] - ref[sl]) / np.linalg.norm(ref[sl]))
+    gx = host(g_in)
+    errs["input"] = float(np.linalg.norm(gx - ref_x) / np.linalg.norm(ref_x))
+    print("relative L2 error of the gradients:", {k: round(v, 5) for k, v in errs.items()})
+    bad = {k: v for k, v in errs.items() if not v < 3e-2}
+    assert not bad, bad
+
+
+@pytest.mark.parametrize("W,H", [(40, 24), (130, 18)])
+def test_feature_assembly_and_latent_warp_parity(spp, W, H):
+    rng = np.random.default_rng(W)
+    clean, gb, mv = _gbuf(W, H, 7)
+    L0 = (clean * rng.random((3, H, W))).astype(np.float32)
+    s = rng.uniform(0.03, 3.0, (H, W)).astype(np.float32)
+    n = rng.integers(0, 4, (H, W)).astype(np.int32)
+    prev = (rng.random((3, H, W)) * 3).astype(np.float32)
+    raw = (rng.standard_normal((TS.N_LATENT, H, W)) * 2).astype(np.float32)
+    mv = mv.astype(np.float32)
+    bnd = spp.binding
+    g = {k: dev(v.astype(np.float32)) for k, v in gb.items()}
+    lat = torch.empty(TS.N_LATENT, H, W, device="cuda")
+    bnd.check(bnd.spp_warp_latent(dev(raw), dev(mv), W, H, lat))
+    ref_lat = TS.warp_channels(np.tanh(raw.astype(np.float64)), mv)
+    assert np.allclose(host(lat), ref_lat, rtol=2e-6, atol=1e-6)
+    lat_np = host(lat)
+    x19 = torch.empty(19, H, W, device="cuda")
+    bnd.check(bnd.spp_assemble_sampler_features(g["albedo"], g["normal"], g["depth"], dev(mv),
+                                                dev(prev), lat, W, H, x19))
+    ref19 = TS.sampler_features(gb["albedo"], gb["normal"], gb["depth"], mv, prev, lat_np)
+    assert np.allclose(host(x19), ref19, rtol=2e-6, atol=1e-6)
+    x24 = torch.empty(24, H, W, device="cuda")
+    bnd.check(bnd.spp_assemble_denoiser_features(dev(L0), dev(s), dev(n, torch.int32),
+                                                 g["albedo"], g["normal"], g["depth"], dev(mv),
+                                                 dev(prev), lat, W, H, x24))
+    ref24 = TS.denoiser_features(L0, s, n, gb["albedo"], gb["normal"], gb["depth"], mv, prev,
+                                 lat_np)
+    assert np.allclose(host(x24), ref24, rtol=2e-6, atol=1e-6)
+    # first frame: no previous output, no latents
+    bnd.check(bnd.spp_assemble_denoiser_features(dev(L0), dev(s), dev(n, torch.int32),
+                                                 g["albedo"], g["normal"], g["depth"], dev(mv),
+                                                 None, None, W, H, x24))
+    assert torch.all(x24[14:] == 0)
+    # input-gradient mapping, in its two halves
+    gx = rng.standard_normal((24, H, W)).astype(np.float32)
+    gL0 = torch.zeros(3, H, W, device="cuda")
+    gs = torch.zeros(H * W, device="cuda")
+    bnd.check(bnd.spp_denoiser_features_backward(dev(L0), dev(s), dev(gx), W, H, gL0, None))
+    assert torch.all(gs == 0)
+    bnd.check(bnd.spp_denoiser_features_backward(dev(L0), dev(s), dev(gx), W, H, None, gs))
+    rL0, rs = TS.denoiser_features_backward(L0, s, gx)
+    assert np.allclose(host(gL0), rL0, rtol=2e-6, atol=1e-7)
+    assert np.allclose(host(gs).reshape(H, W), rs, rtol=2e-6, atol=1e-7)
+
+
+def _demod_inputs(W, H, L, seed, temporal=True):
+    rng = np.random.default_rng(seed)
+    L0 = (rng.random((3, H, W)) * 3).astype(np.float32)
+    L0[:, rng.random((H, W)) < 0.6] = 0
+    c = rng.uniform(-2.5, 2.5, (3, H, W)).astype(np.float32)
+    c[0, 0, :4] = [9.0, -9.0, 8.5, -12.0]
+    logits = [z.astype(np.float32) for z in inp.random_logits(W, H, L, seed=seed, temporal=temporal)]
+    warped = (rng.random((3, H, W)) * 2).astype(np.float32) if temporal else None
+    mask = (rng.random((H, W)) < 0.1).astype(np.uint8) if temporal else None
+    return L0, c, logits, warped, mask
+
+
+def _gpu_demod_frame(spp, L0, c, logits, warped, mask, L, tm):
+    bnd = spp.binding
+    _, H, W = L0.shape
+    m = torch.empty(3, H, W, device="cuda")
+    layers = [torch.empty(3, H >> l, W >> l, device="cuda") for l in range(L)]
+    wd = torch.empty(3, H, W, device="cuda") if warped is not None else None
+    bnd.check(bnd.spp_demodulate(dev(L0), dev(c), None if warped is None else dev(warped), W, H, L,
+                                 m, layers, wd))
+    hats = [torch.empty(3, H >> l, W >> l, device="cuda") for l in range(L)]
+    lg = [dev(z) for z in logits]
+    mk = None if mask is None else dev(mask, torch.uint8)
+    for l in range(L - 1, -1, -1):
+        bnd.check(bnd.spp_reconstruct_level(layers[l], lg[l], lg[l].shape[0],
+                                            hats[l + 1] if l + 1 < L else None,
+                                            wd if l == 0 else None, mk if l == 0 else None,
+                                            W >> l, H >> l, None, hats[l], None))
+    hdr = torch.empty(3, H, W, device="cuda")
+    ldr = torch.empty(3, H, W, device="cuda")
+    bnd.check(bnd.spp_remodulate_tonemap(hats[0], m, W, H, tm, hdr, ldr))
+    return dict(m=m, layers=layers, wd=wd, hats=hats, hdr=hdr, ldr=ldr, lg=lg, mask=mk)
+
+
+@pytest.mark.parametrize("W,H,L,temporal", [(64, 32, 3, True), (96, 40, 3, False),
+                                             (1920, 1080, 3, True), (128, 64, 5, True)])
+def test_demodulated_frame_parity(spp, W, H, L, temporal):
+    L0, c, logits, warped, mask = _demod_inputs(W, H, L, W + H, temporal)
+    tm = spp.binding.make_tonemap(alpha=1.1, beta=0.9, exposure=0.3, shadow=0.4, highlight=0.6)
+    out = _gpu_demod_frame(spp, L0, c, logits, warped, mask, L, tm)
+    hdr, k = TS.reconstruct_demod(L0, c, logits, warped, mask, L)
+    assert np.allclose(host(out["m"]), k["m"], rtol=2e-6, atol=0)
+    for l in range(L):
+        assert np.allclose(host(out["layers"][l]), k["layers"][l], rtol=1e-5, atol=1e-30)
+    if warped is not None:
+        assert np.allclose(host(out["wd"]), k["Wd"], rtol=2e-6, atol=0)
+    got = host(out["hdr"])
+    assert np.all(np.abs(got - hdr) <= 1e-5 * np.abs(hdr) + 1e-30), \
+        float((np.abs(got - hdr) / np.maximum(np.abs(hdr), 1e-30)).max())
+    ldr = oracle.tonemap(hdr, 1.1, 0.9, 0.3, 0.4, 0.6)
+    assert np.allclose(host(out["ldr"]), ldr, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("W,H,temporal", [(64, 32, True), (48, 24, False), (512, 256, True)])
+def test_demodulated_frame_backward_parity(spp, W, H, temporal):
+    L = 3
+    L0, c, logits, warped, mask = _demod_inputs(W, H, L, 3 * W + H, temporal)
+    tm = spp.binding.make_tonemap()
+    out = _gpu_demod_frame(spp, L0, c, logits, warped, mask, L, tm)
+    bnd = spp.binding
+    g = np.random.default_rng(5).standard_normal((3, H, W)).astype(np.float32)
+    g_t = dev(g)
+    g_R = [torch.zeros(3, H >> l, W >> l, device="cuda") for l in range(L)]
+    g_n = [torch.zeros(3, H >> l, W >> l, device="cuda") for l in range(L)]
+    g_lg = [torch.empty_like(z) for z in out["lg"]]
+    g_wd = torch.zeros(3, H, W, device="cuda") if temporal else None
+    bnd.check(bnd.spp_remodulate_backward(g_t, out["m"], W, H, g_R[0]))
+    for l in range(L):
+        bnd.check(bnd.spp_reconstruct_level_backward(
+            out["layers"][l], out["lg"][l], out["lg"][l].shape[0],
+            out["hats"][l + 1] if l + 1 < L else None, out["wd"] if l == 0 else None,
+            out["mask"] if l == 0 else None, W >> l, H >> l, g_R[l], g_lg[l], g_n[l],
+            g_R[l + 1] if l + 1 < L else None, g_wd if l == 0 else None))
+    bnd.check(bnd.spp_pyramid_backward(g_n, W, H, L, g_n[0]))
+    g_L0 = torch.empty(3, H, W, device="cuda")
+    g_c = torch.empty(3, H, W, device="cuda")
+    bnd.check(bnd.spp_demodulate_backward(out["hdr"], g_t, out["layers"][0], g_n[0], out["wd"],
+                                          g_wd, dev(c), out["m"], W, H, g_L0, g_c))
+    r_lg, r_L0, r_c = TS.reconstruct_demod_backward(L0, c, logits, g, warped, mask, L)
+    for l in range(L):
+        assert_grad(host(g_lg[l]), r_lg[l], f"logits {l}", rtol=3e-4, afrac=3e-5)
+    assert_grad(host(g_L0), r_L0, "L0", rtol=1e-4, afrac=1e-5)
+    assert_grad(host(g_c), r_c, "c", rtol=3e-4, afrac=3e-5)
+    assert np.all(host(g_c)[0, 0, :4] == 0)
+
+
+def test_two_stage_training_beats_plain(spp):
+    """The sampler and the denoiser, trained jointly on the GPU through the
+    whole pipeline (remodulation, gather pyramid, demodulation, denoiser
+    input, splat, density), beat the plain method (uniform density, fixed
+    kernels) on held-out two-frame samples.  Both networks start as the
+    plain method (near-zero head weights; the denoiser's head biases are the
+    fixed logits, m = 1, zero latents), so any gain is learned."""
+    from paper_2602_08642_gb300 import learned as Lm
+    from paper_2602_08642_gb300 import two_stage as T2
+    size, budget = 64, 0.25
+    train = [Lm.FrameData(inp.training_pair(size, seed=100 + i)) for i in range(24)]
+    held = [Lm.FrameData(inp.training_pair(size, seed=900 + i)) for i in range(8)]
+    fb = inp.fixed_head_bias()
+    ts = torch.from_numpy(inp.unet_params(U.layers("sampler"), seed=3))
+    td = torch.from_numpy(inp.unet_params(
+        U.layers("denoiser"), seed=4,
+        head_bias={"h0": np.concatenate([fb["h0"][:54], np.zeros(10, np.float32)]),
+                   "h1": fb["h1"], "h2": fb["h2"]}))
+    fixed = [torch.from_numpy(a).cuda() for a in inp.fixed_logits(size, size, 3, True)]
+    plain = float(np.mean(Lm.evaluate(held, budget, None, fixed)))
+    start = float(np.mean(T2.evaluate(held, budget, ts, td)))
+    assert abs(start - plain) < 0.25  # the initial pipeline is the plain method
+    tr = T2.TwoStageTrainer(ts, td, 8, size, budget, lr=1e-3)
+    rng = np.random.default_rng(0)
+    losses = []
+    for k in range(200):
+        idx = rng.choice(len(train), 8, replace=False)
+        losses.append(tr.step([train[i] for i in idx], seed=1000 + 17 * k))
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-20:]) < np.mean(losses[:20])
+    for net in (tr.p.sampler, tr.p.denoiser):
+        assert spp.binding.spp_get_status(net.status) == 0
+    ours = float(np.mean(T2.evaluate(held, budget, tr.p.sampler.theta, tr.p.denoiser.theta)))
+    print(f"held-out PSNR: plain {plain:.2f} dB, two-stage start {start:.2f} dB, "
+          f"trained {ours:.2f} dB; loss {np.mean(losses[:20]):.4f} -> {np.mean(losses[-20:]):.4f}")
+    assert ours > plain + 1.0
