@@ -544,6 +544,99 @@ def run_learned(args, spp, Bnd, dev, rank):
         "kernel logits and density logit within 0.5-0.8 % RMS of the exact FP64 network "
         "(tests/test_gpu_unet.py::test_predict_parity); reconstruction given the logits within "
         "1e-5 relative (tests/test_gpu_parity.py)")
+    del net
+    out["two_stage"] = run_two_stage(args, spp, Bnd, dev, rank, frames, refs, W, H, F, peaks,
+                                     peak_kind)
+    return out
+
+
+def run_two_stage(args, spp, Bnd, dev, rank, frames, refs, W, H, F, peaks, peak_kind):
+    """The two-stage pipeline (sampler network, rendering, denoiser network
+    with learned demodulation and shared latents), trained on the GPU like
+    the joint predictor, on the same frames: per-frame time (every step from
+    the sampler's feature assembly to the tone-mapped output) and PSNR."""
+    import torch
+
+    import spp_inputs as inp
+    from paper_2602_08642_gb300 import learned as Lm
+    from paper_2602_08642_gb300 import two_stage as T2
+
+    train = [Lm.FrameData(inp.training_pair(128, seed=100 + i + 1000 * rank)) for i in range(32)]
+    fb = inp.fixed_head_bias()
+    ts = torch.from_numpy(inp.unet_params(T2.layer_table(Bnd.SPP_NET_SAMPLER), seed=3))
+    td = torch.from_numpy(inp.unet_params(
+        T2.layer_table(Bnd.SPP_NET_DENOISER), seed=4,
+        head_bias={"h0": np.concatenate([fb["h0"][:54], np.zeros(10, np.float32)]),
+                   "h1": fb["h1"], "h2": fb["h2"]}))
+    tr = T2.TwoStageTrainer(ts, td, 8, 128, 0.25, lr=1e-3)
+    rng = np.random.default_rng(rank)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    for k in range(args.train_steps):
+        idx = rng.choice(len(train), 8, replace=False)
+        losses.append(tr.step([train[i] for i in idx], seed=1000 + 17 * k))
+    torch.cuda.synchronize()
+    train_ms = (time.perf_counter() - t0) * 1e3 / max(args.train_steps, 1)
+    theta_s, theta_d = tr.p.sampler.theta, tr.p.denoiser.theta
+    del tr, train
+
+    stream = torch.cuda.current_stream()
+    flops = T2.flops_per_frame(W, H)
+    out = {"pipeline": "sampler features -> sampler U-Net (BF16 tcgen05) -> density softmax -> "
+                       "sample map -> renderer stand-in -> splat -> denoiser features -> "
+                       "denoiser U-Net -> demodulation + pyramid -> gather pyramid with the "
+                       "temporal term -> remodulation + tone map; latents warped to the next "
+                       "frame",
+           "training": {"steps": args.train_steps, "crop": 128, "batch": 8, "spp": 0.25,
+                        "ms_per_step": train_ms, "loss_first20": float(np.mean(losses[:20])),
+                        "loss_last20": float(np.mean(losses[-20:]))},
+           "networks": {"gflop_per_frame": flops / 1e9}, "budgets": {}}
+    p = None
+    for budget in (0.125, 0.25, 0.5):
+        p = T2.TwoStage(theta_s, theta_d, 1, W, H, budget)
+        x_of = lambda k: frames[k % F]  # noqa: E731
+        p.begin_sequence()
+        psnr = []
+        for k in range(F):  # one coherent pass: PSNR of frames 1..F-1
+            x = x_of(k)
+            p.frame([x], [x["mv"]], [x["clean"]], 0, k)
+            if k > 0:
+                p.ref[0].copy_(refs[k])
+                psnr.append(p.psnr(0))
+        steps = 12
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(F, F + steps):
+            x = x_of(k)
+            p.frame([x], [x["mv"]], [x["clean"]], 0, k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        for fr in p.frames:
+            fr.check_status()
+        out["budgets"][str(budget)] = {"ms": e0.elapsed_time(e1) / steps,
+                                       "psnr_db": float(np.mean(psnr))}
+        if budget != 0.5:
+            del p
+    # the two networks alone, on the last frame's inputs
+    reps = 10
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        p.sampler.forward()
+        p.denoiser.forward()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    tflops = flops / (ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    out["networks"].update({"ms": ms, "tflops": tflops, "bf16_peak_tflops": peak,
+                            "frac_of_bf16_peak": tflops / peak, "peak_kind": peak_kind})
+    del p
     return out
 
 

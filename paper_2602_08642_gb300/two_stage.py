@@ -42,6 +42,19 @@ def _zeros(*shape, dtype=torch.float32):
     return torch.zeros(*shape, dtype=dtype, device="cuda")
 
 
+def layer_table(net: int):
+    """[(name, cin, cout, relu)] of the present layers of network `net`, in
+    parameter order (from the library)."""
+    names = ("e0a", "e0b", "e1a", "e1b", "e2a", "e2b", "h2", "d1a", "d1b", "h1", "d0a", "d0b",
+             "h0")
+    out = []
+    for i, n in enumerate(names):
+        cin, cout, relu = B.spp_net_layer(net, i)
+        if cout:
+            out.append((n, cin, cout, relu))
+    return out
+
+
 def flops_per_frame(W: int, H: int) -> int:
     """Multiply-adds x 2 of one sampler and one denoiser forward pass."""
     total = 0
