@@ -1,0 +1,120 @@
+"""Oracles of the pipeline variants of Sec. 7 (ablations): the
+low-resolution density map and the systematic (exact-integer-total)
+rounding of the sample map.
+
+TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: the tests,
+``__graft_entry__.smoke()`` and the CPU baseline leg of ``bench.py`` call it;
+the product never imports it.
+
+Low-resolution density (Sec. 7, the density predicted at full resolution is
+brought to a quarter of the pixels before the stochastic sampling).  Reading:
+P = nearest upsampling of the f x f block means (f = 2: a quarter of the
+pixels), applied to the density before the budget normalisation.  P is a
+symmetric projection (block-constant images are fixed, <P a, b> = <a, P b>),
+so the same map takes the gradient with respect to P d back to d.  The block
+mean is summed in FP32 as a pairwise tree (each row of the block: adjacent
+pairs, then pairs of pairs; then the row sums the same way, top to bottom)
+and scaled by 1/f^2 (exact), so the GPU reproduces it bit for bit and a
+block-constant image is an exact fixed point.
+
+Systematic rounding (the exact-integer-total reading of the budget of Sec. 3:
+the realised sample count is fixed to within one sample instead of varying
+by about sqrt(B N)).  Every pixel's interval of length s_i is laid end to end
+on one line, shifted by one frame offset U; pixel i receives the integers
+its interval covers.  In 32.32 fixed point, exactly and independently of
+the summation order:
+  q_i = round-to-nearest-even(s_i 2^32)       (s_i of Sec. 3, FP64)
+  P_i = q_0 + ... + q_i (P_-1 = 0),  A_i = P_{i-1} + U,  U in [0, 2^32)
+  offsets_i = floor(A_i / 2^32),  n_i = offsets_{i+1} - offsets_i,
+  T = floor((P_{N-1} + U) / 2^32)
+so n_i = f_i + extra_i with f_i = floor(q_i / 2^32) and extra_i iff
+a_i + p_i >= 1, a_i = (A_i mod 2^32) 2^-32, p_i = (q_i mod 2^32) 2^-32: the
+stochastic test of Sec. 4.2 with u_i replaced by the position a_i of the
+pixel's interval on the integer grid (over a uniform U, E[n_i] = q_i 2^-32).
+The holdout weight of an extra sample is the relaxed ramp of Sec. 4.3 at
+u = a_i (h, lambda as for the stochastic map; hard mode: 1).
+U = the top 32 bits of element 2^62 of the SplitMix64 stream of
+(seed, frame) (key = mix(seed + (frame + 1) gamma), element i = mix(key +
+(i + 1) gamma)).
+
+Pins (tests/test_oracle_variants_pins.py): block-constant images are fixed
+points, the sum is preserved (FP64), symmetry, agreement with a library
+reshape-mean, and the density gradient through P against finite
+differences; for the systematic map the total within one sample of B N,
+unbiasedness over all offsets U on a grid, evenly spaced samples for a
+constant density, and agreement with the C oracle's independent stochastic
+assignment at u = a_i.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def density_lowres(d, W: int, H: int, factor: int) -> np.ndarray:
+    """P d for d [H*W] (or [H][W]) FP32; returns FP32 [H*W]."""
+    f = int(factor)
+    d = np.asarray(d, np.float32).reshape(H, W)
+    if f not in (1, 2, 4, 8) or H % f or W % f:
+        raise ValueError("factor 1, 2, 4 or 8 dividing W and H")
+    def tree(parts):
+        while len(parts) > 1:
+            parts = [(parts[k] + parts[k + 1]).astype(np.float32) for k in range(0, len(parts), 2)]
+        return parts[0]
+
+    rows = [tree([d[r::f, c::f] for c in range(f)]) for r in range(f)]
+    mean = (tree(rows) * np.float32(1.0 / (f * f))).astype(np.float32)
+    return np.repeat(np.repeat(mean, f, axis=0), f, axis=1).reshape(-1)
+
+
+# ------------------------------------------------------ systematic rounding
+M64 = (1 << 64) - 1
+GAMMA = 0x9E3779B97F4A7C15
+
+
+def _mix(z: int) -> int:
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def systematic_offset(seed: int, frame: int) -> int:
+    key = _mix((seed + (frame + 1) * GAMMA) & M64)
+    return _mix((key + ((1 << 62) + 1) * GAMMA) & M64) >> 32
+
+
+class SystematicAlloc:
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def alloc_systematic(d, B: float, phi: float = 0.125, lam: float = 10.0, hard: bool = False,
+                     seed: int = 0x5EED, frame: int = 0, U: int | None = None):
+    """Systematic sample map of the FP32 density d [N] (Sec. 3 budget)."""
+    import oracle
+    rc, S, a, c = oracle.budget_coeffs(d, B, phi)
+    if rc != 0:
+        raise ValueError(f"budget rc={rc}")
+    d64 = np.asarray(d, np.float32).astype(np.float64).ravel()
+    s = a + c * d64                                   # FP64, product then sum
+    q = np.rint(np.ldexp(s, 32)).astype(np.int64)    # ties to even
+    if U is None:
+        U = systematic_offset(seed, frame)
+    P = np.concatenate([[0], np.cumsum(q)]).astype(np.int64)
+    A = P[:-1] + np.int64(U)
+    offsets = np.concatenate([A >> 32, [(P[-1] + np.int64(U)) >> 32]]).astype(np.int64)
+    f = q >> 32
+    p32 = q & 0xFFFFFFFF
+    a32 = A & 0xFFFFFFFF
+    extra = (a32 + p32) >= (1 << 32)
+    n = f + extra
+    assert np.array_equal(np.diff(offsets), n)
+    w = np.ones(d64.size)
+    if not hard:
+        h = (2.0 * lam) / (2.0 * lam - 1.0)
+        idx = np.flatnonzero(extra)
+        u = a32[idx].astype(np.float64) * 2.0 ** -32
+        pp = p32[idx].astype(np.float64) * 2.0 ** -32
+        r = (lam / pp) * ((u + pp) - 1.0)
+        w[idx] = h * np.clip(r, 0.0, 1.0)
+    return SystematicAlloc(counts=n, offsets=offsets, s=s, q=q, U=U, a32=a32, extra=extra,
+                           w=w.astype(np.float32), T=int(offsets[-1]))

@@ -1,0 +1,103 @@
+"""Pins of the variant oracles (oracle/variants.py) against closed forms,
+a library reshape-mean and finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.variants as V
+
+
+def _p64(d, W, H, f):
+    m = np.asarray(d, np.float64).reshape(H // f, f, W // f, f).mean(axis=(1, 3))
+    return np.repeat(np.repeat(m, f, axis=0), f, axis=1).reshape(-1)
+
+
+@pytest.mark.parametrize("f", [2, 4])
+def test_density_lowres_is_the_block_mean(f):
+    W, H = 24, 16
+    d = np.random.default_rng(f).lognormal(size=H * W).astype(np.float32)
+    got = V.density_lowres(d, W, H, f)
+    assert got.dtype == np.float32
+    assert np.allclose(got, _p64(d, W, H, f), rtol=1e-6, atol=0)
+    # block-constant images are fixed points (bit for bit), the sum is kept
+    assert np.array_equal(V.density_lowres(got, W, H, f), got)
+    assert abs(got.astype(np.float64).sum() - d.astype(np.float64).sum()) < 1e-5 * d.sum()
+    # symmetry <P a, b> = <a, P b> (FP64 projection)
+    b = np.random.default_rng(7).standard_normal(H * W)
+    assert abs(_p64(d, W, H, f) @ b - d.astype(np.float64) @ _p64(b, W, H, f)) < 1e-9 * np.abs(b).sum()
+
+
+def test_density_gradient_through_the_projection(orc):
+    """s = phi B + (1 - phi) B N (P d) / sum d with d = exp(z - max z): since
+    P is symmetric and keeps the sum, dLoss/dz is the density backward of
+    P applied to dLoss/ds (Sec. 3 normalisation); checked by central FD."""
+    W, H, f, B, phi = 8, 8, 2, 0.25, 0.125
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal(H * W)
+    g = rng.standard_normal(H * W)
+
+    def loss(zz):
+        d = np.exp(zz - zz.max())
+        s = B * phi + (1 - phi) * B * (H * W) * _p64(d, W, H, f) / d.sum()
+        return float(g @ s)
+
+    gz = orc.density_backward(z, _p64(g, W, H, f), B, phi)
+    for i in range(0, H * W, 5):
+        zp, zm = z.copy(), z.copy()
+        zp[i] += 1e-6
+        zm[i] -= 1e-6
+        fd = (loss(zp) - loss(zm)) / 2e-6
+        assert abs(fd - gz[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gz[i])
+
+
+# ------------------------------------------------------ systematic rounding
+@pytest.mark.parametrize("B,seed", [(0.25, 1), (0.125, 2), (1.7, 3)])
+def test_systematic_total_is_the_budget(orc, B, seed):
+    """T = floor((sum q + U) / 2^32) is within one sample of B N (the q_i
+    round s_i to 2^-33, and sum s_i = B N up to FP64 rounding)."""
+    W, H = 64, 48
+    d = np.random.default_rng(seed).lognormal(sigma=1.5, size=W * H).astype(np.float32)
+    a = V.alloc_systematic(d, B, seed=seed, frame=4)
+    assert a.T == (int(a.q.sum()) + a.U) >> 32
+    assert abs(a.T - B * W * H) < 1 + W * H * 2.0 ** -32
+    f = a.q >> 32
+    assert np.all((a.counts == f) | (a.counts == f + 1))
+    assert a.offsets[0] == 0 and np.all(np.diff(a.offsets) >= 0)
+
+
+def test_systematic_is_unbiased_over_the_offset(orc):
+    """Over all frame offsets U on the 2^-12 grid, the mean count of every
+    pixel is q_i 2^-32 to within 2^-12 (its interval covers q_i 2^-32
+    integers on average)."""
+    d = np.random.default_rng(5).lognormal(size=12).astype(np.float32)
+    counts = np.zeros(12)
+    K = 1 << 12
+    for k in range(K):
+        counts += V.alloc_systematic(d, 0.4, U=k << 20).counts
+    mean = counts / K
+    assert np.all(np.abs(mean - V.alloc_systematic(d, 0.4, U=0).q * 2.0 ** -32) <= 2.0 ** -12 + 1e-12)
+
+
+def test_systematic_constant_density_is_evenly_spaced(orc):
+    W, H = 32, 8
+    d = np.ones(W * H, np.float32)
+    a = V.alloc_systematic(d, 0.25, seed=9)
+    idx = np.flatnonzero(a.counts)
+    assert a.T == 64 and np.all(np.diff(idx) == 4)  # every 4th pixel
+
+
+def test_systematic_decision_is_the_stochastic_rule_at_u_a(orc):
+    """The C oracle's stochastic assignment (Sec. 4.2-4.3), given s = q 2^-32
+    and u = a_i, returns the same counts and ramp weights."""
+    W, H = 40, 20
+    d = np.random.default_rng(6).lognormal(size=W * H).astype(np.float32)
+    a = V.alloc_systematic(d, 0.6, seed=3, frame=2)
+    for i in range(W * H):
+        s = float(a.q[i]) * 2.0 ** -32
+        u = float(a.a32[i]) * 2.0 ** -32
+        if abs(u - (1.0 - (s - np.floor(s)))) < 1e-12:
+            continue  # the tie a + p = 1 (the ramp is 0 there either way)
+        n, w, e = orc.assign_one(s, u, 10.0, False)
+        assert n == a.counts[i], i
+        if e:
+            assert abs(w - float(a.w[i])) <= 1e-6 * max(1.0, abs(w)), i
