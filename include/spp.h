@@ -652,6 +652,41 @@ int spp_demodulate_backward(const float *out_hdr, const float *grad_out, const f
                             const float *c, const float *m, int W, int H, float *grad_L0,
                             float *grad_c, cudaStream_t stream);
 
+/* ------------------------------------------ f4: variants of the pipeline */
+/* Systematic (exact-integer-total) sample map: the reading of the budget of
+ * Sec. 3 in which the realised total is fixed to within one sample.  The
+ * pixels' intervals of length s_i (the same s_i as spp_alloc_sample_map) are
+ * laid end to end from a frame offset U and every pixel receives the
+ * integers its interval covers; in 32.32 fixed point (exact, independent of
+ * the summation order):
+ *   q_i = s_i 2^32 rounded to nearest even, P_i = q_0 + ... + q_i,
+ *   offsets_i = (P_{i-1} + U) >> 32, n_i = offsets_{i+1} - offsets_i,
+ *   T = (P_{N-1} + U) >> 32  (|T - B N| < 1 + N 2^-32),
+ * U = the top 32 bits of element 2^62 of the (seed, frame) stream.  n_i is
+ * floor(q_i 2^-32) plus one extra sample iff a_i + p_i >= 1 with a_i the
+ * fractional position (P_{i-1} + U) mod 2^32 and p_i = q_i mod 2^32 (both
+ * times 2^-32): the stochastic test of Sec. 4.2 at u = a_i; its holdout
+ * weight is the ramp of Sec. 4.3 at u = a_i (1 in hard mode).  Arguments,
+ * outputs and workspace as spp_alloc_sample_map (SPP_FLAG_TEST_STALL_TILE1
+ * is rejected: this map has no waits between blocks). */
+int spp_alloc_sample_map_systematic(const float *d, int W, int H, const spp_params *p,
+                                    int32_t *counts, int32_t *offsets, int32_t *sample_pixel,
+                                    int64_t capacity, float *s_out, float *holdout_w,
+                                    int64_t *total, int32_t *status, void *ws, size_t ws_bytes,
+                                    cudaStream_t stream);
+
+/* Low-resolution density map (the ablation of Sec. 7 that samples from a
+ * density at a quarter of the pixels): out = P d, every factor x factor
+ * block (factor 1, 2, 4 or 8 dividing W and H) replaced by its mean, summed
+ * in FP32 as a pairwise tree (each row of the block: adjacent pairs, then
+ * pairs of pairs; then the row sums, top to bottom) and scaled by
+ * 1/factor^2.  P is a symmetric projection that keeps the sum, so the same
+ * call maps the gradient with respect to out (grad_s of the allocation) to
+ * the gradient with respect to d before spp_density_backward.  out may
+ * equal d. */
+int spp_density_lowres(const float *d, int W, int H, int factor, float *out,
+                       cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

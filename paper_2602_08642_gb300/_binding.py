@@ -135,6 +135,9 @@ _SIGS = {
     "spp_remodulate_tonemap": (_I, [_P, _P, _I, _I, ctypes.POINTER(spp_tonemap), _P, _P, _P]),
     "spp_remodulate_backward": (_I, [_P, _P, _I, _I, _P, _P]),
     "spp_demodulate_backward": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P, _P, _P]),
+    "spp_alloc_sample_map_systematic": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _P, _P,
+                                             _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "spp_density_lowres": (_I, [_P, _I, _I, _I, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -600,3 +603,19 @@ def spp_demodulate_backward(out_hdr, grad_out, L0d, grad_L0d, Wd, grad_Wd, c, m,
                                        _dev(grad_L0d, f), _dev(Wd, f), _dev(grad_Wd, f),
                                        _dev(c, f), _dev(m, f), W, H, _dev(grad_L0, f),
                                        _dev(grad_c, f), _stream(stream))
+
+
+# ------------------------------------------------- f4: pipeline variants
+def spp_alloc_sample_map_systematic(d, W, H, params: spp_params, counts, offsets, sample_pixel,
+                                    capacity, s_out, holdout_w, total, status, ws,
+                                    stream=None) -> int:
+    return lib.spp_alloc_sample_map_systematic(
+        _dev(d, torch.float32), W, H, ctypes.byref(params), _dev(counts, torch.int32),
+        _dev(offsets, torch.int32), _dev(sample_pixel, torch.int32), int(capacity),
+        _dev(s_out, torch.float32), _dev(holdout_w, torch.float32), _dev(total, torch.int64),
+        _dev(status, torch.int32), _dev(ws), _nbytes(ws), _stream(stream))
+
+
+def spp_density_lowres(d, W, H, factor, out, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_density_lowres(_dev(d, f), W, H, int(factor), _dev(out, f), _stream(stream))

@@ -611,6 +611,132 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
     (void)num_tiles;
 }
 
+// ------------------------------------------------- systematic rounding
+// The exact-integer-total variant: pixel intervals of length s_i laid end to
+// end from a frame offset U, in 32.32 fixed point (q_i = s_i 2^32 rounded to
+// nearest even, an exact integer prefix P):
+//   offsets_i = (P_{i-1} + U) >> 32, n_i = offsets_{i+1} - offsets_i,
+//   extra_i iff a_i + p_i >= 2^32 with a_i = (P_{i-1} + U) mod 2^32 and
+//   p_i = q_i mod 2^32; the holdout ramp of Sec. 4.3 at u = a_i 2^-32.
+// Reduce-then-scan with no waits between blocks: tile sums of q, one block
+// scans them, then every tile scans its own pixels from its prefix.
+__device__ __forceinline__ long long fixed_q(float d, double a, double c) {
+    const double sd = __dadd_rn(a, __dmul_rn(c, static_cast<double>(d)));
+    return __double2ll_rn(__dmul_rn(sd, 4294967296.0));
+}
+
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long &total) {
+    __shared__ long long s_w[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    long long before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+        const long long t = s_w[w];
+        if (w < warp) before += t;
+        all += t;
+    }
+    __syncthreads();  // s_w may be reused by the caller's next scan
+    total = all;
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+sys_tile_sum_kernel(const float *__restrict__ d, long long N, const AllocHeader *hdr,
+                    long long *__restrict__ tile_sums) {
+    const long long base = static_cast<long long>(blockIdx.x) * kTile +
+                           static_cast<long long>(threadIdx.x) * kScanItems;
+    const int valid = hdr->valid;
+    const double a = hdr->a, c = hdr->c;
+    long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (base + q < N && valid) sum += fixed_q(d[base + q], a, c);
+    long long total;
+    (void)block_excl_scan_ll(sum, total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of the tile sums in place, one block.
+__global__ void __launch_bounds__(kScanThreads)
+sys_scan_tiles_kernel(long long *__restrict__ tile_sums, int num_tiles) {
+    const int per = (num_tiles + kScanThreads - 1) / kScanThreads;
+    const int t0 = static_cast<int>(threadIdx.x) * per;
+    long long mine = 0;
+    for (int k = 0; k < per && t0 + k < num_tiles; ++k) mine += tile_sums[t0 + k];
+    long long total;
+    long long run = block_excl_scan_ll(mine, total);
+    for (int k = 0; k < per && t0 + k < num_tiles; ++k) {
+        const long long v = tile_sums[t0 + k];
+        tile_sums[t0 + k] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+sys_assign_kernel(const float *__restrict__ d, long long N, const AllocHeader *hdr,
+                  const long long *__restrict__ tile_prefix, unsigned long long U, int hard,
+                  int32_t *__restrict__ counts, int32_t *__restrict__ offsets,
+                  int32_t *__restrict__ sample_pixel, long long capacity,
+                  float *__restrict__ s_out, float *__restrict__ w_out, long long *total,
+                  int32_t *status) {
+    const long long base = static_cast<long long>(blockIdx.x) * kTile +
+                           static_cast<long long>(threadIdx.x) * kScanItems;
+    const int valid = hdr->valid;
+    const double a = hdr->a, c = hdr->c, lam = hdr->lam, h = hdr->h;
+    long long qv[kScanItems];
+    long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        qv[q] = (base + q < N && valid) ? fixed_q(d[base + q], a, c) : 0;
+        sum += qv[q];
+    }
+    long long tot;
+    long long A = tile_prefix[blockIdx.x] + block_excl_scan_ll(sum, tot) +
+                  static_cast<long long>(U);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const long long i = base + q;
+        if (i >= N) break;
+        const long long f = qv[q] >> 32;
+        const unsigned long long p32 = static_cast<unsigned long long>(qv[q]) & 0xFFFFFFFFull;
+        const unsigned long long a32 = static_cast<unsigned long long>(A) & 0xFFFFFFFFull;
+        const bool extra = a32 + p32 >= (1ull << 32);
+        const int n = static_cast<int>(f) + (extra ? 1 : 0);
+        const int off = static_cast<int>(A >> 32);
+        double wd = 1.0;
+        if (extra && !hard) {
+            const double u = __dmul_rn(static_cast<double>(a32), 0x1p-32);
+            const double p = __dmul_rn(static_cast<double>(p32), 0x1p-32);
+            const double r0 = __dmul_rn(__ddiv_rn(lam, p), __dsub_rn(__dadd_rn(u, p), 1.0));
+            wd = __dmul_rn(h, r0 < 0.0 ? 0.0 : (r0 > 1.0 ? 1.0 : r0));
+        }
+        offsets[i] = off;
+        if (counts) counts[i] = n;
+        s_out[i] = valid ? __double2float_rn(__dadd_rn(a, __dmul_rn(c, static_cast<double>(d[i]))))
+                         : 1.0f;
+        w_out[i] = __double2float_rn(wd);
+        for (int r = 0; r < n; ++r) {
+            const long long t = static_cast<long long>(off) + r;
+            if (t < capacity) sample_pixel[t] = static_cast<int32_t>(i);
+        }
+        A += qv[q];
+        if (i == N - 1) {
+            const long long T = A >> 32;
+            offsets[N] = static_cast<int32_t>(T);
+            *total = T;
+            if (T > capacity) set_status(status, SPP_ERR_CAPACITY);
+        }
+    }
+}
+
 }  // namespace
 
 size_t alloc_tiles(long long N) { return static_cast<size_t>((N + kTile - 1) / kTile); }
@@ -632,7 +758,7 @@ namespace {
 int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &dither,
                int32_t *counts, int32_t *offsets, int32_t *sample_pixel, int64_t capacity,
                float *s_out, float *holdout_w, int64_t *total, int32_t *status, void *ws,
-               size_t ws_bytes, cudaStream_t stream) {
+               size_t ws_bytes, cudaStream_t stream, bool systematic = false) {
     if (!p || W < 0 || H < 0 || capacity < 0) return SPP_ERR_ARG;
     if (static_cast<long long>(W) * H == 0) {  // empty frame: T = 0, offsets[0] = 0
         if (!offsets || !total) return SPP_ERR_ARG;
@@ -680,6 +806,19 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     budget_sum_kernel<<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(d, N, hdr, args,
                                                                              status);
     const int num_tiles = static_cast<int>(alloc_tiles(N));
+    if (systematic) {
+        // the frame offset U: the top 32 bits of element 2^62 of the stream
+        const unsigned long long U =
+            stream_bits(stream_key(p->seed, p->frame), 1ull << 62) >> 32;
+        auto *tile_sums = reinterpret_cast<long long *>(tiles);
+        sys_tile_sum_kernel<<<num_tiles, kScanThreads, 0, stream>>>(d, N, hdr, tile_sums);
+        sys_scan_tiles_kernel<<<1, kScanThreads, 0, stream>>>(tile_sums, num_tiles);
+        sys_assign_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
+            d, N, hdr, tile_sums, U, args.hard, counts, offsets, sample_pixel, capacity, s_out,
+            holdout_w, reinterpret_cast<long long *>(total), status);
+        count_launch(4);
+        return launch_status();
+    }
     Dither dt = dither;
     dt.W = W;
     assign_scan_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
@@ -701,6 +840,16 @@ int spp_alloc_sample_map(const float *d, int W, int H, const spp_params *p, int3
                          size_t ws_bytes, cudaStream_t stream) {
     return spp::alloc_impl(d, W, H, p, spp::Dither{}, counts, offsets, sample_pixel, capacity,
                            s_out, holdout_w, total, status, ws, ws_bytes, stream);
+}
+
+int spp_alloc_sample_map_systematic(const float *d, int W, int H, const spp_params *p,
+                                    int32_t *counts, int32_t *offsets, int32_t *sample_pixel,
+                                    int64_t capacity, float *s_out, float *holdout_w,
+                                    int64_t *total, int32_t *status, void *ws, size_t ws_bytes,
+                                    cudaStream_t stream) {
+    if (p && (p->flags & SPP_FLAG_TEST_STALL_TILE1)) return SPP_ERR_ARG;
+    return spp::alloc_impl(d, W, H, p, spp::Dither{}, counts, offsets, sample_pixel, capacity,
+                           s_out, holdout_w, total, status, ws, ws_bytes, stream, true);
 }
 
 int spp_alloc_sample_map_dithered(const float *d, int W, int H, const spp_params *p,

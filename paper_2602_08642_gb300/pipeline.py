@@ -76,6 +76,14 @@ class Frame:
                                                 self.alloc_ws, stream),
                 "spp_alloc_sample_map_dithered")
 
+    def alloc_systematic(self, d: torch.Tensor, params: B.spp_params, stream=None):
+        """alloc with systematic (exact-integer-total) rounding."""
+        B.check(B.spp_alloc_sample_map_systematic(d, self.W, self.H, params, self.counts,
+                                                  self.offsets, self.sample_pixel, self.capacity,
+                                                  self.s, self.holdout_w, self.total,
+                                                  self.status, self.alloc_ws, stream),
+                "spp_alloc_sample_map_systematic")
+
     def render(self, clean: torch.Tensor, seed: int, frame: int, stream=None):
         B.check(B.spp_render_synthetic(clean, self.offsets, self.sample_pixel, self.total,
                                        self.capacity, self.W, self.H, seed, frame, self.rgb,

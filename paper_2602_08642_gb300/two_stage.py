@@ -70,8 +70,20 @@ class TwoStage:
     """Sampler + denoiser state for batches of B frames of W x H."""
 
     def __init__(self, theta_s: torch.Tensor, theta_d: torch.Tensor, B_: int, W: int, H: int,
-                 budget: float, train: bool = False, dither_mask=None):
+                 budget: float, train: bool = False, dither_mask=None, density_factor: int = 1,
+                 rounding: str = "stochastic"):
+        """density_factor > 1 samples from the density averaged over
+        factor x factor blocks (the low-resolution density map of Sec. 7);
+        rounding "systematic" uses the exact-integer-total sample map
+        (inference only: the splat's backward recomputes the white-noise
+        uniforms of the stochastic map)."""
+        if rounding not in ("stochastic", "systematic"):
+            raise ValueError("rounding must be 'stochastic' or 'systematic'")
+        if rounding == "systematic" and (train or dither_mask is not None):
+            raise ValueError("systematic rounding is an inference-time variant")
         self.B, self.W, self.H, self.budget, self.train = B_, W, H, budget, train
+        self.density_factor, self.rounding = density_factor, rounding
+        self.d_lr = [_zeros(H, W) for _ in range(B_)] if density_factor > 1 else None
         self.sampler = Predictor(theta_s, B_, W, H, train, net=B.SPP_NET_SAMPLER)
         self.denoiser = Predictor(theta_d, B_, W, H, train, net=B.SPP_NET_DENOISER,
                                   input_grad=train)
@@ -106,9 +118,15 @@ class TwoStage:
     def begin_sequence(self):
         self.has_prev = False
 
-    def _alloc(self, fr, d, params):
+    def _alloc(self, b, fr, d, params):
+        if self.density_factor > 1:
+            B.check(B.spp_density_lowres(d, self.W, self.H, self.density_factor, self.d_lr[b]),
+                    "density lowres")
+            d = self.d_lr[b]
         if self.dither is not None:
             fr.alloc_dithered(d, params, self.dither)
+        elif self.rounding == "systematic":
+            fr.alloc_systematic(d, params)
         else:
             fr.alloc(d, params)
 
@@ -136,7 +154,7 @@ class TwoStage:
             fr = self.frames[b]
             self.params[b] = B.make_params(self.budget, uniform_fraction=PHI, seed=seed + b,
                                            frame=frame_index)
-            self._alloc(fr, sp.density[b], self.params[b])
+            self._alloc(b, fr, sp.density[b], self.params[b])
             fr.render(cleans[b], (seed + b) ^ 0xC0FFEE, frame_index)
             fr.splat()
             g = gbufs[b]
@@ -235,6 +253,9 @@ class TwoStage:
                 "splat backward")
         B.check(B.spp_denoiser_features_backward(fr.layers[0], fr.s, dn.g_x[b], W, H, None,
                                                  self.g_s), "features backward")
+        if self.density_factor > 1:  # P is symmetric: the same map on the gradient
+            B.check(B.spp_density_lowres(self.g_s, W, H, self.density_factor, self.g_s),
+                    "density lowres backward")
         B.check(B.spp_density_backward(sp.density[b], W * H, self.budget, PHI, self.g_s,
                                        sp.g_heads[0][b, 0], self.dbws), "density backward")
 
@@ -247,15 +268,16 @@ class TwoStage:
 
 class TwoStageTrainer:
     """Trains the sampler and the denoiser jointly on two-frame samples
-    (learned.FrameData); options as learned.Trainer."""
+    (learned.FrameData); options as learned.Trainer, plus density_factor (the
+    low-resolution density map)."""
 
     def __init__(self, theta_s, theta_d, batch: int, size: int, budget: float = 0.25,
                  lr: float = 1e-3, weight_decay: float = 1e-4, objective: str = "l1",
                  betas=(0.9, 0.999), random_tmo: bool = False, total_steps: int | None = None,
-                 seed: int = 0, dither_mask=None):
+                 seed: int = 0, dither_mask=None, density_factor: int = 1):
         import numpy as np
         self.p = TwoStage(theta_s, theta_d, batch, size, size, budget, train=True,
-                          dither_mask=dither_mask)
+                          dither_mask=dither_mask, density_factor=density_factor)
         self.lr, self.wd = lr, weight_decay
         self.objective, self.betas, self.random_tmo = objective, betas, random_tmo
         self.total_steps = total_steps
@@ -298,10 +320,12 @@ class TwoStageTrainer:
 
 
 def evaluate(samples: list, budget: float, theta_s, theta_d, seed: int = 99,
-             dither_mask=None) -> list[float]:
+             dither_mask=None, density_factor: int = 1,
+             rounding: str = "stochastic") -> list[float]:
     """PSNR of frame t of each two-frame sample (as learned.evaluate)."""
     W, H = samples[0].W, samples[0].H
-    p = TwoStage(theta_s, theta_d, 1, W, H, budget, dither_mask=dither_mask)
+    p = TwoStage(theta_s, theta_d, 1, W, H, budget, dither_mask=dither_mask,
+                 density_factor=density_factor, rounding=rounding)
     out = []
     for i, s in enumerate(samples):
         p.begin_sequence()

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings_and_version():
     import paper_2602_08642_gb300 as spp
-    assert spp.spp_abi_version() == 5
+    assert spp.spp_abi_version() == 6
     for code in range(0, -9, -1):
         assert spp.spp_strerror(code) and spp.spp_strerror(code) != "unknown status code"
     assert spp.spp_strerror(-99) == "unknown status code"
