@@ -37,13 +37,34 @@ U = the top 32 bits of element 2^62 of the SplitMix64 stream of
 (seed, frame) (key = mix(seed + (frame + 1) gamma), element i = mix(key +
 (i + 1) gamma)).
 
+Gradient estimators of the discretisation (the ablation of Sec. 7 that
+compares the relaxed ramp of Sec. 4.3 with the straight-through estimator,
+Bengio et al. 2013, and the Gumbel-softmax / binary concrete relaxation,
+Jang et al. 2017, Maddison et al. 2017), with L^0 = (sum_{k<f} S_k +
+e w S_f) / s per pixel (Eq. stoch_rnoisy), f = floor(s), p = s - f:
+  straight-through  forward: the hard rule e = [u > 1 - p], w = 1; backward:
+                    de/dp := 1, so dL^0/ds = (S_f - L^0) / s, where S_f is the
+                    sample of slot f, rendered for the gradient when the
+                    forward did not trace it (the paper trains on
+                    pre-rendered samples, so every slot exists)
+  Gumbel-softmax    forward (training): the extra sample is always traced
+                    (p > 0) with weight w = sigma(lambda (ln(p / (1 - p)) +
+                    ln(u / (1 - u)))), lambda the inverse temperature;
+                    backward: dw/dp = lambda w (1 - w) / (p (1 - p)); at test
+                    time the hard rule, w > 1/2 iff u > 1 - p
+DASR's surrogate (Kuznetsov et al. 2018) is not defined in the paper and is
+not built.
+
 Pins (tests/test_oracle_variants_pins.py): block-constant images are fixed
 points, the sum is preserved (FP64), symmetry, agreement with a library
 reshape-mean, and the density gradient through P against finite
 differences; for the systematic map the total within one sample of B N,
 unbiasedness over all offsets U on a grid, evenly spaced samples for a
 constant density, and agreement with the C oracle's independent stochastic
-assignment at u = a_i.
+assignment at u = a_i; for the estimators: the Gumbel relaxation's gradient
+against finite differences of its forward, its hard limit (lambda -> inf) is
+the stochastic map, and the straight-through gradient against its closed
+form on one pixel.
 """
 from __future__ import annotations
 
@@ -118,3 +139,69 @@ def alloc_systematic(d, B: float, phi: float = 0.125, lam: float = 10.0, hard: b
         w[idx] = h * np.clip(r, 0.0, 1.0)
     return SystematicAlloc(counts=n, offsets=offsets, s=s, q=q, U=U, a32=a32, extra=extra,
                            w=w.astype(np.float32), T=int(offsets[-1]))
+
+
+# ------------------------------------------------ gradient estimators
+def gumbel_weight(p, u, lam):
+    """sigma(lam (ln(p / (1 - p)) + ln(u / (1 - u)))), FP64."""
+    p = np.asarray(p, np.float64)
+    u = np.asarray(u, np.float64)
+    with np.errstate(divide="ignore", over="ignore"):
+        x = lam * (np.log(p / (1.0 - p)) + np.log(u / (1.0 - u)))
+        return 1.0 / (1.0 + np.exp(-x))
+
+
+def alloc_gumbel(d, B: float, phi: float = 0.125, lam: float = 10.0, seed: int = 0x5EED,
+                 frame: int = 0):
+    """Training-time sample map of the Gumbel-softmax estimator: every pixel
+    with p > 0 gets its extra sample, weighted by the relaxed indicator."""
+    import oracle
+    rc, S, a, c = oracle.budget_coeffs(d, B, phi)
+    if rc != 0:
+        raise ValueError(f"budget rc={rc}")
+    d64 = np.asarray(d, np.float32).astype(np.float64).ravel()
+    s = a + c * d64
+    f = np.floor(s)
+    p = s - f
+    u = np.array([oracle.pixel_uniform(seed, frame, i) for i in range(s.size)])
+    extra = p > 0.0
+    n = f.astype(np.int64) + extra
+    w = np.where(extra, gumbel_weight(np.where(extra, p, 0.5), u, lam), 1.0)
+    offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+    return SystematicAlloc(counts=n, offsets=offsets, s=s, w=w.astype(np.float32), extra=extra,
+                           u=u, p=p, T=int(offsets[-1]))
+
+
+def splat_backward_estimator(a, rgb, L0, grad_L0, estimator: str, lam: float = 10.0,
+                             clean=None, render_seed: int = 0, frame: int = 0) -> np.ndarray:
+    """dLoss/ds of the splat under the straight-through or Gumbel-softmax
+    estimator; a: the allocation (counts, offsets, s, extra; for Gumbel its
+    weights w and p), rgb [T][3] the traced samples."""
+    import oracle
+    rgb = np.asarray(rgb, np.float64).reshape(-1, 3)
+    L0 = np.asarray(L0, np.float64).reshape(3, -1)
+    g = np.asarray(grad_L0, np.float64).reshape(3, -1)
+    s = np.asarray(a.s, np.float64)
+    N = s.size
+    out = -(g * L0).sum(axis=0) / s
+    if estimator == "gumbel":
+        for i in np.flatnonzero(a.extra):
+            w = float(a.w[i])
+            p = float(a.p[i])
+            dw = lam * w * (1.0 - w) / (p * (1.0 - p))
+            S = rgb[a.offsets[i + 1] - 1]
+            out[i] += float(g[:, i] @ S) * dw / s[i]
+    elif estimator == "straight_through":
+        clean = np.asarray(clean, np.float64).reshape(3, -1)
+        for i in range(N):
+            f = int(np.floor(s[i]))
+            if s[i] - f <= 0.0:
+                continue
+            if a.counts[i] > f:
+                S = rgb[a.offsets[i + 1] - 1]
+            else:  # the untraced sample of slot f
+                S = clean[:, i] * oracle.sample_noise(render_seed, frame, i, f)
+            out[i] += float(g[:, i] @ S) / s[i]
+    else:
+        raise ValueError(estimator)
+    return out

@@ -101,3 +101,69 @@ def test_systematic_decision_is_the_stochastic_rule_at_u_a(orc):
         assert n == a.counts[i], i
         if e:
             assert abs(w - float(a.w[i])) <= 1e-6 * max(1.0, abs(w)), i
+
+
+# ------------------------------------------------ gradient estimators
+def _gumbel_case(orc, W=12, H=8, B=0.6, lam=4.0):
+    d = np.random.default_rng(21).lognormal(size=W * H).astype(np.float32)
+    a = V.alloc_gumbel(d, B, lam=lam, seed=31, frame=2)
+    clean, _ = __import__("spp_inputs").scene(W, H, seed=5)
+    rgb = orc.render(clean, a.offsets, 0xC0FFEE, 2)
+    return a, rgb, clean, W, H
+
+
+def test_gumbel_gradient_matches_fd(orc):
+    """With u and the traced set fixed, L^0 is a smooth function of s: the
+    estimator's gradient is its exact derivative."""
+    lam = 4.0
+    a, rgb, clean, W, H = _gumbel_case(orc, lam=lam)
+    g = np.random.default_rng(22).standard_normal((3, H * W))
+    f = np.floor(a.s)
+
+    def L0_of(s):
+        w = np.where(a.extra, V.gumbel_weight(np.where(a.extra, s - f, 0.5), a.u, lam), 1.0)
+        return orc.splat(a.offsets, rgb, s, w, a.extra, W, H, 1)[0].reshape(3, -1)
+
+    L0 = L0_of(a.s)
+    grad = V.splat_backward_estimator(a, rgb, L0, g, "gumbel", lam=lam)
+    for i in np.flatnonzero(a.extra)[:25]:
+        if not (1e-4 < a.p[i] < 1 - 1e-4):
+            continue
+        sp, sm = a.s.copy(), a.s.copy()
+        sp[i] += 1e-7
+        sm[i] -= 1e-7
+        fd = float((g * (L0_of(sp) - L0_of(sm))).sum()) / 2e-7
+        assert abs(fd - grad[i]) <= 1e-5 * max(1.0, abs(fd)), (i, fd, grad[i])
+
+
+def test_gumbel_hard_limit_is_the_stochastic_rule(orc):
+    """As lambda grows, w -> [u > 1 - p]: the test-time decision of the
+    Gumbel estimator is the stochastic map of Sec. 4.2."""
+    W, H = 16, 16
+    d = np.random.default_rng(23).lognormal(size=W * H).astype(np.float32)
+    a = V.alloc_gumbel(d, 0.4, lam=1e9, seed=7, frame=1)
+    ref = orc.alloc(d, 0.4, hard=True, seed=7, frame=1)
+    hard_extra = a.extra & (a.w > 0.5)
+    assert np.array_equal(np.floor(a.s).astype(np.int64) + hard_extra, ref.counts)
+
+
+def test_straight_through_uses_the_renderers_sample(orc):
+    """The untraced sample of slot f is the renderer stand-in's sample of
+    that slot (the one it returns when the pixel gets f + 1 samples), and
+    dLoss/ds = sum_c g_c (S_f,c - L^0_c) / s on a pixel with p > 0."""
+    W, H = 6, 4
+    d = np.random.default_rng(24).lognormal(size=W * H).astype(np.float32)
+    a = orc.alloc(d, 0.7, hard=True, seed=9, frame=3)
+    clean, _ = __import__("spp_inputs").scene(W, H, seed=6)
+    rgb = orc.render(clean, a.offsets, 0xBEEF, 3)
+    L0 = orc.splat(a.offsets, rgb, a.s, a.w, a.extra, W, H, 1)[0].reshape(3, -1)
+    g = np.random.default_rng(25).standard_normal((3, H * W))
+    grad = V.splat_backward_estimator(a, rgb, L0, g, "straight_through", clean=clean,
+                                      render_seed=0xBEEF, frame=3)
+    i = int(np.flatnonzero((a.counts == np.floor(a.s)) & (a.s > np.floor(a.s)))[0])
+    more = a.counts.copy()
+    more[i] += 1  # the same frame with one more sample on pixel i
+    off2 = np.concatenate([[0], np.cumsum(more)])
+    S_f = orc.render(clean, off2, 0xBEEF, 3)[off2[i + 1] - 1]
+    expect = float(g[:, i] @ (S_f - L0[:, i])) / a.s[i]
+    assert abs(grad[i] - expect) <= 1e-12 * max(1.0, abs(expect))
