@@ -45,6 +45,12 @@ extern "C" {
 /* Holdout weighting of the extra sample. */
 #define SPP_HOLDOUT_RAMP 0 /* relaxed ramp of Eq. relaxed_holdout with h of Eq. h_factor */
 #define SPP_HOLDOUT_HARD 1 /* hard step of Eq. holdout (the lambda -> inf limit), weight 1 */
+/* training forward of the Gumbel-softmax estimator (the ablation of Sec. 7):
+ * every pixel with p > 0 gets its extra sample, weighted by
+ * sigma(lambda (ln(p / (1 - p)) + ln(u / (1 - u)))), lambda the inverse
+ * temperature; the count map then exceeds B N (capacity for about N (1 + B)
+ * samples).  Not with the systematic map. */
+#define SPP_HOLDOUT_GUMBEL 2
 
 /* spp_params.flags */
 #define SPP_FLAG_EXACT_FP64 1u /* evaluate every pixel on the FP64 path (no FP32 filter) */
@@ -60,7 +66,7 @@ typedef struct spp_params {
     double lambda;           /* ramp temperature, >= 1; the paper uses 10 */
     uint64_t seed;           /* seed of the per-pixel uniforms u_i */
     uint32_t frame;          /* frame index t (selects the uniform stream) */
-    int32_t holdout_mode;    /* SPP_HOLDOUT_RAMP or SPP_HOLDOUT_HARD */
+    int32_t holdout_mode;    /* SPP_HOLDOUT_RAMP, SPP_HOLDOUT_HARD or SPP_HOLDOUT_GUMBEL */
     uint32_t flags;          /* SPP_FLAG_* */
     uint32_t reserved;       /* must be 0 */
 } spp_params;
@@ -674,6 +680,32 @@ int spp_alloc_sample_map_systematic(const float *d, int W, int H, const spp_para
                                     int64_t capacity, float *s_out, float *holdout_w,
                                     int64_t *total, int32_t *status, void *ws, size_t ws_bytes,
                                     cudaStream_t stream);
+
+/* Gradient estimators of the discretisation (the ablation of Sec. 7):
+ * dLoss/ds of the splat (grad_s, OVERWRITTEN) with L^0 = (sum_{k<f} S_k +
+ * e w S_f) / s, f = floor(s), p = s - f:
+ *   SPP_ESTIMATOR_RELAXED           the relaxed ramp of Sec. 4.3, exactly
+ *                                   spp_splat_backward
+ *   SPP_ESTIMATOR_STRAIGHT_THROUGH  forward with SPP_HOLDOUT_HARD; de/dp := 1,
+ *                                   so sum_c g_c (S_f,c - L^0_c) / s on every
+ *                                   pixel with p > 0, S_f the traced extra
+ *                                   sample, or, where the forward traced none,
+ *                                   the renderer stand-in's sample of slot f
+ *                                   (clean and render_seed as given to
+ *                                   spp_render_synthetic, frame p->frame)
+ *   SPP_ESTIMATOR_GUMBEL            forward with SPP_HOLDOUT_GUMBEL; dw/dp =
+ *                                   lambda w (1 - w) / (p (1 - p)) with w =
+ *                                   holdout_w of the forward
+ * Other arguments as spp_splat_backward; clean is read by the
+ * straight-through estimator only. */
+#define SPP_ESTIMATOR_RELAXED 0
+#define SPP_ESTIMATOR_STRAIGHT_THROUGH 1
+#define SPP_ESTIMATOR_GUMBEL 2
+int spp_splat_backward_estimator(const int32_t *offsets, const int32_t *counts, const float *rgb,
+                                 const float *s, const float *layer0, const float *grad_layer0,
+                                 const float *holdout_w, int64_t capacity, int W, int H,
+                                 const spp_params *p, int estimator, const float *clean,
+                                 uint64_t render_seed, float *grad_s, cudaStream_t stream);
 
 /* Low-resolution density map (the ablation of Sec. 7 that samples from a
  * density at a quarter of the pixels): out = P d, every factor x factor

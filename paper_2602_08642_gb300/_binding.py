@@ -35,6 +35,10 @@ SPP_ERR_CUDA = -8
 
 SPP_HOLDOUT_RAMP = 0
 SPP_HOLDOUT_HARD = 1
+SPP_HOLDOUT_GUMBEL = 2
+SPP_ESTIMATOR_RELAXED = 0
+SPP_ESTIMATOR_STRAIGHT_THROUGH = 1
+SPP_ESTIMATOR_GUMBEL = 2
 SPP_FLAG_EXACT_FP64 = 1
 SPP_FLAG_TEST_STALL_TILE1 = 1 << 31
 
@@ -138,6 +142,8 @@ _SIGS = {
     "spp_alloc_sample_map_systematic": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _P, _P,
                                              _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "spp_density_lowres": (_I, [_P, _I, _I, _I, _P, _P]),
+    "spp_splat_backward_estimator": (_I, [_P, _P, _P, _P, _P, _P, _P, _I64, _I, _I,
+                                          ctypes.POINTER(spp_params), _I, _P, _U64, _P, _P]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(lib, _name)
@@ -206,10 +212,10 @@ def spp_alloc_workspace_bytes(W: int, H: int) -> int:
 
 
 def make_params(budget: float, *, uniform_fraction: float = 0.125, lam: float = 10.0,
-                seed: int = 0x5EED, frame: int = 0, hard: bool = False,
+                seed: int = 0x5EED, frame: int = 0, hard: bool = False, gumbel: bool = False,
                 exact_fp64: bool = False) -> spp_params:
-    return spp_params(budget, uniform_fraction, lam, seed & 0xFFFFFFFFFFFFFFFF, frame,
-                      SPP_HOLDOUT_HARD if hard else SPP_HOLDOUT_RAMP,
+    mode = SPP_HOLDOUT_GUMBEL if gumbel else (SPP_HOLDOUT_HARD if hard else SPP_HOLDOUT_RAMP)
+    return spp_params(budget, uniform_fraction, lam, seed & 0xFFFFFFFFFFFFFFFF, frame, mode,
                       SPP_FLAG_EXACT_FP64 if exact_fp64 else 0, 0)
 
 
@@ -619,3 +625,14 @@ def spp_alloc_sample_map_systematic(d, W, H, params: spp_params, counts, offsets
 def spp_density_lowres(d, W, H, factor, out, stream=None) -> int:
     f = torch.float32
     return lib.spp_density_lowres(_dev(d, f), W, H, int(factor), _dev(out, f), _stream(stream))
+
+
+def spp_splat_backward_estimator(offsets, counts, rgb, s, layer0, grad_layer0, holdout_w, capacity,
+                                 W, H, params: spp_params, estimator: int, clean, render_seed,
+                                 grad_s, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_splat_backward_estimator(
+        _dev(offsets, torch.int32), _dev(counts, torch.int32), _dev(rgb, f), _dev(s, f),
+        _dev(layer0, f), _dev(grad_layer0, f), _dev(holdout_w, f), int(capacity), W, H,
+        ctypes.byref(params), int(estimator), _dev(clean, f), render_seed & 0xFFFFFFFFFFFFFFFF,
+        _dev(grad_s, f), _stream(stream))

@@ -53,6 +53,10 @@ struct BudgetArgs {
     int force_exact;
 };
 
+// Holdout modes of the assignment (SPP_HOLDOUT_*): 0 ramp, 1 hard, 2 the
+// training forward of the Gumbel-softmax estimator.
+constexpr int kModeGumbel = 2;
+
 // ---------------------------------------------------------------- K1
 // Every finite FP32 x >= 0 is m 2^(pos - 149) with an integer m < 2^24 and
 // pos in [0, 253].  A thread keeps a 128-bit integer sum of m 2^(pos - 32 b)
@@ -326,6 +330,22 @@ __device__ __noinline__ PixelOut assign_exact(float d, uint64_t bits, double ka,
     const double f = floor(sd);
     const double p = __dsub_rn(sd, f);
     const double t = __dsub_rn(1.0, p);
+    if (hard == kModeGumbel) {
+        // binary concrete relaxation: the extra sample is always traced,
+        // weighted by sigma(lambda (ln(p / (1 - p)) + ln(u / (1 - u))))
+        PixelOut r;
+        const bool extra = p > 0.0;
+        double wd = 1.0;
+        if (extra) {
+            const double x = __dmul_rn(klam, __dadd_rn(log(__ddiv_rn(p, t)),
+                                                       log(__ddiv_rn(u, __dsub_rn(1.0, u)))));
+            wd = __ddiv_rn(1.0, __dadd_rn(1.0, exp(-x)));
+        }
+        r.n = static_cast<int>(f) + (extra ? 1 : 0);
+        r.w = __double2float_rn(wd);
+        r.s = __double2float_rn(sd);
+        return r;
+    }
     const bool extra = (p > 0.0) && (u > t);
     double wd = 1.0;
     if (extra && !hard) {
@@ -771,9 +791,13 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     if (capacity > 0 && !sample_pixel) return SPP_ERR_ARG;
     if (!(p->budget > 0.0) || !(p->budget < 1e30)) return SPP_ERR_ARG;
     if (!(p->uniform_fraction >= 0.0) || !(p->uniform_fraction <= 1.0)) return SPP_ERR_ARG;
-    if (p->holdout_mode != SPP_HOLDOUT_RAMP && p->holdout_mode != SPP_HOLDOUT_HARD)
+    if (p->holdout_mode != SPP_HOLDOUT_RAMP && p->holdout_mode != SPP_HOLDOUT_HARD &&
+        p->holdout_mode != SPP_HOLDOUT_GUMBEL)
         return SPP_ERR_ARG;
     if (p->holdout_mode == SPP_HOLDOUT_RAMP && !(p->lambda >= 1.0 && p->lambda < 1e30))
+        return SPP_ERR_ARG;
+    if (p->holdout_mode == SPP_HOLDOUT_GUMBEL &&
+        (!(p->lambda > 0.0 && p->lambda < 1e30) || systematic))
         return SPP_ERR_ARG;
     if (p->reserved != 0 || (p->flags & ~(SPP_FLAG_EXACT_FP64 | SPP_FLAG_TEST_STALL_TILE1)) != 0)
         return SPP_ERR_ARG;
@@ -794,9 +818,12 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     BudgetArgs args;
     args.budget = p->budget;
     args.phi = p->uniform_fraction;
-    args.lambda = p->holdout_mode == SPP_HOLDOUT_RAMP ? p->lambda : 1.0;
-    args.hard = p->holdout_mode == SPP_HOLDOUT_HARD;
-    args.force_exact = (p->flags & SPP_FLAG_EXACT_FP64) ? 1 : 0;
+    args.lambda = p->holdout_mode == SPP_HOLDOUT_HARD ? 1.0 : p->lambda;
+    args.hard = p->holdout_mode == SPP_HOLDOUT_HARD ? 1
+                : p->holdout_mode == SPP_HOLDOUT_GUMBEL ? kModeGumbel
+                                                        : 0;
+    // the Gumbel forward decides every pixel in FP64 (no float-float filter)
+    args.force_exact = ((p->flags & SPP_FLAG_EXACT_FP64) || args.hard == kModeGumbel) ? 1 : 0;
 
     const long long per_block = static_cast<long long>(kSumThreads) * 32;
     long long grid = (N + per_block - 1) / per_block;

@@ -12,6 +12,7 @@
 // added to global memory with atomics, so their summation order (and the
 // last bits of those gradients) may vary from run to run.
 #include "recon_common.cuh"
+#include "render_common.cuh"
 
 namespace spp {
 namespace {
@@ -419,6 +420,51 @@ splat_backward_kernel(const int32_t *__restrict__ offsets, const int32_t *__rest
     grad_s[i] = acc;
 }
 
+// Straight-through (estimator 1) and Gumbel-softmax (estimator 2) gradients
+// of the splat with respect to s; see spp_splat_backward_estimator.
+__global__ void __launch_bounds__(256)
+splat_backward_est_kernel(const int32_t *__restrict__ offsets, const int32_t *__restrict__ counts,
+                          const float4 *__restrict__ rgb, const float *__restrict__ s,
+                          const float *__restrict__ L0, const float *__restrict__ gL0,
+                          const float *__restrict__ hw, long long N, long long capacity,
+                          int estimator, float lam, const float *__restrict__ clean,
+                          uint64_t render_key, float *__restrict__ grad_s) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float si = s[i];
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc -= gL0[c * N + i] * L0[c * N + i] / si;
+    const float f = floorf(si);
+    const float p = si - f;
+    const int n = counts[i];
+    const bool extra = n > static_cast<int>(f) && p > 0.0f;
+    const long long last = static_cast<long long>(offsets[i]) + n - 1;
+    float3 S = make_float3(0.f, 0.f, 0.f);
+    float scale = 0.0f;
+    if (estimator == 2) {
+        if (extra && last >= 0 && last < capacity) {
+            const float w = hw[i];
+            scale = lam * w * (1.0f - w) / (p * (1.0f - p));
+            const float4 v = rgb[last];
+            S = make_float3(v.x, v.y, v.z);
+        }
+    } else if (p > 0.0f) {
+        scale = 1.0f;
+        if (extra && last >= 0 && last < capacity) {
+            const float4 v = rgb[last];
+            S = make_float3(v.x, v.y, v.z);
+        } else {  // the sample of slot f, which the forward did not trace
+            const float g = render_factor(render_key, static_cast<uint64_t>(i),
+                                          static_cast<uint64_t>(f));
+            S = make_float3(clean[i] * g, clean[N + i] * g, clean[2 * N + i] * g);
+        }
+    }
+    if (scale != 0.0f)
+        acc += (gL0[i] * S.x + gL0[N + i] * S.y + gL0[2 * N + i] * S.z) * scale / si;
+    grad_s[i] = acc;
+}
+
 // Density backward, pass 1: sum d and sum d g (FP64 accumulation).
 __global__ void __launch_bounds__(256)
 density_reduce_kernel(const float *__restrict__ d, const float *__restrict__ g, long long N,
@@ -629,6 +675,37 @@ int spp_splat_backward(const int32_t *offsets, const int32_t *counts, const floa
         offsets, counts, reinterpret_cast<const float4 *>(rgb), s, layer0, grad_layer0, N, capacity,
         stream_key(p->seed, p->frame), static_cast<float>(lam), static_cast<float>(h), hard ? 1 : 0,
         grad_s);
+    count_launch();
+    return launch_status();
+}
+
+int spp_splat_backward_estimator(const int32_t *offsets, const int32_t *counts, const float *rgb,
+                                 const float *s, const float *layer0, const float *grad_layer0,
+                                 const float *holdout_w, int64_t capacity, int W, int H,
+                                 const spp_params *p, int estimator, const float *clean,
+                                 uint64_t render_seed, float *grad_s, cudaStream_t stream) {
+    using namespace spp;
+    if (estimator == SPP_ESTIMATOR_RELAXED)
+        return spp_splat_backward(offsets, counts, rgb, s, layer0, grad_layer0, capacity, W, H, p,
+                                  grad_s, stream);
+    if (estimator != SPP_ESTIMATOR_STRAIGHT_THROUGH && estimator != SPP_ESTIMATOR_GUMBEL)
+        return SPP_ERR_ARG;
+    if (!p || W < 0 || H < 0 || capacity < 0 || !offsets || !counts || !s || !layer0 ||
+        !grad_layer0 || !grad_s || (capacity > 0 && !rgb))
+        return SPP_ERR_ARG;
+    if (estimator == SPP_ESTIMATOR_GUMBEL && (!holdout_w || !(p->lambda > 0.0)))
+        return SPP_ERR_ARG;
+    if (estimator == SPP_ESTIMATOR_STRAIGHT_THROUGH && !clean) return SPP_ERR_ARG;
+    if (!aligned16(offsets) || !aligned16(counts) || !aligned16(s) || !aligned16(layer0) ||
+        !aligned16(grad_layer0) || !aligned16(grad_s) || (rgb && !aligned16(rgb)) ||
+        (holdout_w && !aligned16(holdout_w)) || (clean && !aligned16(clean)))
+        return SPP_ERR_ALIGN;
+    const long long N = static_cast<long long>(W) * H;
+    if (N == 0) return SPP_OK;
+    splat_backward_est_kernel<<<static_cast<unsigned>((N + 255) / 256), 256, 0, stream>>>(
+        offsets, counts, reinterpret_cast<const float4 *>(rgb), s, layer0, grad_layer0, holdout_w,
+        N, capacity, estimator, static_cast<float>(p->lambda), clean,
+        stream_key(render_seed, p->frame), grad_s);
     count_launch();
     return launch_status();
 }

@@ -1,5 +1,6 @@
 // a4: renderer stand-in, and a5: normalised splat (Eq. stoch_rnoisy) with the
 // average-pool pyramid (Eq. app-pyramid) of arXiv 2602.08642.
+#include "render_common.cuh"
 #include "spp_internal.cuh"
 
 namespace spp {
@@ -8,8 +9,7 @@ namespace {
 constexpr int kRenderThreads = 256;
 
 // Sample t of the list: pixel i = sample_pixel[t], slot k = t - offsets[i];
-// value clean_i * exp(0.8 Z - 0.32) with Z from Box-Muller on two 24-bit
-// uniforms of the pixel's SplitMix64 counters (2k+1, 2k+2).
+// value clean_i * render_factor(key, i, k).
 __global__ void __launch_bounds__(kRenderThreads)
 render_kernel(const float *__restrict__ clean, const int32_t *__restrict__ offsets,
               const int32_t *__restrict__ sample_pixel, const long long *__restrict__ total,
@@ -22,23 +22,7 @@ render_kernel(const float *__restrict__ clean, const int32_t *__restrict__ offse
         const int i = sample_pixel[t];
         if (i < 0 || i >= N) continue;
         const uint64_t k = static_cast<uint64_t>(t - offsets[i]);
-        const uint64_t hp = stream_bits(key, static_cast<uint64_t>(i));
-        const uint64_t b1 = mix64(hp + (2ull * k + 1ull) * kGamma);
-        const uint64_t b2 = mix64(hp + (2ull * k + 2ull) * kGamma);
-        // ln u1 with u1 = (m + 1/2) 2^-24 taken exactly: below 1/2 u1 itself is
-        // exact in FP32; above it 1 - u1 = (2(2^24 - m) - 1) 2^-25 is, and
-        // log1p keeps the steep sqrt(-2 ln u1) near u1 = 1 accurate.
-        const uint32_t m1 = static_cast<uint32_t>(b1 >> 40);
-        float lnu;
-        if (m1 < (1u << 23)) {
-            lnu = logf(static_cast<float>(2u * m1 + 1u) * 0x1p-25f);
-        } else {
-            const uint32_t q = (1u << 24) - m1;
-            lnu = log1pf(-static_cast<float>(2u * q - 1u) * 0x1p-25f);
-        }
-        const float u2 = static_cast<float>(static_cast<uint32_t>(b2 >> 40)) * 0x1p-24f;
-        const float z = sqrtf(-2.0f * lnu) * cospif(2.0f * u2);
-        const float g = expf(__fmaf_rn(0.8f, z, -0.32f));
+        const float g = render_factor(key, static_cast<uint64_t>(i), k);
         rgb[t] = make_float4(clean[i] * g, clean[N + i] * g, clean[2 * N + i] * g, 0.0f);
     }
 }

@@ -156,14 +156,34 @@ class FrameData:
         self.H, self.W = self.clean.shape[1:]
 
 
-class Renderer:
-    """Per-frame sampling / reconstruction state for B frames of W x H."""
+ESTIMATORS = {"relaxed": B.SPP_ESTIMATOR_RELAXED,
+              "straight_through": B.SPP_ESTIMATOR_STRAIGHT_THROUGH,
+              "gumbel": B.SPP_ESTIMATOR_GUMBEL}
+GUMBEL_LAMBDA = 10.0  # inverse temperature of the Gumbel-softmax relaxation
 
-    def __init__(self, B_: int, W: int, H: int, budget: float, dither_mask=None):
+
+class Renderer:
+    """Per-frame sampling / reconstruction state for B frames of W x H.
+
+    estimator selects the gradient of the discretisation (Sec. 4.3, and the
+    ablation of Sec. 7): "relaxed" (the ramp), "straight_through" (hard
+    forward) or "gumbel" (relaxed forward that traces every extra sample).
+    With train=False the straight-through and Gumbel models run the hard
+    test-time rule."""
+
+    def __init__(self, B_: int, W: int, H: int, budget: float, dither_mask=None,
+                 estimator: str = "relaxed", train: bool = True):
+        if estimator not in ESTIMATORS:
+            raise ValueError(f"unknown estimator {estimator}")
         self.B, self.W, self.H, self.budget = B_, W, H, budget
+        self.estimator, self.train = estimator, train
         # blue-noise rank mask (device int16 [T][T]) or None for white noise
         self.dither = dither_mask
-        self.frames = [Frame(W, H, LEVELS, max_budget=budget) for _ in range(B_)]
+        # the Gumbel forward traces the extra sample of every pixel
+        cap_budget = budget + 1.0 if (estimator == "gumbel" and train) else budget
+        self.frames = [Frame(W, H, LEVELS, max_budget=cap_budget) for _ in range(B_)]
+        self.cur_clean = [None] * B_
+        self.cur_seed = [0] * B_
         self.tm = B.make_tonemap()
         self.hdr_prev = [_zeros(3, H, W) for _ in range(B_)]
         self.warped = [_zeros(3, H, W) for _ in range(B_)]
@@ -196,7 +216,10 @@ class Renderer:
             fr.alloc(d, params)
 
     def params(self, frame: int, seed: int):
-        return B.make_params(self.budget, uniform_fraction=PHI, seed=seed, frame=frame)
+        gumbel = self.estimator == "gumbel" and self.train
+        hard = self.estimator != "relaxed" and not gumbel
+        return B.make_params(self.budget, uniform_fraction=PHI, seed=seed, frame=frame, hard=hard,
+                             gumbel=gumbel, lam=GUMBEL_LAMBDA if gumbel else 10.0)
 
     def previous_frame(self, b: int, d, logits, clean, seed: int, frame: int):
         """Frame t-1 of sample b (no temporal term); its output goes to hdr_prev[b]."""
@@ -218,6 +241,7 @@ class Renderer:
         for the backward), with the temporal term over warped[b]."""
         fr = self.frames[b]
         self.cur_params[b] = self.params(frame, seed)
+        self.cur_clean[b], self.cur_seed[b] = clean, seed ^ 0xC0FFEE
         self._alloc(fr, d, self.cur_params[b])
         fr.render(clean, seed ^ 0xC0FFEE, frame)
         fr.splat()
@@ -274,10 +298,10 @@ class Renderer:
                 self.g_warped if l == 0 else None), "level backward")
         B.check(B.spp_pyramid_backward(self.g_noisy, self.W, self.H, LEVELS, self.g_noisy[0]),
                 "pyramid backward")
-        B.check(B.spp_splat_backward(fr.offsets, fr.counts, fr.rgb, fr.s, fr.layers[0],
-                                     self.g_noisy[0], fr.capacity, self.W, self.H,
-                                     self.cur_params[b], self.g_s),
-                "splat backward")
+        B.check(B.spp_splat_backward_estimator(
+            fr.offsets, fr.counts, fr.rgb, fr.s, fr.layers[0], self.g_noisy[0], fr.holdout_w,
+            fr.capacity, self.W, self.H, self.cur_params[b], ESTIMATORS[self.estimator],
+            self.cur_clean[b], self.cur_seed[b], self.g_s), "splat backward")
         B.check(B.spp_density_backward(d, self.W * self.H, self.budget, PHI, self.g_s,
                                        g_logits[3], self.dws), "density backward")
 
@@ -308,10 +332,10 @@ class Trainer:
     def __init__(self, theta: torch.Tensor, batch: int, size: int, budget: float = 0.25,
                  lr: float = 1e-3, weight_decay: float = 1e-4, objective: str = "l1",
                  betas=(0.9, 0.999), random_tmo: bool = False, total_steps: int | None = None,
-                 seed: int = 0, dither_mask=None):
+                 seed: int = 0, dither_mask=None, estimator: str = "relaxed"):
         import numpy as np
         self.net = Predictor(theta, batch, size, size, train=True)
-        self.rnd = Renderer(batch, size, size, budget, dither_mask)
+        self.rnd = Renderer(batch, size, size, budget, dither_mask, estimator=estimator)
         self.lr, self.wd = lr, weight_decay
         self.objective, self.betas, self.random_tmo = objective, betas, random_tmo
         self.total_steps = total_steps
@@ -357,14 +381,15 @@ class Trainer:
 
 def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None,
              fixed_logits: list[torch.Tensor] | None = None, seed: int = 99,
-             temporal: list | None = None, dither_mask=None) -> list[float]:
+             temporal: list | None = None, dither_mask=None,
+             estimator: str = "relaxed") -> list[float]:
     """PSNR (tone-mapped sRGB against the tone-mapped clean image) of frame
     t of each sample.  theta None runs the plain method: uniform density
     d = 1 and the fixed logits (54 / 29 / 25 channels).  If ``temporal`` is
     a list, the temporal error mean |dI - dI_ref| of Eq. loss_temporal of
     each sample is appended to it."""
     W, H = samples[0].W, samples[0].H
-    rnd = Renderer(1, W, H, budget, dither_mask)
+    rnd = Renderer(1, W, H, budget, dither_mask, estimator=estimator, train=False)
     net = Predictor(theta, 1, W, H) if theta is not None else None
     ones = torch.ones(H, W, device="cuda")
     out = []
