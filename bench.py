@@ -545,9 +545,44 @@ def run_learned(args, spp, Bnd, dev, rank):
         "(tests/test_gpu_unet.py::test_predict_parity); reconstruction given the logits within "
         "1e-5 relative (tests/test_gpu_parity.py)")
     del net
+    out["estimator_ablation"] = run_estimator_ablation(args, spp, rank)
     out["two_stage"] = run_two_stage(args, spp, Bnd, dev, rank, frames, refs, W, H, F, peaks,
                                      peak_kind)
     return out
+
+
+def run_estimator_ablation(args, spp, rank):
+    """The gradient estimators of the discretisation (Sec. 4.3 and the
+    ablation of Sec. 7): the joint predictor trained from the same start
+    with the relaxed ramp, the straight-through estimator and the
+    Gumbel-softmax relaxation; held-out PSNR at 0.25 spp on 128 x 128
+    two-frame samples (each model with its own test-time rule)."""
+    import torch
+
+    import spp_inputs as inp
+    from paper_2602_08642_gb300 import learned as Lm
+
+    size, budget = 128, 0.25
+    steps = max(args.train_steps // 2, 1)
+    train = [Lm.FrameData(inp.training_pair(size, seed=100 + i + 1000 * rank)) for i in range(32)]
+    held = [Lm.FrameData(inp.training_pair(size, seed=5000 + i)) for i in range(8)]
+    fixed = [torch.from_numpy(a).cuda() for a in inp.fixed_logits(size, size, 3, True)]
+    res = {"steps": steps, "crop": size, "batch": 8, "spp": budget,
+           "plain_psnr_db": float(np.mean(Lm.evaluate(held, budget, None, fixed)))}
+    for est in ("relaxed", "straight_through", "gumbel"):
+        theta0 = torch.from_numpy(inp.unet_params(Lm.layer_table(), seed=5,
+                                                  head_bias=inp.fixed_head_bias()))
+        tr = Lm.Trainer(theta0, 8, size, budget, lr=1e-3, estimator=est)
+        rng = np.random.default_rng(rank)
+        losses = []
+        for k in range(steps):
+            idx = rng.choice(len(train), 8, replace=False)
+            losses.append(tr.step([train[i] for i in idx], seed=1000 + 17 * k))
+        res[est] = {"psnr_db": float(np.mean(Lm.evaluate(held, budget, tr.net.theta, None,
+                                                         estimator=est))),
+                    "loss_last20": float(np.mean(losses[-20:]))}
+        del tr
+    return res
 
 
 def run_two_stage(args, spp, Bnd, dev, rank, frames, refs, W, H, F, peaks, peak_kind):
@@ -620,6 +655,24 @@ def run_two_stage(args, spp, Bnd, dev, rank, frames, refs, W, H, F, peaks, peak_
                                        "psnr_db": float(np.mean(psnr))}
         if budget != 0.5:
             del p
+    # variants of Sec. 7 at 0.25 spp with the same trained networks: the
+    # low-resolution density map (2 x 2 blocks) and systematic rounding
+    variants = {}
+    for name, kw in (("lowres_density_2x2", dict(density_factor=2)),
+                     ("systematic_rounding", dict(rounding="systematic"))):
+        q = T2.TwoStage(theta_s, theta_d, 1, W, H, 0.25, **kw)
+        q.begin_sequence()
+        ps, totals = [], []
+        for k in range(F):
+            x = frames[k % F]
+            q.frame([x], [x["mv"]], [x["clean"]], 0, k)
+            totals.append(int(q.frames[0].total.item()))
+            if k > 0:
+                q.ref[0].copy_(refs[k])
+                ps.append(q.psnr(0))
+        variants[name] = {"psnr_db": float(np.mean(ps)), "samples_per_frame": totals}
+        del q
+    out["variants_at_0.25spp"] = variants
     # the two networks alone, on the last frame's inputs
     reps = 10
     torch.cuda.synchronize()
