@@ -200,6 +200,7 @@ __device__ void finalize_budget(AllocHeader *hdr, const unsigned long long *limb
     hdr->valid = 1;
 }
 
+template <int U>
 __global__ void __launch_bounds__(kSumThreads)
 budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, BudgetArgs args,
                   int32_t *status) {
@@ -215,14 +216,14 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
     const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const long long n4 = N >> 2;
     const float4 *d4 = reinterpret_cast<const float4 *>(d);
-    // eight independent vector loads in flight per thread and iteration; a
-    // warp whose 256 values all lie in the accumulators' span (the common
-    // case) takes the short path, decided by a warp vote so that the re-basing
-    // code stays out of it
-    for (long long q0 = gtid; q0 < n4; q0 += 8 * nthreads) {
-        float4 v4[8];
+    // U independent vector loads in flight per thread and iteration; a warp
+    // whose 128 U values all lie in the accumulators' span (the common case)
+    // takes the short path, decided by a warp vote so that the re-basing code
+    // stays out of it
+    for (long long q0 = gtid; q0 < n4; q0 += U * nthreads) {
+        float4 v4[U];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < U; ++r) {
             const long long q = q0 + r * nthreads;
             v4[r] = q < n4 ? __ldg(d4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -230,7 +231,7 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
         int wmin = 1 << 20, wmax = -(1 << 20);
         bool ok = true;
 #pragma unroll
-        for (int r = 0; r < 32; ++r) {
+        for (int r = 0; r < 4 * U; ++r) {
             const uint32_t bits = __float_as_uint(v[r]);
             const uint32_t mag = bits & 0x7fffffffu;
             ok &= mag < 0x7f800000u && bits == mag;  // finite, not negative
@@ -246,7 +247,7 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
         ok &= wmin >= A.b && wmax <= A.b + 1;
         if (__all_sync(__activemask(), ok)) {
 #pragma unroll
-            for (int r = 0; r < 32; ++r) {
+            for (int r = 0; r < 4 * U; ++r) {
                 const uint32_t mag = __float_as_uint(v[r]);
                 const uint32_t e = mag >> 23;
                 const unsigned long long m = (mag & 0x7fffffu) | (e ? 0x800000u : 0u);
@@ -259,7 +260,7 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < 32; ++r) accum_value(v[r], A, lim, bad);
+            for (int r = 0; r < 4 * U; ++r) accum_value(v[r], A, lim, bad);
         }
     }
     for (long long i = (n4 << 2) + gtid; i < N; i += nthreads) accum_value(d[i], A, lim, bad);
@@ -825,13 +826,16 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     // the Gumbel forward decides every pixel in FP64 (no float-float filter)
     args.force_exact = ((p->flags & SPP_FLAG_EXACT_FP64) || args.hard == kModeGumbel) ? 1 : 0;
 
-    const long long per_block = static_cast<long long>(kSumThreads) * 32;
+    // 8 values per thread and pass: enough blocks to fill every SM several
+    // times over (the per-element carry chain is latency-bound)
+    constexpr int kSumU = 2;
+    const long long per_block = static_cast<long long>(kSumThreads) * 4 * kSumU;
     long long grid = (N + per_block - 1) / per_block;
     const long long max_grid = static_cast<long long>(sm_count()) * 8;
     if (grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
-    budget_sum_kernel<<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(d, N, hdr, args,
-                                                                             status);
+    budget_sum_kernel<kSumU><<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(
+        d, N, hdr, args, status);
     const int num_tiles = static_cast<int>(alloc_tiles(N));
     if (systematic) {
         // the frame offset U: the top 32 bits of element 2^62 of the stream
