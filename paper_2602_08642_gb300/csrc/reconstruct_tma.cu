@@ -9,18 +9,18 @@
 //   logits  box 32 x 8 x C       (C = 25, 29 or 54 planes)
 //   noisy   box 40 x 12 x 3      (the tile plus a 2-pixel halo; x starts at
 //                                 x0 - 4 so that it is 16-byte aligned)
-//   motion  box 40 x 12 x 2      (full resolution only)
+//   warped  box 40 x 12 x 3      (full resolution only: W_t L_{t-1}, written
+//                                 by warp_prev_kernel, on the same halo)
 // NS stages are in flight, so HBM keeps streaming while the threads compute.
 // There is no CTA-wide barrier in the tile loop: each warp waits on the
 // stage's mbarrier, the last warp done with a stage refills it, and the two
 // warps of a pixel row meet on their own mbarrier.
-// Halo cells outside the image arrive zero-filled and are replaced by their
-// clamp-to-edge source in shared memory.  At full resolution the warped
-// previous frame W_t L_{t-1} on the tile's halo is built by the threads
-// (bilinear, each halo pixel with its own motion vector); its global loads for
-// tile k+1 are issued before tile k is computed, so their latency hides
-// behind that work.  Every mbarrier wait is bounded: on expiry the CTA records
-// SPP_ERR_TIMEOUT, waits (bounded) for its copies still in flight and exits.
+// Halo cells outside the image arrive zero-filled and are never read: tiles
+// whose 5 x 5 footprint crosses the border index their clamp-to-edge source
+// cells.  The coarser level's four upsampling taps and the disocclusion mask
+// are plain loads issued one tile ahead.  Every mbarrier wait is bounded: on
+// expiry the CTA records SPP_ERR_TIMEOUT, waits (bounded) for its copies
+// still in flight and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
