@@ -8,6 +8,10 @@
 //   assign_scan_kernel  per pixel: s_i = a + c d_i, n_i, holdout weight; a
 //                       single-pass decoupled look-back scan of n_i gives the
 //                       offsets; each pixel writes its slots of the sample list.
+// Frames of more than 64 tiles of 2048 pixels replace the second kernel by
+// two without waits between blocks (assign_tile_kernel: decisions, counts
+// and tile sums; offsets_kernel: tile prefix from the earlier tile sums,
+// local scan, offsets and sample list), which is faster at full resolution.
 //
 // Bit-exactness of the count map.  The decisions floor(s_i) and
 // u_i > 1 - p_i are those of FP64 round-to-nearest arithmetic.  FP64 is slow
@@ -29,6 +33,9 @@ constexpr int kWords = 13;       // carry-propagated 32-bit words of the total
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kTile = kScanThreads * kScanItems;
+// frames of at most this many tiles use the single-pass scan (one launch);
+// larger ones the two-pass form without waits between blocks
+constexpr int kSinglePassMaxTiles = 64;
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
@@ -632,6 +639,191 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
     (void)num_tiles;
 }
 
+// ------------------------------------------- two-pass form (large frames)
+// The same sample map without waits between blocks: assign_tile_kernel
+// decides every pixel (counts, s, holdout weight) and the sum of its tile;
+// offsets_kernel takes its tile's prefix as the sum of the earlier tiles'
+// sums, scans its pixels and writes the offsets and the sample list.  Used
+// when the frame has many tiles (the counts are an output anyway, so the
+// second pass re-reads them from L2); small frames keep the single pass.
+__global__ void __launch_bounds__(kScanThreads, 4)
+assign_tile_kernel(const float *__restrict__ d, long long N, const AllocHeader *hdr_c,
+                   uint64_t key, Dither dither, int hard, int32_t *__restrict__ counts,
+                   float *__restrict__ s_out, float *__restrict__ w_out,
+                   int *__restrict__ tile_sums) {
+    const int tile = blockIdx.x;
+    const long long base = static_cast<long long>(tile) * kTile +
+                           static_cast<long long>(threadIdx.x) * kScanItems;
+    Coef k;
+    const int valid = hdr_c->valid;
+    k.a = hdr_c->a;
+    k.c = hdr_c->c;
+    k.lam = hdr_c->lam;
+    k.h = hdr_c->h;
+    k.a_hi = hdr_c->a_hi;
+    k.a_lo = hdr_c->a_lo;
+    k.c_hi = hdr_c->c_hi;
+    k.c_lo = hdr_c->c_lo;
+    k.lam_f = hdr_c->lam_f;
+    k.h_f = hdr_c->h_f;
+    k.hard = hard;
+    k.fast = hdr_c->fast_ok;
+
+    float dv[kScanItems];
+    const bool full = base + kScanItems <= N;
+    if (full) {
+        const float4 v0 = __ldcs(reinterpret_cast<const float4 *>(d + base));
+        const float4 v1 = __ldcs(reinterpret_cast<const float4 *>(d + base) + 1);
+        dv[0] = v0.x; dv[1] = v0.y; dv[2] = v0.z; dv[3] = v0.w;
+        dv[4] = v1.x; dv[5] = v1.y; dv[6] = v1.z; dv[7] = v1.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) dv[q] = (base + q < N) ? d[base + q] : 0.0f;
+    }
+    int n[kScanItems];
+    float wv[kScanItems], sv[kScanItems];
+    int tsum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const long long i = base + q;
+        n[q] = 0;
+        wv[q] = 1.0f;
+        sv[q] = 1.0f;
+        if (i < N && valid) {
+            const uint64_t bits = dither.mask ? dither_bits(dither, i)
+                                              : stream_bits(key, static_cast<uint64_t>(i));
+            int nq = 0;
+            float wq = 1.0f, sq = 1.0f;
+            bool done = false;
+            if (k.fast) done = assign_fast(dv[q], bits, k, nq, wq, sq);
+            if (!done) {
+                const PixelOut r = assign_exact(dv[q], bits, k.a, k.c, k.lam, k.h, k.hard);
+                nq = r.n;
+                wq = r.w;
+                sq = r.s;
+            }
+            n[q] = nq;
+            wv[q] = wq;
+            sv[q] = sq;
+        }
+        tsum += n[q];
+    }
+    if (full) {
+        int4 *c4 = reinterpret_cast<int4 *>(counts + base);
+        c4[0] = make_int4(n[0], n[1], n[2], n[3]);
+        c4[1] = make_int4(n[4], n[5], n[6], n[7]);
+        float4 *s4 = reinterpret_cast<float4 *>(s_out + base);
+        s4[0] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+        s4[1] = make_float4(sv[4], sv[5], sv[6], sv[7]);
+        float4 *w4 = reinterpret_cast<float4 *>(w_out + base);
+        w4[0] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+        w4[1] = make_float4(wv[4], wv[5], wv[6], wv[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) {
+            if (base + q < N) {
+                counts[base + q] = n[q];
+                s_out[base + q] = sv[q];
+                w_out[base + q] = wv[q];
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, off);
+    __shared__ int s_w[kScanThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = tsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_w[w];
+        tile_sums[tile] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+offsets_kernel(const int32_t *__restrict__ counts, long long N, const int *__restrict__ tile_sums,
+               int num_tiles, int32_t *__restrict__ offsets, int32_t *__restrict__ sample_pixel,
+               long long capacity, long long *total, int32_t *status) {
+    const int tile = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int s_w[kScanThreads / 32];
+    __shared__ int s_pre;
+    // this tile's prefix: the sum of the earlier tiles' sums
+    int pre = 0;
+    for (int t = threadIdx.x; t < tile; t += kScanThreads) pre += tile_sums[t];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) pre += __shfl_down_sync(0xffffffffu, pre, off);
+    if (lane == 0) s_w[warp] = pre;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < kScanThreads / 32; ++w) t += s_w[w];
+        s_pre = t;
+    }
+    __syncthreads();
+    const long long base = static_cast<long long>(tile) * kTile +
+                           static_cast<long long>(threadIdx.x) * kScanItems;
+    int n[kScanItems];
+    const bool full = base + kScanItems <= N;
+    if (full) {
+        const int4 c0 = reinterpret_cast<const int4 *>(counts + base)[0];
+        const int4 c1 = reinterpret_cast<const int4 *>(counts + base)[1];
+        n[0] = c0.x; n[1] = c0.y; n[2] = c0.z; n[3] = c0.w;
+        n[4] = c1.x; n[5] = c1.y; n[6] = c1.z; n[7] = c1.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) n[q] = base + q < N ? counts[base + q] : 0;
+    }
+    int tsum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) tsum += n[q];
+    int incl = tsum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    __syncthreads();  // s_w is reused
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    int before = 0;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w)
+        if (w < warp) before += s_w[w];
+    int run = s_pre + before + incl - tsum;
+    int off[kScanItems];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        off[q] = run;
+        run += n[q];
+    }
+    if (full) {
+        int4 *o4 = reinterpret_cast<int4 *>(offsets + base);
+        o4[0] = make_int4(off[0], off[1], off[2], off[3]);
+        o4[1] = make_int4(off[4], off[5], off[6], off[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q)
+            if (base + q < N) offsets[base + q] = off[q];
+    }
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        for (int r = 0; r < n[q]; ++r) {
+            const long long t = static_cast<long long>(off[q]) + r;
+            if (t < capacity) sample_pixel[t] = static_cast<int32_t>(base + q);
+        }
+    }
+    // the owner of the last pixel closes the scan
+    if (base <= N - 1 && N - 1 < base + kScanItems) {
+        offsets[N] = run;
+        *total = run;
+        if (static_cast<long long>(run) > capacity) set_status(status, SPP_ERR_CAPACITY);
+    }
+    (void)num_tiles;
+}
+
 // ------------------------------------------------- systematic rounding
 // The exact-integer-total variant: pixel intervals of length s_i laid end to
 // end from a frame offset U, in 32.32 fixed point (q_i = s_i 2^32 rounded to
@@ -852,6 +1044,18 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     }
     Dither dt = dither;
     dt.W = W;
+    const bool stall = (p->flags & SPP_FLAG_TEST_STALL_TILE1) != 0;
+    if (num_tiles > kSinglePassMaxTiles && counts && !stall) {
+        auto *tile_sums = reinterpret_cast<int *>(tiles);
+        assign_tile_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
+            d, N, hdr, stream_key(p->seed, p->frame), dt, args.hard, counts, s_out, holdout_w,
+            tile_sums);
+        offsets_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
+            counts, N, tile_sums, num_tiles, offsets, sample_pixel, capacity,
+            reinterpret_cast<long long *>(total), status);
+        count_launch(3);
+        return launch_status();
+    }
     assign_scan_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
         d, N, hdr, hdr, tiles, stream_key(p->seed, p->frame), dt, args.hard,
         (p->flags & SPP_FLAG_TEST_STALL_TILE1) ? 1 : 0, counts, offsets,
