@@ -287,10 +287,22 @@ def run_ours(args, rank, world, local):
     warped = torch.empty((3, H, W), device=dev)
     state = {"prev": None, "parity": 0}
     ev_l0 = []
+    # W_t L_{t-1} needs only the previous output and the motion: it runs on a
+    # side stream, overlapping the sampling and the coarse levels, and level 0
+    # waits for it
+    side = torch.cuda.Stream(device=dev)
+    ev_prev = torch.cuda.Event()
+    ev_warp = torch.cuda.Event()
 
     def step(k, timed_l0=False, inp=None):
         t = k % F
         x = inp if inp is not None else frames[t]
+        prev = state["prev"]
+        if prev is not None:  # the first frame of the run has no previous output
+            ev_prev.record(stream)
+            side.wait_event(ev_prev)
+            Bnd.check(spp.spp_warp_previous(prev, x["mv"], W, H, warped, stream=side), "warp")
+            ev_warp.record(side)
         params = spp.make_params(B, frame=t + rank * 1000)
         fr.alloc(x["d"], params)
         fr.render(x["clean"], 0xC0FFEE + rank, t)
@@ -301,9 +313,8 @@ def run_ours(args, rank, world, local):
                 fr.layers[l], x["logits"][l], C, hats[l + 1] if l + 1 < L else None, None, None,
                 W >> l, H >> l, None, hats[l], None, status=fr.status), "level")
         out = fr.hdr[state["parity"]]
-        prev = state["prev"]
-        if prev is not None:  # the first frame of the run has no previous output
-            Bnd.check(spp.spp_warp_previous(prev, x["mv"], W, H, warped), "warp")
+        if prev is not None:
+            stream.wait_event(ev_warp)
         if timed_l0:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -701,38 +712,69 @@ def run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, worl
         pinned.append(dict(d=pin(x["d"]), clean=pin(x["clean"]),
                            logits=[pin(a) for a in x["logits"]], mv=pin(x["mv"]),
                            mask=pin(x["mask"])))
-    staging = dict(d=torch.empty_like(pinned[0]["d"], device=dev),
-                   clean=torch.empty_like(pinned[0]["clean"], device=dev),
-                   logits=[torch.empty_like(a, device=dev) for a in pinned[0]["logits"]],
-                   mv=torch.empty_like(pinned[0]["mv"], device=dev),
-                   mask=torch.empty_like(pinned[0]["mask"], device=dev))
+
+    def make_staging():
+        return dict(d=torch.empty_like(pinned[0]["d"], device=dev),
+                    clean=torch.empty_like(pinned[0]["clean"], device=dev),
+                    logits=[torch.empty_like(a, device=dev) for a in pinned[0]["logits"]],
+                    mv=torch.empty_like(pinned[0]["mv"], device=dev),
+                    mask=torch.empty_like(pinned[0]["mask"], device=dev))
+
+    # two staging sets: the copy stream fills one with frame k + 1's inputs
+    # while the frame stream computes frame k from the other (the host link,
+    # about 210 GB/s, is the bound); the result goes back on its own stream
+    staging = [make_staging(), make_staging()]
+    copy_stream = torch.cuda.Stream(device=dev)
+    d2h_stream = torch.cuda.Stream(device=dev)
+    ev_copied = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_used = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_done = torch.cuda.Event()
+    ev_read = torch.cuda.Event()
     out_host = torch.empty((3, H, W), dtype=torch.float32).pin_memory()
     h2d = sum(t.numel() * t.element_size() for t in
               [pinned[0]["d"], pinned[0]["clean"], pinned[0]["mv"], pinned[0]["mask"],
                *pinned[0]["logits"]])
     d2h = out_host.numel() * out_host.element_size()
 
-    def e2e_step(k):
-        x = pinned[k % F]
-        staging["d"].copy_(x["d"], non_blocking=True)
-        staging["clean"].copy_(x["clean"], non_blocking=True)
-        for a, b in zip(staging["logits"], x["logits"]):
-            a.copy_(b, non_blocking=True)
-        staging["mv"].copy_(x["mv"], non_blocking=True)
-        staging["mask"].copy_(x["mask"], non_blocking=True)
-        step(k, inp=staging)
-        out_host.copy_(fr.ldr, non_blocking=True)
+    def issue_copy(k):
+        x, buf = pinned[k % F], staging[k % 2]
+        copy_stream.wait_event(ev_used[k % 2])  # the frame that read this set is done
+        with torch.cuda.stream(copy_stream):
+            buf["d"].copy_(x["d"], non_blocking=True)
+            buf["clean"].copy_(x["clean"], non_blocking=True)
+            for a, b in zip(buf["logits"], x["logits"]):
+                a.copy_(b, non_blocking=True)
+            buf["mv"].copy_(x["mv"], non_blocking=True)
+            buf["mask"].copy_(x["mask"], non_blocking=True)
+        ev_copied[k % 2].record(copy_stream)
 
+    def e2e_step(k, last):
+        stream.wait_event(ev_copied[k % 2])
+        stream.wait_event(ev_read)  # the previous result has left fr.ldr
+        step(k, inp=staging[k % 2])
+        ev_used[k % 2].record(stream)
+        ev_done.record(stream)
+        d2h_stream.wait_event(ev_done)
+        with torch.cuda.stream(d2h_stream):
+            out_host.copy_(fr.ldr, non_blocking=True)
+        ev_read.record(d2h_stream)
+        if not last:
+            issue_copy(k + 1)
+
+    issue_copy(0)
     for k in range(2):
-        e2e_step(k)
+        e2e_step(k, last=k == 1)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
+    copy_stream.wait_event(t0)
+    issue_copy(2)
     for k in range(args.e2e_steps):
-        e2e_step(2 + k)
+        e2e_step(2 + k, last=k == args.e2e_steps - 1)
+    stream.wait_event(ev_read)  # the last result is on the host
     t1.record(stream)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
