@@ -45,10 +45,10 @@ UNIT = "Mpix/s"
 # which the hash checks.
 LEVEL0_TRAFFIC = {
     "workload": "1080p",
-    "bytes_per_launch": 549_248_000,
+    "bytes_per_launch": 549_250_560,
     "sources": ("paper_2602_08642_gb300/csrc/reconstruct_tma.cu",
                 "paper_2602_08642_gb300/csrc/recon_common.cuh"),
-    "sha256": "91b9d86b5afe9297f082cc6a4cd308114da63ee72eacab55ca6a5f6bcff88ff5",
+    "sha256": "9194da26579f858e8165c41766296461958ccd4c9d725c3f44b10a19f4cd3945",
 }
 
 
