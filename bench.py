@@ -94,6 +94,28 @@ def dist_env():
     return rank, world, local
 
 
+def slowest_rank_ms(ms_local: float, world: int, device="cpu") -> float:
+    """The job's timed region ends with its slowest rank: the maximum over
+    the ranks of the local milliseconds (every rank gets it)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms: float) -> float:
+    """Units (pixels) processed by all ranks together per second, in millions."""
+    return units_per_rank * world / (ms / 1e3) / 1e6
+
+
+def rank_frame(t: int, rank: int) -> int:
+    """Frame index of the seeded streams of rank `rank`'s frame t: every rank
+    samples and renders its own frames (weak scaling, no shared data)."""
+    return t + rank * 1000
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
@@ -303,7 +325,7 @@ def run_ours(args, rank, world, local):
             side.wait_event(ev_prev)
             Bnd.check(spp.spp_warp_previous(prev, x["mv"], W, H, warped, stream=side), "warp")
             ev_warp.record(side)
-        params = spp.make_params(B, frame=t + rank * 1000)
+        params = spp.make_params(B, frame=rank_frame(t, rank))
         fr.alloc(x["d"], params)
         fr.render(x["clean"], 0xC0FFEE + rank, t)
         fr.splat()
@@ -358,11 +380,8 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
     fr.check_status()
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = N * args.steps * world / (ms_max / 1e3) / 1e6
+    ms_max = slowest_rank_ms(ms, world, dev)
+    value = whole_job_rate(N * args.steps, world, ms_max)
 
     l0_ms = [a.elapsed_time(b) for a, b in ev_l0]
     l0_avg = sum(l0_ms) / len(l0_ms)
@@ -777,12 +796,8 @@ def run_e2e(args, spp, Bnd, fr, host_inputs, step, dev, stream, W, H, L, F, worl
     stream.wait_event(ev_read)  # the last result is on the host
     t1.record(stream)
     torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    return {"value": W * H * args.e2e_steps * world / (ms / 1e3) / 1e6, "unit": UNIT,
+    ms = slowest_rank_ms(t0.elapsed_time(t1), world, dev)
+    return {"value": whole_job_rate(W * H * args.e2e_steps, world, ms), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "ms_per_step": ms / args.e2e_steps, "steps": args.e2e_steps}
 

@@ -114,3 +114,63 @@ def test_binding_rejects_host_tensors():
     fr_args = [torch.zeros(4)] * 3
     with pytest.raises(ValueError):
         spp.binding._dev(fr_args[0])
+
+
+def test_host_argument_errors_two_stage_and_variants(lib):
+    """The two-stage, variant and estimator entry points validate on the
+    host before any CUDA call."""
+    import paper_2602_08642_gb300._binding as B
+    a = _fake(0x10000)
+    a256 = _fake(0x20000)
+    mis = _fake(0x10004)
+    n = None
+    arr = (ctypes.c_void_p * 5)(0x10000, 0x10000, 0x10000, 0x10000, 0x10000)
+    layers = ctypes.cast(arr, ctypes.c_void_p)
+    # networks: unknown net, absent-head pointers, shapes, alignment
+    nf = B.lib.spp_net_forward
+    assert nf(3, a256, a, 1, 32, 32, a, a, a, a256, 1 << 30, a, n) == B.SPP_ERR_ARG
+    assert nf(2, a256, a, 1, 32, 32, a, None, a, a256, 1 << 30, a, n) == B.SPP_ERR_ARG
+    assert nf(1, a256, a, 1, 30, 32, a, None, None, a256, 1 << 30, a, n) == B.SPP_ERR_SHAPE
+    a16 = _fake(0x10010)  # 16- but not 256-byte aligned
+    assert nf(1, a16, a, 1, 32, 32, a, None, None, a256, 1 << 30, a, n) == B.SPP_ERR_ALIGN
+    assert nf(1, a256, a, 1, 32, 32, a, None, None, a256, 16, a, n) == B.SPP_ERR_WORKSPACE
+    nb = B.lib.spp_net_backward
+    assert nb(2, a256, 1, 32, 32, a256, 1 << 30, a, None, a, a, None, a256, 1 << 30, a, n) == \
+        B.SPP_ERR_ARG
+    assert nb(1, a256, 1, 32, 32, a256, 1 << 30, a, None, None, a, mis, a256, 1 << 30, a, n) == \
+        B.SPP_ERR_ALIGN
+    ds = B.lib.spp_density_softmax
+    assert ds(a, 1, 32, 32, 100, a, a, 64, n) == B.SPP_ERR_ARG  # stride below W H
+    # two-stage per-pixel steps
+    assert B.lib.spp_warp_latent(None, a, 8, 8, a, n) == B.SPP_ERR_ARG
+    assert B.lib.spp_assemble_denoiser_features(a, a, a, a, a, a, a, None, None, 8, 8, mis, n) == \
+        B.SPP_ERR_ALIGN
+    assert B.lib.spp_denoiser_features_backward(a, a, a, 8, 8, None, None, n) == B.SPP_ERR_ARG
+    dm = B.lib.spp_demodulate
+    assert dm(a, a, None, 30, 32, 3, a, layers, None, n) == B.SPP_ERR_SHAPE
+    assert dm(a, a, None, 32, 32, 6, a, layers, None, n) == B.SPP_ERR_ARG
+    assert dm(a, a, a, 32, 32, 3, a, layers, None, n) == B.SPP_ERR_ARG  # warped needs an output
+    tm = B.make_tonemap(highlight=0.0)
+    assert B.lib.spp_remodulate_tonemap(a, a, 8, 8, ctypes.byref(tm), a, a, n) == B.SPP_ERR_ARG
+    assert B.lib.spp_demodulate_backward(a, a, a, a, a, None, a, a, 8, 8, a, a, n) == \
+        B.SPP_ERR_ARG  # Wd without its gradient
+    # variants
+    lr = B.lib.spp_density_lowres
+    assert lr(a, 32, 32, 3, a, n) == B.SPP_ERR_ARG
+    assert lr(a, 30, 32, 4, a, n) == B.SPP_ERR_SHAPE
+    assert lr(mis, 32, 32, 2, a, n) == B.SPP_ERR_ALIGN
+    sy = B.lib.spp_alloc_sample_map_systematic
+    g = B.make_params(0.25, gumbel=True)
+    assert sy(a, 4, 4, ctypes.byref(g), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
+    st = B.make_params(0.25)
+    st.flags |= B.SPP_FLAG_TEST_STALL_TILE1
+    assert sy(a, 4, 4, ctypes.byref(st), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
+    # estimators: unknown estimator; straight-through needs the clean image
+    p = B.make_params(0.25, hard=True)
+    eb = B.lib.spp_splat_backward_estimator
+    assert eb(a, a, a, a, a, a, a, 16, 8, 8, ctypes.byref(p), 7, a, 0, a, n) == B.SPP_ERR_ARG
+    assert eb(a, a, a, a, a, a, a, 16, 8, 8, ctypes.byref(p), 1, None, 0, a, n) == B.SPP_ERR_ARG
+    # Gumbel mode needs a positive inverse temperature
+    bad = B.make_params(0.25, gumbel=True, lam=0.0)
+    f = B.lib.spp_alloc_sample_map
+    assert f(a, 4, 4, ctypes.byref(bad), a, a, a, 16, a, a, a, a, a, 4096, n) == B.SPP_ERR_ARG
