@@ -605,6 +605,14 @@ int spp_density_softmax(const float *z, int B, int W, int H, int64_t batch_strid
 int spp_warp_latent(const float *raw, const float *mv, int W, int H, float *out,
                     cudaStream_t stream);
 
+/* The same in two steps, each source value's tanh taken once: out [7][H][W]
+ * = tanh(raw) (spp_latent_tanh), then W_t of C planes along mv
+ * (spp_warp_channels, the bilinear warp of spp_warp_previous on every
+ * plane); spp_warp_channels(spp_latent_tanh(raw)) = spp_warp_latent(raw). */
+int spp_latent_tanh(const float *raw, int W, int H, float *out, cudaStream_t stream);
+int spp_warp_channels(const float *src, int C, const float *mv, int W, int H, float *out,
+                      cudaStream_t stream);
+
 /* Sampler input in19 [19][H][W]: the 12 channels of spp_assemble_features,
  * then warped_latent [7][H][W] (NULL: zeros, the first frame). */
 int spp_assemble_sampler_features(const float *albedo, const float *normal, const float *depth,

@@ -142,6 +142,8 @@ _SIGS = {
     "spp_alloc_sample_map_systematic": (_I, [_P, _I, _I, ctypes.POINTER(spp_params), _P, _P, _P,
                                              _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "spp_density_lowres": (_I, [_P, _I, _I, _I, _P, _P]),
+    "spp_latent_tanh": (_I, [_P, _I, _I, _P, _P]),
+    "spp_warp_channels": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "spp_splat_backward_estimator": (_I, [_P, _P, _P, _P, _P, _P, _P, _I64, _I, _I,
                                           ctypes.POINTER(spp_params), _I, _P, _U64, _P, _P]),
 }
@@ -636,3 +638,14 @@ def spp_splat_backward_estimator(offsets, counts, rgb, s, layer0, grad_layer0, h
         _dev(layer0, f), _dev(grad_layer0, f), _dev(holdout_w, f), int(capacity), W, H,
         ctypes.byref(params), int(estimator), _dev(clean, f), render_seed & 0xFFFFFFFFFFFFFFFF,
         _dev(grad_s, f), _stream(stream))
+
+
+def spp_latent_tanh(raw, W, H, out, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_latent_tanh(_dev(raw, f), W, H, _dev(out, f), _stream(stream))
+
+
+def spp_warp_channels(src, C, mv, W, H, out, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_warp_channels(_dev(src, f), int(C), _dev(mv, f), W, H, _dev(out, f),
+                                 _stream(stream))

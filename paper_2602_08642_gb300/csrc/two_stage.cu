@@ -72,6 +72,31 @@ __global__ void warp_latent_kernel(const float *__restrict__ raw, const float *_
     }
 }
 
+// The latents passed on, tanh of the raw planes (each source value once).
+__global__ void latent_tanh_kernel(const float *__restrict__ raw, int64_t n,
+                                   float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        out[i] = tanhf(raw[i]);
+}
+
+// W_t of C planes (the previous-frame warp of Appendix A on every channel).
+__global__ void warp_channels_kernel(const float *__restrict__ src, int C,
+                                     const float *__restrict__ mv, int W, int H,
+                                     float *__restrict__ out) {
+    const int64_t N = static_cast<int64_t>(W) * H;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < N;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int x = static_cast<int>(i % W), y = static_cast<int>(i / W);
+        const Taps t = warp_taps(mv, N, W, H, x, y, i);
+        for (int c = 0; c < C; ++c) {
+            const float *p = src + c * N;
+            out[c * N + i] = (1.0f - t.fy) * ((1.0f - t.fx) * p[t.i00] + t.fx * p[t.i01]) +
+                             t.fy * ((1.0f - t.fx) * p[t.i10] + t.fx * p[t.i11]);
+        }
+    }
+}
+
 __global__ void sampler_features_kernel(const float *__restrict__ albedo,
                                         const float *__restrict__ normal,
                                         const float *__restrict__ depth,
@@ -239,6 +264,27 @@ extern "C" int spp_warp_latent(const float *raw, const float *mv, int W, int H, 
     const int64_t n = static_cast<int64_t>(W) * H;
     if (n == 0) return SPP_OK;
     spp::warp_latent_kernel<<<grid_for(n), 256, 0, stream>>>(raw, mv, W, H, out);
+    count_launch();
+    return launch_status();
+}
+
+extern "C" int spp_latent_tanh(const float *raw, int W, int H, float *out, cudaStream_t stream) {
+    if (!raw || !out || W < 0 || H < 0) return SPP_ERR_ARG;
+    if (!aligned16(raw) || !aligned16(out)) return SPP_ERR_ALIGN;
+    const int64_t n = static_cast<int64_t>(spp::kLatent) * W * H;
+    if (n == 0) return SPP_OK;
+    spp::latent_tanh_kernel<<<grid_for(n), 256, 0, stream>>>(raw, n, out);
+    count_launch();
+    return launch_status();
+}
+
+extern "C" int spp_warp_channels(const float *src, int C, const float *mv, int W, int H,
+                                 float *out, cudaStream_t stream) {
+    if (!src || !mv || !out || C <= 0 || W < 0 || H < 0) return SPP_ERR_ARG;
+    if (!aligned16(src) || !aligned16(mv) || !aligned16(out)) return SPP_ERR_ALIGN;
+    const int64_t n = static_cast<int64_t>(W) * H;
+    if (n == 0) return SPP_OK;
+    spp::warp_channels_kernel<<<grid_for(n), 256, 0, stream>>>(src, C, mv, W, H, out);
     count_launch();
     return launch_status();
 }

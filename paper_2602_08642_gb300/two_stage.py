@@ -92,7 +92,7 @@ class TwoStage:
         self.frames = [Frame(W, H, LEVELS, max_budget=budget) for _ in range(B_)]
         z3 = lambda: [_zeros(3, H, W) for _ in range(B_)]
         self.hdr_prev, self.warped, self.warped_ldr = z3(), z3(), z3()
-        self.latent_raw = [_zeros(NL, H, W) for _ in range(B_)]
+        self.latent = [_zeros(NL, H, W) for _ in range(B_)]  # tanh of the raw planes
         self.warped_latent = [_zeros(NL, H, W) for _ in range(B_)]
         self.m, self.wd, self.hdr, self.ldr = z3(), z3(), z3(), z3()
         self.dlayers = [[_zeros(3, H >> l, W >> l) for l in range(LEVELS)] for _ in range(B_)]
@@ -143,8 +143,8 @@ class TwoStage:
                 B.check(B.spp_warp_previous(self.hdr_prev[b], mvs[b], W, H, self.warped[b]), "warp")
                 B.check(B.spp_tonemap_image(self.warped[b], W, H, self.tm, self.warped_ldr[b]),
                         "tonemap")
-                B.check(B.spp_warp_latent(self.latent_raw[b], mvs[b], W, H, self.warped_latent[b]),
-                        "warp latent")
+                B.check(B.spp_warp_channels(self.latent[b], NL, mvs[b], W, H,
+                                            self.warped_latent[b]), "warp latent")
             g = gbufs[b]
             B.check(B.spp_assemble_sampler_features(
                 g["albedo"], g["normal"], g["depth"], mvs[b], self.warped_ldr[b] if tp else None,
@@ -180,7 +180,8 @@ class TwoStage:
                                              self.ldr[b]), "remodulate")
         for b in range(self.B):
             self.hdr_prev[b].copy_(self.hdr[b])
-            self.latent_raw[b].copy_(dn.heads[0][b, LP:LP + NL])
+            B.check(B.spp_latent_tanh(dn.heads[0][b, LP:LP + NL], W, H, self.latent[b]),
+                    "latents")
         self.has_prev = True
 
     def logits(self, b: int):

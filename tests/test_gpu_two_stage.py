@@ -227,6 +227,13 @@ def test_feature_assembly_and_latent_warp_parity(spp, W, H):
     bnd.check(bnd.spp_warp_latent(dev(raw), dev(mv), W, H, lat))
     ref_lat = TS.warp_channels(np.tanh(raw.astype(np.float64)), mv)
     assert np.allclose(host(lat), ref_lat, rtol=2e-6, atol=1e-6)
+    # the two-step form: tanh once per source value, then the warp of 7 planes
+    th = torch.empty(TS.N_LATENT, H, W, device="cuda")
+    bnd.check(bnd.spp_latent_tanh(dev(raw), W, H, th))
+    assert np.allclose(host(th), np.tanh(raw.astype(np.float64)), rtol=4e-7, atol=1e-7)
+    lat2 = torch.empty(TS.N_LATENT, H, W, device="cuda")
+    bnd.check(bnd.spp_warp_channels(th, TS.N_LATENT, dev(mv), W, H, lat2))
+    assert np.allclose(host(lat2), ref_lat, rtol=2e-6, atol=1e-6)
     lat_np = host(lat)
     x19 = torch.empty(19, H, W, device="cuda")
     bnd.check(bnd.spp_assemble_sampler_features(g["albedo"], g["normal"], g["depth"], dev(mv),
