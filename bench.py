@@ -710,8 +710,8 @@ def run_two_stage(args, spp, Bnd, dev, rank, frames, refs, W, H, F, peaks, peak_
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        p.sampler.forward()
-        p.denoiser.forward()
+        p.sampler.forward_prepared()
+        p.denoiser.forward_prepared()
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps

@@ -581,6 +581,16 @@ size_t spp_net_workspace_bytes(int net, int B, int W, int H);
 int spp_net_forward(int net, const void *packed, const float *in, int B, int W, int H,
                     float *head0, float *head1, float *head2, void *ws, size_t ws_bytes,
                     int32_t *status, cudaStream_t stream);
+/* Where the forward keeps its BF16 NHWC copy of the input inside ws: byte
+ * offset and channels (the input padded to 16 or 32; image b starts at
+ * offset + b H W channels 2 bytes).  spp_assemble_sampler_input /
+ * spp_assemble_denoiser_input write it there directly, and
+ * spp_net_forward_prepared then runs the network without the FP32 input
+ * (the same results as spp_net_forward on the FP32 features). */
+int spp_net_input_layout(int net, int B, int W, int H, size_t *offset, int *channels);
+int spp_net_forward_prepared(int net, const void *packed, int B, int W, int H, float *head0,
+                             float *head1, float *head2, void *ws, size_t ws_bytes,
+                             int32_t *status, cudaStream_t stream);
 size_t spp_net_backward_workspace_bytes(int net, int B, int W, int H);
 /* Backward of spp_net_forward: grad_theta (OVERWRITTEN) from the head
  * gradients (same shapes as the heads); if grad_in is not NULL also the
@@ -630,6 +640,20 @@ int spp_assemble_denoiser_features(const float *L0, const float *s, const int32_
                                    const float *mv, const float *warped_prev_hdr,
                                    const float *warped_latent, int W, int H, float *in24,
                                    cudaStream_t stream);
+
+/* The same inputs written straight as the networks' BF16 NHWC input copy of
+ * one image, [H][W][32] (x_nhwc32: inside the forward workspace, see
+ * spp_net_input_layout; values rounded to nearest even from the FP32 values
+ * above, channels 19 / 24 .. 31 zero). */
+int spp_assemble_sampler_input(const float *albedo, const float *normal, const float *depth,
+                               const float *mv, const float *warped_prev_ldr,
+                               const float *warped_latent, int W, int H, uint16_t *x_nhwc32,
+                               cudaStream_t stream);
+int spp_assemble_denoiser_input(const float *L0, const float *s, const int32_t *counts,
+                                const float *albedo, const float *normal, const float *depth,
+                                const float *mv, const float *warped_prev_hdr,
+                                const float *warped_latent, int W, int H, uint16_t *x_nhwc32,
+                                cudaStream_t stream);
 
 /* Adds the gradient reaching L0 and s through the denoiser input:
  * grad_L0 += grad_in24[0..2] / (1 + L0), grad_s += grad_in24[3] / (1 + s);

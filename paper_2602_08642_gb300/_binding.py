@@ -143,6 +143,10 @@ _SIGS = {
                                              _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "spp_density_lowres": (_I, [_P, _I, _I, _I, _P, _P]),
     "spp_latent_tanh": (_I, [_P, _I, _I, _P, _P]),
+    "spp_net_input_layout": (_I, [_I, _I, _I, _I, ctypes.POINTER(_SZ), ctypes.POINTER(_I)]),
+    "spp_net_forward_prepared": (_I, [_I, _P, _I, _I, _I, _P, _P, _P, _P, _SZ, _P, _P]),
+    "spp_assemble_sampler_input": (_I, [_P, _P, _P, _P, _P, _P, _I, _I, _P, _P]),
+    "spp_assemble_denoiser_input": (_I, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P, _P]),
     "spp_warp_channels": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "spp_splat_backward_estimator": (_I, [_P, _P, _P, _P, _P, _P, _P, _I64, _I, _I,
                                           ctypes.POINTER(spp_params), _I, _P, _U64, _P, _P]),
@@ -649,3 +653,37 @@ def spp_warp_channels(src, C, mv, W, H, out, stream=None) -> int:
     f = torch.float32
     return lib.spp_warp_channels(_dev(src, f), int(C), _dev(mv, f), W, H, _dev(out, f),
                                  _stream(stream))
+
+
+def spp_net_input_layout(net: int, B_: int, W: int, H: int):
+    """(byte offset, channels) of the BF16 NHWC input copy in the forward workspace."""
+    off, ch = _SZ(), _I()
+    check(lib.spp_net_input_layout(net, B_, W, H, ctypes.byref(off), ctypes.byref(ch)),
+          "spp_net_input_layout")
+    return off.value, ch.value
+
+
+def spp_net_forward_prepared(net, packed, B_, W, H, head0, head1, head2, ws, status,
+                             stream=None) -> int:
+    f = torch.float32
+    return lib.spp_net_forward_prepared(net, _dev(packed), B_, W, H, _dev(head0, f),
+                                        _dev(head1, f), _dev(head2, f), _dev(ws), _nbytes(ws),
+                                        _dev(status, torch.int32), _stream(stream))
+
+
+def spp_assemble_sampler_input(albedo, normal, depth, mv, warped_prev_ldr, warped_latent, W, H,
+                               x_nhwc32, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_assemble_sampler_input(_dev(albedo, f), _dev(normal, f), _dev(depth, f),
+                                          _dev(mv, f), _dev(warped_prev_ldr, f),
+                                          _dev(warped_latent, f), W, H,
+                                          _dev(x_nhwc32, torch.bfloat16), _stream(stream))
+
+
+def spp_assemble_denoiser_input(L0, s, counts, albedo, normal, depth, mv, warped_prev_hdr,
+                                warped_latent, W, H, x_nhwc32, stream=None) -> int:
+    f = torch.float32
+    return lib.spp_assemble_denoiser_input(
+        _dev(L0, f), _dev(s, f), _dev(counts, torch.int32), _dev(albedo, f), _dev(normal, f),
+        _dev(depth, f), _dev(mv, f), _dev(warped_prev_hdr, f), _dev(warped_latent, f), W, H,
+        _dev(x_nhwc32, torch.bfloat16), _stream(stream))

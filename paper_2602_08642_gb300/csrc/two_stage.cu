@@ -5,6 +5,8 @@
 // and the backward of these steps.  All of them are streaming kernels over
 // planar FP32 images (one thread per pixel, grid-stride loops), bound by
 // HBM; the networks themselves run in unet.cu / conv_tc.cu.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "recon_common.cuh"
@@ -97,54 +99,91 @@ __global__ void warp_channels_kernel(const float *__restrict__ src, int C,
     }
 }
 
-__global__ void sampler_features_kernel(const float *__restrict__ albedo,
-                                        const float *__restrict__ normal,
-                                        const float *__restrict__ depth,
-                                        const float *__restrict__ mv,
-                                        const float *__restrict__ prev,
-                                        const float *__restrict__ latent, int64_t n,
-                                        float *__restrict__ out) {
-    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+// The sampler's 19 input values of pixel i (FP32).
+__device__ __forceinline__ void sampler_values(const float *__restrict__ albedo,
+                                               const float *__restrict__ normal,
+                                               const float *__restrict__ depth,
+                                               const float *__restrict__ mv,
+                                               const float *__restrict__ prev,
+                                               const float *__restrict__ latent, int64_t n,
+                                               int64_t i, float (&v)[32]) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            out[c * n + i] = albedo[c * n + i];
-            out[(3 + c) * n + i] = normal[c * n + i];
-            out[(9 + c) * n + i] = prev ? prev[c * n + i] : 0.f;
-        }
-        out[6 * n + i] = logf(depth[i]) * kInvLn100;
-        out[7 * n + i] = mv[i] * 0.125f;
-        out[8 * n + i] = mv[n + i] * 0.125f;
-#pragma unroll
-        for (int c = 0; c < kLatent; ++c) out[(12 + c) * n + i] = latent ? latent[c * n + i] : 0.f;
+    for (int c = 0; c < 3; ++c) {
+        v[c] = albedo[c * n + i];
+        v[3 + c] = normal[c * n + i];
+        v[9 + c] = prev ? prev[c * n + i] : 0.f;
     }
+    v[6] = logf(depth[i]) * kInvLn100;
+    v[7] = mv[i] * 0.125f;
+    v[8] = mv[n + i] * 0.125f;
+#pragma unroll
+    for (int c = 0; c < kLatent; ++c) v[12 + c] = latent ? latent[c * n + i] : 0.f;
+#pragma unroll
+    for (int c = 12 + kLatent; c < 32; ++c) v[c] = 0.f;
 }
 
-__global__ void denoiser_features_kernel(const float *__restrict__ L0, const float *__restrict__ s,
-                                         const int32_t *__restrict__ counts,
-                                         const float *__restrict__ albedo,
-                                         const float *__restrict__ normal,
-                                         const float *__restrict__ depth,
-                                         const float *__restrict__ mv,
-                                         const float *__restrict__ prev,
-                                         const float *__restrict__ latent, int64_t n,
-                                         float *__restrict__ out) {
+// The denoiser's 24 input values of pixel i (FP32).
+__device__ __forceinline__ void denoiser_values(const float *__restrict__ L0,
+                                                const float *__restrict__ s,
+                                                const int32_t *__restrict__ counts,
+                                                const float *__restrict__ albedo,
+                                                const float *__restrict__ normal,
+                                                const float *__restrict__ depth,
+                                                const float *__restrict__ mv,
+                                                const float *__restrict__ prev,
+                                                const float *__restrict__ latent, int64_t n,
+                                                int64_t i, float (&v)[32]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = log1pf(L0[c * n + i]);
+        v[5 + c] = albedo[c * n + i];
+        v[8 + c] = normal[c * n + i];
+        v[14 + c] = prev ? log1pf(prev[c * n + i]) : 0.f;
+    }
+    v[3] = log1pf(s[i]);
+    v[4] = log1pf(static_cast<float>(counts[i]));
+    v[11] = logf(depth[i]) * kInvLn100;
+    v[12] = mv[i] * 0.125f;
+    v[13] = mv[n + i] * 0.125f;
+#pragma unroll
+    for (int c = 0; c < kLatent; ++c) v[17 + c] = latent ? latent[c * n + i] : 0.f;
+#pragma unroll
+    for (int c = 17 + kLatent; c < 32; ++c) v[c] = 0.f;
+}
+
+// FP32 planar [C][H][W] (C = 19 or 24) or the network's BF16 NHWC input
+// copy [H][W][32] (rounded to nearest even, padding channels zero).
+template <bool DENOISER, bool NHWC>
+__global__ void features_kernel(const float *__restrict__ L0, const float *__restrict__ s,
+                                const int32_t *__restrict__ counts,
+                                const float *__restrict__ albedo, const float *__restrict__ normal,
+                                const float *__restrict__ depth, const float *__restrict__ mv,
+                                const float *__restrict__ prev, const float *__restrict__ latent,
+                                int64_t n, float *__restrict__ out,
+                                __nv_bfloat16 *__restrict__ out16) {
+    constexpr int C = DENOISER ? 17 + kLatent : 12 + kLatent;
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float v[32];
+        if (DENOISER)
+            denoiser_values(L0, s, counts, albedo, normal, depth, mv, prev, latent, n, i, v);
+        else
+            sampler_values(albedo, normal, depth, mv, prev, latent, n, i, v);
+        if (NHWC) {
+            uint32_t w[16];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            out[c * n + i] = log1pf(L0[c * n + i]);
-            out[(5 + c) * n + i] = albedo[c * n + i];
-            out[(8 + c) * n + i] = normal[c * n + i];
-            out[(14 + c) * n + i] = prev ? log1pf(prev[c * n + i]) : 0.f;
+            for (int k = 0; k < 16; ++k) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                w[k] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out16 + i * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) out[c * n + i] = v[c];
         }
-        out[3 * n + i] = log1pf(s[i]);
-        out[4 * n + i] = log1pf(static_cast<float>(counts[i]));
-        out[11 * n + i] = logf(depth[i]) * kInvLn100;
-        out[12 * n + i] = mv[i] * 0.125f;
-        out[13 * n + i] = mv[n + i] * 0.125f;
-#pragma unroll
-        for (int c = 0; c < kLatent; ++c) out[(17 + c) * n + i] = latent ? latent[c * n + i] : 0.f;
     }
 }
 
@@ -301,8 +340,9 @@ extern "C" int spp_assemble_sampler_features(const float *albedo, const float *n
         return SPP_ERR_ALIGN;
     const int64_t n = static_cast<int64_t>(W) * H;
     if (n == 0) return SPP_OK;
-    spp::sampler_features_kernel<<<grid_for(n), 256, 0, stream>>>(
-        albedo, normal, depth, mv, warped_prev_ldr, warped_latent, n, in19);
+    spp::features_kernel<false, false><<<grid_for(n), 256, 0, stream>>>(
+        nullptr, nullptr, nullptr, albedo, normal, depth, mv, warped_prev_ldr, warped_latent, n,
+        in19, nullptr);
     count_launch();
     return launch_status();
 }
@@ -322,8 +362,51 @@ extern "C" int spp_assemble_denoiser_features(const float *L0, const float *s,
         return SPP_ERR_ALIGN;
     const int64_t n = static_cast<int64_t>(W) * H;
     if (n == 0) return SPP_OK;
-    spp::denoiser_features_kernel<<<grid_for(n), 256, 0, stream>>>(
-        L0, s, counts, albedo, normal, depth, mv, warped_prev_hdr, warped_latent, n, in24);
+    spp::features_kernel<true, false><<<grid_for(n), 256, 0, stream>>>(
+        L0, s, counts, albedo, normal, depth, mv, warped_prev_hdr, warped_latent, n, in24,
+        nullptr);
+    count_launch();
+    return launch_status();
+}
+
+extern "C" int spp_assemble_sampler_input(const float *albedo, const float *normal,
+                                          const float *depth, const float *mv,
+                                          const float *warped_prev_ldr,
+                                          const float *warped_latent, int W, int H,
+                                          uint16_t *x_nhwc32, cudaStream_t stream) {
+    if (W < 0 || H < 0 || !albedo || !normal || !depth || !mv || !x_nhwc32) return SPP_ERR_ARG;
+    if (!aligned16(albedo) || !aligned16(normal) || !aligned16(depth) || !aligned16(mv) ||
+        !aligned16(x_nhwc32) || (warped_prev_ldr && !aligned16(warped_prev_ldr)) ||
+        (warped_latent && !aligned16(warped_latent)))
+        return SPP_ERR_ALIGN;
+    const int64_t n = static_cast<int64_t>(W) * H;
+    if (n == 0) return SPP_OK;
+    spp::features_kernel<false, true><<<grid_for(n), 256, 0, stream>>>(
+        nullptr, nullptr, nullptr, albedo, normal, depth, mv, warped_prev_ldr, warped_latent, n,
+        nullptr, reinterpret_cast<__nv_bfloat16 *>(x_nhwc32));
+    count_launch();
+    return launch_status();
+}
+
+extern "C" int spp_assemble_denoiser_input(const float *L0, const float *s, const int32_t *counts,
+                                           const float *albedo, const float *normal,
+                                           const float *depth, const float *mv,
+                                           const float *warped_prev_hdr,
+                                           const float *warped_latent, int W, int H,
+                                           uint16_t *x_nhwc32, cudaStream_t stream) {
+    if (W < 0 || H < 0 || !L0 || !s || !counts || !albedo || !normal || !depth || !mv ||
+        !x_nhwc32)
+        return SPP_ERR_ARG;
+    if (!aligned16(L0) || !aligned16(s) || !aligned16(counts) || !aligned16(albedo) ||
+        !aligned16(normal) || !aligned16(depth) || !aligned16(mv) || !aligned16(x_nhwc32) ||
+        (warped_prev_hdr && !aligned16(warped_prev_hdr)) ||
+        (warped_latent && !aligned16(warped_latent)))
+        return SPP_ERR_ALIGN;
+    const int64_t n = static_cast<int64_t>(W) * H;
+    if (n == 0) return SPP_OK;
+    spp::features_kernel<true, true><<<grid_for(n), 256, 0, stream>>>(
+        L0, s, counts, albedo, normal, depth, mv, warped_prev_hdr, warped_latent, n, nullptr,
+        reinterpret_cast<__nv_bfloat16 *>(x_nhwc32));
     count_launch();
     return launch_status();
 }

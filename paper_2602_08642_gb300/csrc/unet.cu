@@ -290,7 +290,7 @@ int forward(int net, const unsigned char *packed, const float *in, int B, int W,
     heads[H0] = head0;
     heads[H1] = head1;
     heads[H2] = head2;
-    {
+    if (in) {  // else the BF16 NHWC input copy is already in the workspace
         const int64_t n = static_cast<int64_t>(B) * W * H;
         const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 8 * sm_count()));
         auto *x = reinterpret_cast<__nv_bfloat16 *>(ws + A.xin);
@@ -435,6 +435,33 @@ extern "C" int spp_net_forward(int net, const void *packed, const float *in, int
     return spp::unet::forward(net, static_cast<const unsigned char *>(packed), in, B, W, H, nullptr,
                               head0, head1, head2, static_cast<unsigned char *>(ws), status,
                               stream);
+}
+
+extern "C" int spp_net_input_layout(int net, int B, int W, int H, size_t *offset,
+                                    int *channels) {
+    if (!valid_net(net) || B < 0 || W < 0 || H < 0 || !offset || !channels) return SPP_ERR_ARG;
+    const spp::unet::ActLayout A = spp::unet::act_layout(net, B, W, H);
+    *offset = A.xin;
+    *channels = A.xin_c;
+    return SPP_OK;
+}
+
+extern "C" int spp_net_forward_prepared(int net, const void *packed, int B, int W, int H,
+                                        float *head0, float *head1, float *head2, void *ws,
+                                        size_t ws_bytes, int32_t *status, cudaStream_t stream) {
+    if (!valid_net(net) || B < 0 || W < 0 || H < 0 || !packed || !head0 || !ws)
+        return SPP_ERR_ARG;
+    const spp::unet::NetSpec &n = spp::unet::kNets[net];
+    if ((n.heads[1] && !head1) || (n.heads[2] && !head2)) return SPP_ERR_ARG;
+    if (W % 4 || H % 4) return SPP_ERR_SHAPE;
+    if (!aligned256(packed) || !aligned256(ws) || !aligned16(head0) ||
+        (n.heads[1] && !aligned16(head1)) || (n.heads[2] && !aligned16(head2)))
+        return SPP_ERR_ALIGN;
+    if (ws_bytes < spp::unet::act_layout(net, B, W, H).total) return SPP_ERR_WORKSPACE;
+    if (static_cast<int64_t>(B) * W * H == 0) return SPP_OK;
+    return spp::unet::forward(net, static_cast<const unsigned char *>(packed), nullptr, B, W, H,
+                              nullptr, head0, head1, head2, static_cast<unsigned char *>(ws),
+                              status, stream);
 }
 
 extern "C" size_t spp_density_softmax_workspace_bytes(int B) {

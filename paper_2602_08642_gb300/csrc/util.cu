@@ -58,7 +58,7 @@ const char *spp_strerror(int code) {
     }
 }
 
-int spp_abi_version(void) { return 6; }
+int spp_abi_version(void) { return 7; }
 
 uint64_t spp_launch_count(void) { return spp::g_launches.load(std::memory_order_relaxed); }
 

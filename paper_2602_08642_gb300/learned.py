@@ -125,6 +125,25 @@ class Predictor:
             B.check(B.spp_density_softmax(self.heads[0], self.B, self.W, self.H, hw, self.density,
                                           self.dws), "spp_density_softmax")
 
+    def input_nhwc(self, b: int) -> torch.Tensor:
+        """The forward's BF16 NHWC input copy of image b inside the workspace,
+        [H][W][channels]; written by the direct assembly entries, consumed
+        by forward_prepared."""
+        off, ch = B.spp_net_input_layout(self.net, self.B, self.W, self.H)
+        n = self.H * self.W * ch
+        return self.fws[off + 2 * n * b: off + 2 * n * (b + 1)].view(torch.bfloat16).view(
+            self.H, self.W, ch)
+
+    def forward_prepared(self):
+        """Forward on the BF16 input already in the workspace (input_nhwc)."""
+        B.check(B.spp_net_forward_prepared(self.net, self.packed, self.B, self.W, self.H,
+                                           *self.heads, self.fws, self.status),
+                "spp_net_forward_prepared")
+        if self.net == B.SPP_NET_SAMPLER:
+            hw = self.W * self.H
+            B.check(B.spp_density_softmax(self.heads[0], self.B, self.W, self.H, hw, self.density,
+                                          self.dws), "spp_density_softmax")
+
     def backward(self):
         B.check(B.spp_net_backward(self.net, self.packed, self.B, self.W, self.H, self.fws,
                                    *self.g_heads, self.grad, self.g_x, self.bws, self.status),

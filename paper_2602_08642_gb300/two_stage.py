@@ -87,6 +87,9 @@ class TwoStage:
         self.sampler = Predictor(theta_s, B_, W, H, train, net=B.SPP_NET_SAMPLER)
         self.denoiser = Predictor(theta_d, B_, W, H, train, net=B.SPP_NET_DENOISER,
                                   input_grad=train)
+        # the assembly kernels write each network's BF16 NHWC input in place
+        self.sp_in = [self.sampler.input_nhwc(b) for b in range(B_)]
+        self.dn_in = [self.denoiser.input_nhwc(b) for b in range(B_)]
         self.dither = dither_mask
         self.tm = B.make_tonemap()
         self.frames = [Frame(W, H, LEVELS, max_budget=budget) for _ in range(B_)]
@@ -146,10 +149,10 @@ class TwoStage:
                 B.check(B.spp_warp_channels(self.latent[b], NL, mvs[b], W, H,
                                             self.warped_latent[b]), "warp latent")
             g = gbufs[b]
-            B.check(B.spp_assemble_sampler_features(
+            B.check(B.spp_assemble_sampler_input(
                 g["albedo"], g["normal"], g["depth"], mvs[b], self.warped_ldr[b] if tp else None,
-                self.warped_latent[b] if tp else None, W, H, sp.x[b]), "sampler features")
-        sp.forward()
+                self.warped_latent[b] if tp else None, W, H, self.sp_in[b]), "sampler input")
+        sp.forward_prepared()
         for b in range(self.B):
             fr = self.frames[b]
             self.params[b] = B.make_params(self.budget, uniform_fraction=PHI, seed=seed + b,
@@ -158,11 +161,11 @@ class TwoStage:
             fr.render(cleans[b], (seed + b) ^ 0xC0FFEE, frame_index)
             fr.splat()
             g = gbufs[b]
-            B.check(B.spp_assemble_denoiser_features(
+            B.check(B.spp_assemble_denoiser_input(
                 fr.layers[0], fr.s, fr.counts, g["albedo"], g["normal"], g["depth"], mvs[b],
                 self.warped[b] if tp else None, self.warped_latent[b] if tp else None, W, H,
-                dn.x[b]), "denoiser features")
-        dn.forward()
+                self.dn_in[b]), "denoiser input")
+        dn.forward_prepared()
         for b in range(self.B):
             fr = self.frames[b]
             h0 = dn.heads[0][b]

@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings_and_version():
     import paper_2602_08642_gb300 as spp
-    assert spp.spp_abi_version() == 6
+    assert spp.spp_abi_version() == 7
     for code in range(0, -9, -1):
         assert spp.spp_strerror(code) and spp.spp_strerror(code) != "unknown status code"
     assert spp.spp_strerror(-99) == "unknown status code"
@@ -139,6 +139,22 @@ def test_host_argument_errors_two_stage_and_variants(lib):
         B.SPP_ERR_ARG
     assert nb(1, a256, 1, 32, 32, a256, 1 << 30, a, None, None, a, mis, a256, 1 << 30, a, n) == \
         B.SPP_ERR_ALIGN
+    fp = B.lib.spp_net_forward_prepared
+    assert fp(3, a256, 1, 32, 32, a, None, None, a256, 1 << 30, a, n) == B.SPP_ERR_ARG
+    assert fp(1, a256, 1, 30, 32, a, None, None, a256, 1 << 30, a, n) == B.SPP_ERR_SHAPE
+    assert fp(1, a16, 1, 32, 32, a, None, None, a256, 1 << 30, a, n) == B.SPP_ERR_ALIGN
+    assert fp(1, a256, 1, 32, 32, a, None, None, a256, 16, a, n) == B.SPP_ERR_WORKSPACE
+    off, ch = ctypes.c_size_t(), ctypes.c_int()
+    assert B.lib.spp_net_input_layout(1, 2, 32, 16, ctypes.byref(off), ctypes.byref(ch)) == 0
+    assert ch.value == 32 and off.value % 256 == 0
+    assert B.lib.spp_net_input_layout(0, 2, 32, 16, ctypes.byref(off), ctypes.byref(ch)) == 0
+    assert ch.value == 16
+    assert B.lib.spp_net_input_layout(5, 2, 32, 16, ctypes.byref(off), ctypes.byref(ch)) == \
+        B.SPP_ERR_ARG
+    assert B.lib.spp_assemble_sampler_input(a, a, a, a, None, None, 8, 8, mis, n) == \
+        B.SPP_ERR_ALIGN
+    assert B.lib.spp_assemble_denoiser_input(None, a, a, a, a, a, a, None, None, 8, 8, a, n) == \
+        B.SPP_ERR_ARG
     ds = B.lib.spp_density_softmax
     assert ds(a, 1, 32, 32, 100, a, a, 64, n) == B.SPP_ERR_ARG  # stride below W H
     # two-stage per-pixel steps

@@ -264,6 +264,64 @@ def test_feature_assembly_and_latent_warp_parity(spp, W, H):
     assert np.allclose(host(gs).reshape(H, W), rs, rtol=2e-6, atol=1e-7)
 
 
+@pytest.mark.parametrize("spec", ["sampler", "denoiser"])
+@pytest.mark.parametrize("temporal", [True, False])
+@pytest.mark.parametrize("W,H", [(40, 24), (132, 20)])
+def test_direct_bf16_input_matches_the_fp32_path(spp, spec, temporal, W, H):
+    """The assembly entries that write the networks' BF16 NHWC input in
+    place give bit for bit the copy the forward makes from the FP32
+    features (one round-to-nearest-even of the same FP32 values), and the
+    prepared forward the same heads."""
+    from paper_2602_08642_gb300 import learned as Lm
+    bnd = spp.binding
+    net = bnd.SPP_NET_SAMPLER if spec == "sampler" else bnd.SPP_NET_DENOISER
+    Bn = 2
+    rng = np.random.default_rng(W + temporal)
+    p = Lm.Predictor(torch.from_numpy(_theta(spec)), Bn, W, H, net=net)
+    args = []
+    for b in range(Bn):
+        clean, gb, mv = _gbuf(W, H, 11 + b)
+        g = {k: dev(v) for k, v in gb.items()}
+        prev = dev(rng.random((3, H, W)) * 2) if temporal else None
+        lat = dev(rng.uniform(-1, 1, (TS.N_LATENT, H, W))) if temporal else None
+        if spec == "sampler":
+            a = (g["albedo"], g["normal"], g["depth"], dev(mv), prev, lat, W, H)
+            bnd.check(bnd.spp_assemble_sampler_features(*a, p.x[b]))
+        else:
+            L0 = dev(clean * rng.random((3, H, W)))
+            s = dev(rng.uniform(0.03, 3.0, (H, W)))
+            n = dev(rng.integers(0, 4, (H, W)), torch.int32)
+            a = (L0, s, n, g["albedo"], g["normal"], g["depth"], dev(mv), prev, lat, W, H)
+            bnd.check(bnd.spp_assemble_denoiser_features(*a, p.x[b]))
+        args.append(a)
+    p.forward()
+    heads = [None if h is None else h.clone() for h in p.heads]
+    off, ch = bnd.spp_net_input_layout(net, Bn, W, H)
+    assert ch == 32 and off % 256 == 0
+    want = [p.input_nhwc(b).clone() for b in range(Bn)]
+    for b in range(Bn):
+        ref = torch.zeros(H, W, 32, dtype=torch.bfloat16, device="cuda")
+        ref[..., :p.cin] = p.x[b].permute(1, 2, 0).to(torch.bfloat16)
+        assert torch.equal(want[b].view(torch.int16), ref.view(torch.int16))
+        p.input_nhwc(b).fill_(float("nan"))
+        fn = bnd.spp_assemble_sampler_input if spec == "sampler" else \
+            bnd.spp_assemble_denoiser_input
+        bnd.check(fn(*args[b], p.input_nhwc(b)))
+        assert torch.equal(p.input_nhwc(b).view(torch.int16), want[b].view(torch.int16))
+    for h in p.heads:
+        if h is not None:
+            h.zero_()
+    p.forward_prepared()
+    torch.cuda.synchronize()
+    for h, r in zip(p.heads, heads):
+        if h is not None:
+            assert torch.equal(h, r)
+    if spec == "sampler":
+        d = p.density.clone()
+        p.forward()
+        assert torch.equal(p.density, d)
+
+
 def _demod_inputs(W, H, L, seed, temporal=True):
     rng = np.random.default_rng(seed)
     L0 = (rng.random((3, H, W)) * 3).astype(np.float32)
