@@ -92,6 +92,16 @@ int spp_abi_version(void);
  * counter, incremented at every launch). */
 uint64_t spp_launch_count(void);
 
+/* Programmatic dependent launch of the plain path's kernels (sample map,
+ * renderer stand-in, splat, pipelined reconstruction): when on (the
+ * default), each may be scheduled while the kernel before it in the stream
+ * is still running and waits on the device for that kernel's completion
+ * before it touches memory, so launch latency and block start-up overlap the
+ * previous kernel's tail.  Results are identical either way.  Process-wide;
+ * spp_set_dependent_launch returns the previous setting. */
+int spp_set_dependent_launch(int on);
+int spp_get_dependent_launch(void);
+
 /* Copies the device status word to the host (synchronises the stream) and
  * returns it (SPP_OK or an SPP_ERR_* code); SPP_ERR_CUDA if the copy fails. */
 int spp_get_status(const int32_t *status, cudaStream_t stream);

@@ -67,6 +67,8 @@ _SIGS = {
     "spp_strerror": (ctypes.c_char_p, [_I]),
     "spp_abi_version": (_I, []),
     "spp_launch_count": (_U64, []),
+    "spp_set_dependent_launch": (_I, [_I]),
+    "spp_get_dependent_launch": (_I, []),
     "spp_get_status": (_I, [_P, _P]),
     "spp_clear_status": (_I, [_P, _P]),
     "spp_alloc_workspace_bytes": (_SZ, [_I, _I]),
@@ -203,6 +205,15 @@ def spp_abi_version() -> int:
 
 def spp_launch_count() -> int:
     return int(lib.spp_launch_count())
+
+
+def spp_set_dependent_launch(on: bool) -> bool:
+    """Turns programmatic dependent launch on or off; returns the previous setting."""
+    return bool(lib.spp_set_dependent_launch(1 if on else 0))
+
+
+def spp_get_dependent_launch() -> bool:
+    return bool(lib.spp_get_dependent_launch())
 
 
 def spp_get_status(status: torch.Tensor, stream=None) -> int:

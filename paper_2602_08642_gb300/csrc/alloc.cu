@@ -211,6 +211,8 @@ template <int U>
 __global__ void __launch_bounds__(kSumThreads)
 budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, BudgetArgs args,
                   int32_t *status) {
+    pdl_wait();
+    pdl_trigger();
     unsigned long long lim[kLimbs];
 #pragma unroll
     for (int j = 0; j < kLimbs; ++j) lim[j] = 0ull;
@@ -452,6 +454,8 @@ assign_scan_kernel(const float *__restrict__ d, long long N, const AllocHeader *
     __shared__ int s_warp_excl[kScanThreads / 32];
     __shared__ int s_warp_tot[kScanThreads / 32];
     __shared__ int s_prefix;
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0) s_tile = static_cast<int>(atomicAdd(&hdr->tile_counter, 1u));
     __syncthreads();
     const int tile = s_tile;
@@ -651,6 +655,8 @@ assign_tile_kernel(const float *__restrict__ d, long long N, const AllocHeader *
                    uint64_t key, Dither dither, int hard, int32_t *__restrict__ counts,
                    float *__restrict__ s_out, float *__restrict__ w_out,
                    int *__restrict__ tile_sums) {
+    pdl_wait();
+    pdl_trigger();
     const int tile = blockIdx.x;
     const long long base = static_cast<long long>(tile) * kTile +
                            static_cast<long long>(threadIdx.x) * kScanItems;
@@ -745,6 +751,8 @@ __global__ void __launch_bounds__(kScanThreads)
 offsets_kernel(const int32_t *__restrict__ counts, long long N, const int *__restrict__ tile_sums,
                int num_tiles, int32_t *__restrict__ offsets, int32_t *__restrict__ sample_pixel,
                long long capacity, long long *total, int32_t *status) {
+    pdl_wait();
+    pdl_trigger();
     const int tile = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ int s_w[kScanThreads / 32];
@@ -1026,8 +1034,8 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     const long long max_grid = static_cast<long long>(sm_count()) * 8;
     if (grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
-    budget_sum_kernel<kSumU><<<static_cast<unsigned>(grid), kSumThreads, 0, stream>>>(
-        d, N, hdr, args, status);
+    launch_dependent(budget_sum_kernel<kSumU>, dim3(static_cast<unsigned>(grid)),
+                     dim3(kSumThreads), 0, stream, d, N, hdr, args, status);
     const int num_tiles = static_cast<int>(alloc_tiles(N));
     if (systematic) {
         // the frame offset U: the top 32 bits of element 2^62 of the stream
@@ -1047,20 +1055,20 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     const bool stall = (p->flags & SPP_FLAG_TEST_STALL_TILE1) != 0;
     if (num_tiles > kSinglePassMaxTiles && counts && !stall) {
         auto *tile_sums = reinterpret_cast<int *>(tiles);
-        assign_tile_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
-            d, N, hdr, stream_key(p->seed, p->frame), dt, args.hard, counts, s_out, holdout_w,
-            tile_sums);
-        offsets_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
-            counts, N, tile_sums, num_tiles, offsets, sample_pixel, capacity,
-            reinterpret_cast<long long *>(total), status);
+        launch_dependent(assign_tile_kernel, dim3(num_tiles), dim3(kScanThreads), 0, stream, d,
+                         N, hdr, stream_key(p->seed, p->frame), dt, args.hard, counts, s_out,
+                         holdout_w, tile_sums);
+        launch_dependent(offsets_kernel, dim3(num_tiles), dim3(kScanThreads), 0, stream, counts,
+                         N, tile_sums, num_tiles, offsets, sample_pixel, capacity,
+                         reinterpret_cast<long long *>(total), status);
         count_launch(3);
         return launch_status();
     }
-    assign_scan_kernel<<<num_tiles, kScanThreads, 0, stream>>>(
-        d, N, hdr, hdr, tiles, stream_key(p->seed, p->frame), dt, args.hard,
-        (p->flags & SPP_FLAG_TEST_STALL_TILE1) ? 1 : 0, counts, offsets,
-        sample_pixel, capacity, s_out, holdout_w, reinterpret_cast<long long *>(total), status,
-        num_tiles);
+    launch_dependent(assign_scan_kernel, dim3(num_tiles), dim3(kScanThreads), 0, stream, d, N,
+                     hdr, hdr, tiles, stream_key(p->seed, p->frame), dt, args.hard,
+                     (p->flags & SPP_FLAG_TEST_STALL_TILE1) ? 1 : 0, counts, offsets,
+                     sample_pixel, capacity, s_out, holdout_w,
+                     reinterpret_cast<long long *>(total), status, num_tiles);
     count_launch(2);
     return launch_status();
 }

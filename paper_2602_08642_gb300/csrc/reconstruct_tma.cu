@@ -151,6 +151,8 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
         fence_mbar_init();
     }
     __syncthreads();
+    pdl_wait();  // the previous kernel's outputs (this level's inputs) are complete
+    pdl_trigger();
     if (my_tiles == 0) return;
 
     auto tile_xy = [&](int k, int &x0, int &y0) {
@@ -474,8 +476,8 @@ int launch_variant(const CUtensorMap &ml, const CUtensorMap &mn, const CUtensorM
     g.num_tiles = g.tiles_x * tiles_y;
     int grid = sm_count();
     if (grid > g.num_tiles) grid = g.num_tiles;
-    kern<<<grid, kThreads, smem, stream>>>(ml, mn, mw, coarse, mask, Wl, Hl, g, out, out_ldr, tm,
-                                           status);
+    launch_dependent(kern, dim3(grid), dim3(kThreads), smem, stream, ml, mn, mw, coarse, mask, Wl,
+                     Hl, g, out, out_ldr, tm, status);
     count_launch();
     return launch_status();
 }

@@ -14,6 +14,8 @@ __global__ void __launch_bounds__(kRenderThreads)
 render_kernel(const float *__restrict__ clean, const int32_t *__restrict__ offsets,
               const int32_t *__restrict__ sample_pixel, const long long *__restrict__ total,
               long long capacity, long long N, uint64_t key, float4 *__restrict__ rgb) {
+    pdl_wait();
+    pdl_trigger();
     long long T = *total;
     if (T > capacity) T = capacity;
     const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
@@ -45,6 +47,8 @@ splat_kernel(const int32_t *__restrict__ offsets, const float4 *__restrict__ rgb
              const float *__restrict__ s, const float *__restrict__ hw, long long capacity, int W,
              int H, int L, LayerPtrs layers) {
     __shared__ float buf[2][3][kSplatH][kSplatTX + 1];
+    pdl_wait();
+    pdl_trigger();
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * kSplatTX, y0 = blockIdx.y * kSplatH;
     const long long N = static_cast<long long>(W) * H;
@@ -157,9 +161,10 @@ int spp_render_synthetic(const float *clean, const int32_t *offsets, const int32
     long long grid = (capacity + kRenderThreads - 1) / kRenderThreads;
     const long long max_grid = static_cast<long long>(sm_count()) * 8;
     if (grid > max_grid) grid = max_grid;
-    render_kernel<<<static_cast<unsigned>(grid), kRenderThreads, 0, stream>>>(
-        clean, offsets, sample_pixel, reinterpret_cast<const long long *>(total), capacity, N,
-        stream_key(seed, frame), reinterpret_cast<float4 *>(rgb));
+    launch_dependent(render_kernel, dim3(static_cast<unsigned>(grid)), dim3(kRenderThreads), 0,
+                     stream, clean, offsets, sample_pixel,
+                     reinterpret_cast<const long long *>(total), capacity, N,
+                     stream_key(seed, frame), reinterpret_cast<float4 *>(rgb));
     count_launch();
     return launch_status();
 }
@@ -183,8 +188,8 @@ int spp_splat_samples(const int32_t *offsets, const float *rgb, const float *s,
     if (static_cast<long long>(W) * H == 0) return SPP_OK;
     dim3 block(kSplatTX, kSplatTY);
     dim3 grid((W + kSplatTX - 1) / kSplatTX, (H + kSplatH - 1) / kSplatH);
-    splat_kernel<<<grid, block, 0, stream>>>(offsets, reinterpret_cast<const float4 *>(rgb), s,
-                                             holdout_w, capacity, W, H, L, lp);
+    launch_dependent(splat_kernel, grid, block, 0, stream, offsets,
+                     reinterpret_cast<const float4 *>(rgb), s, holdout_w, capacity, W, H, L, lp);
     count_launch();
     return launch_status();
 }

@@ -15,6 +15,10 @@ extern std::atomic<uint64_t> g_launches;
 
 inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Whether launch_dependent asks for programmatic serialisation (process-wide,
+// spp_set_dependent_launch).
+extern std::atomic<int> g_dependent_launch;
+
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Streaming multiprocessor count of the current device (cached per device).
@@ -22,6 +26,44 @@ int sm_count();
 
 // Maps the last CUDA error of a launch sequence to an SPP code.
 inline int launch_status() { return cudaGetLastError() == cudaSuccess ? SPP_OK : SPP_ERR_CUDA; }
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched by
+// launch_dependent may be scheduled while the kernel before it in the stream
+// is still running; pdl_wait() returns once that kernel has completed and its
+// memory operations are visible, so every such kernel calls it before its
+// first global load or store.  pdl_trigger() allows the next kernel's blocks
+// to be scheduled; called after pdl_wait(), at most two kernels of a stream
+// are resident at a time.  Both are no-ops in a kernel launched normally.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches kernel<<<grid, block, smem, stream>>>(args...) with programmatic
+// stream serialisation, so that its launch and prologue overlap the end of
+// the previous kernel in the stream; falls back to a plain launch if the
+// attribute is refused.
+template <typename... KArgs, typename... Args>
+inline void launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t stream, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    if (g_dependent_launch.load(std::memory_order_relaxed)) {
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...) == cudaSuccess) return;
+        (void)cudaGetLastError();
+        cfg.numAttrs = 0;
+    }
+    (void)cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // Records a device-side error: the first one wins.
 __device__ __forceinline__ void set_status(int32_t *status, int code) {

@@ -9,6 +9,7 @@
 namespace spp {
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_dependent_launch{1};
 
 int sm_count() {
     static std::mutex mu;
@@ -61,6 +62,10 @@ const char *spp_strerror(int code) {
 int spp_abi_version(void) { return 7; }
 
 uint64_t spp_launch_count(void) { return spp::g_launches.load(std::memory_order_relaxed); }
+
+int spp_set_dependent_launch(int on) { return spp::g_dependent_launch.exchange(on ? 1 : 0); }
+
+int spp_get_dependent_launch(void) { return spp::g_dependent_launch.load(); }
 
 int spp_get_status(const int32_t *status, cudaStream_t stream) {
     if (!status) return SPP_ERR_ARG;
