@@ -11,14 +11,16 @@
 //                                 x0 - 4 so that it is 16-byte aligned)
 //   warped  box 40 x 12 x 3      (full resolution only: W_t L_{t-1}, written
 //                                 by warp_prev_kernel, on the same halo)
+//   coarse  box 24 x 5 x 3       (below a coarser level: the cells of L-hat of
+//                                 that level the tile's upsampling taps read;
+//                                 x starts at x0 / 2 - 4, 16-byte aligned)
 // NS stages are in flight, so HBM keeps streaming while the threads compute.
 // There is no CTA-wide barrier in the tile loop: each warp waits on the
 // stage's mbarrier, the last warp done with a stage refills it, and the two
 // warps of a pixel row meet on their own mbarrier.
 // Halo cells outside the image arrive zero-filled and are never read: tiles
 // whose 5 x 5 footprint crosses the border index their clamp-to-edge source
-// cells.  The coarser level's four upsampling taps and the disocclusion mask
-// are plain loads issued one tile ahead.  Every mbarrier wait is bounded: on
+// cells.  The disocclusion mask is a plain load issued one tile ahead.  Every mbarrier wait is bounded: on
 // expiry the CTA records SPP_ERR_TIMEOUT, waits (bounded) for its copies
 // still in flight and exits.
 #include <cuda.h>
@@ -38,16 +40,24 @@ constexpr int kPixels = kPX * kPY;  // 256 pixels per tile
 constexpr int kThreads = 2 * kPixels; // two threads per pixel, each summing half of the taps
 constexpr int kBoxX = kPX + 8;     // 40: noisy / motion box width, x from x0 - 4
 constexpr int kBoxY = kPY + 4;     // 12: rows y0 - 2 .. y0 + 9
+constexpr int kCoarseX = kPX / 2 + 8;  // 24: coarse columns x0/2 - 4 .. x0/2 + 19
+constexpr int kCoarseY = kPY / 2 + 1;  // 5: coarse rows y0/2 .. y0/2 + 4
 constexpr int kWaitLimit = 1 << 20;
 
-template <int C, bool TEMP>
+template <int C, bool UP, bool TEMP>
 struct Stage {
     static constexpr int kLogitFloats = kPX * kPY * C;
     static constexpr int kNoisyFloats = kBoxX * kBoxY * 3;
     static constexpr int kWarpedFloats = TEMP ? kBoxX * kBoxY * 3 : 0;
-    static constexpr int kFloats = kLogitFloats + kNoisyFloats + kWarpedFloats;
-    static constexpr uint32_t kBytes = kFloats * 4u;
-    static_assert((kLogitFloats * 4) % 128 == 0 && (kNoisyFloats * 4) % 128 == 0, "box alignment");
+    static constexpr int kCoarseFloats = UP ? kCoarseX * kCoarseY * 3 : 0;
+    static constexpr int kCoarseSlot = (kCoarseFloats + 31) / 32 * 32;  // 128-byte multiple
+    // stage stride in floats, and the bytes its copies bring
+    static constexpr int kFloats = kLogitFloats + kNoisyFloats + kWarpedFloats + kCoarseSlot;
+    static constexpr uint32_t kBytes =
+        (kLogitFloats + kNoisyFloats + kWarpedFloats + kCoarseFloats) * 4u;
+    static_assert((kLogitFloats * 4) % 128 == 0 && (kNoisyFloats * 4) % 128 == 0 &&
+                      (kFloats * 4) % 128 == 0,
+                  "box alignment");
 };
 
 // ------------------------------------------------------------ PTX wrappers
@@ -116,11 +126,12 @@ template <int C, bool UP, bool TEMP, bool TONE, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
 recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
                  const __grid_constant__ CUtensorMap map_noisy,
-                 const __grid_constant__ CUtensorMap map_warped, const float *__restrict__ coarse,
-                 const uint8_t *__restrict__ mask, int Wl, int Hl, TileGeom geom,
+                 const __grid_constant__ CUtensorMap map_warped,
+                 const __grid_constant__ CUtensorMap map_coarse, const uint8_t *__restrict__ mask,
+                 int Wl, int Hl, TileGeom geom,
                  float *__restrict__ out, float *__restrict__ out_ldr, ToneArgs tm,
                  int32_t *status) {
-    using S = Stage<C, TEMP>;
+    using S = Stage<C, UP, TEMP>;
     static_assert(!TEMP || UP, "temporal term only at full resolution below a coarser level");
     static_assert(NS <= 8, "stage bookkeeping holds 8 stages");
     constexpr int kWarps = kThreads / 32;
@@ -163,6 +174,9 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
     auto logits_of = [&](int s) { return stages + s * S::kFloats; };
     auto noisy_of = [&](int s) { return stages + s * S::kFloats + S::kLogitFloats; };
     auto warped_of = [&](int s) { return stages + s * S::kFloats + S::kLogitFloats + S::kNoisyFloats; };
+    auto coarse_of = [&](int s) {
+        return stages + s * S::kFloats + S::kLogitFloats + S::kNoisyFloats + S::kWarpedFloats;
+    };
 
     auto issue = [&](int k) {
         const int s = k % NS;
@@ -174,6 +188,7 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
         tma_load_3d(logits_of(s), &map_logits, &full[s], x0, y0, 0);
         tma_load_3d(noisy_of(s), &map_noisy, &full[s], x0 - 4, y0 - 2, 0);
         if (TEMP) tma_load_3d(warped_of(s), &map_warped, &full[s], x0 - 4, y0 - 2, 0);
+        if (UP) tma_load_3d(coarse_of(s), &map_coarse, &full[s], x0 / 2 - 4, y0 / 2, 0);
     };
     if (tid == 0)
         for (int k = 0; k < NS && k < my_tiles; ++k) issue(k);
@@ -216,30 +231,36 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
     const int ty = warp & 7, tx = lane;
     const int p = ty * kPX + tx;
 
-    // per-pixel values outside the boxes, loaded one tile ahead (half 1)
-    float cv[12];
+    // the disocclusion mask, loaded one tile ahead (half 1)
     bool use_t = false;
-    auto prefetch = [&](int k, float (&c)[12], bool &ut) {
+    auto prefetch = [&](int k, bool &ut) {
         int x0, y0;
         tile_xy(k, x0, y0);
         const int xc = min(x0 + tx, Wl - 1), yc = min(y0 + ty, Hl - 1);
-        if (TEMP) ut = !(mask && __ldg(mask + static_cast<long long>(yc) * Wl + xc));
-        if (UP) {
-            const int Wc = Wl >> 1, Hc = Hl >> 1;
-            const long long Nc = static_cast<long long>(Wc) * Hc;
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int cx = min((xc + i) >> 1, Wc - 1), cy = min((yc + j) >> 1, Hc - 1);
-                    const long long q = static_cast<long long>(cy) * Wc + cx;
-                    c[(2 * j + i) * 3 + 0] = __ldg(coarse + q);
-                    c[(2 * j + i) * 3 + 1] = __ldg(coarse + Nc + q);
-                    c[(2 * j + i) * 3 + 2] = __ldg(coarse + 2 * Nc + q);
-                }
-        }
+        ut = !(mask && __ldg(mask + static_cast<long long>(yc) * Wl + xc));
     };
-    if (half == 1) prefetch(0, cv, use_t);
+    if (TEMP && half == 1) prefetch(0, use_t);
+    // the upsampling term: kappa_u weights on the coarse cells of the stage
+    constexpr int kCP = kCoarseX * kCoarseY;
+    auto up_taps = [&](int s, int x0, int y0, const float *lu, float mL, float &ws, float &b0,
+                       float &b1, float &b2) {
+        const float *cb = coarse_of(s);
+        const int xc = min(x0 + tx, Wl - 1), yc = min(y0 + ty, Hl - 1);
+        const int Wc = Wl >> 1, Hc = Hl >> 1;
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int cx = min((xc + i) >> 1, Wc - 1) - (x0 / 2 - 4);
+                const int cy = min((yc + j) >> 1, Hc - 1) - y0 / 2;
+                const int o = cy * kCoarseX + cx;
+                const float e = ex2_approx(fmaf(lu[2 * j + i], kLog2e, -mL));
+                ws += e;
+                b0 = fmaf(e, cb[o], b0);
+                b1 = fmaf(e, cb[kCP + o], b1);
+                b2 = fmaf(e, cb[2 * kCP + o], b2);
+            }
+    };
 
     constexpr int kNC = kBoxX * kBoxY;
     constexpr int kPlane = kPX * kPY;
@@ -251,9 +272,8 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
             abort();
             return;
         }
-        float cvn[12];
         bool use_tn = false;
-        if (half == 1 && k + 1 < my_tiles) prefetch(k + 1, cvn, use_tn);
+        if (TEMP && half == 1 && k + 1 < my_tiles) prefetch(k + 1, use_tn);
 
         // tiles whose 5 x 5 footprint crosses the image border read clamped
         // cells (the zero-filled ones are never read)
@@ -317,14 +337,7 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
                     for (int kk = 4; kk < 29; ++kk) m = fmaxf(m, lg[kk]);
                 }
                 const float mL = m * kLog2e;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float e = ex2_approx(fmaf(lg[q], kLog2e, -mL));
-                    wsum += e;
-                    a0 = fmaf(e, cv[3 * q + 0], a0);
-                    a1 = fmaf(e, cv[3 * q + 1], a1);
-                    a2 = fmaf(e, cv[3 * q + 2], a2);
-                }
+                up_taps(s, x0, y0, lg, mL, wsum, a0, a1, a2);
                 if (use_t) gather_rows(warped_of(s), lg + 4, 0, 5, mL);
             }
         } else {
@@ -351,16 +364,7 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
                 gather_rows(nz, lg, 0, 3, mL);
             else
                 gather_rows(nz, lg, 3, 5, mL);
-            if (UP && half == 1) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float e = ex2_approx(fmaf(lu[q], kLog2e, -mL));
-                    wsum += e;
-                    a0 = fmaf(e, cv[3 * q + 0], a0);
-                    a1 = fmaf(e, cv[3 * q + 1], a1);
-                    a2 = fmaf(e, cv[3 * q + 2], a2);
-                }
-            }
+            if (UP && half == 1) up_taps(s, x0, y0, lu, mL, wsum, a0, a1, a2);
         }
         release(k);
 
@@ -371,8 +375,6 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
             pk[2 * kPixels + p] = a0;
             pk[3 * kPixels + p] = a1;
             pk[4 * kPixels + p] = a2;
-#pragma unroll
-            for (int q = 0; q < 12; ++q) cv[q] = cvn[q];
             use_t = use_tn;
         }
         // rendezvous of the pixel row's two warps (bounded)
@@ -461,11 +463,11 @@ bool make_map(CUtensorMap *map, const float *base, int W, int H, int planes, int
 
 template <int C, bool UP, bool TEMP, bool TONE, int NS>
 int launch_variant(const CUtensorMap &ml, const CUtensorMap &mn, const CUtensorMap &mw,
-                   const float *coarse, const uint8_t *mask, int Wl, int Hl, float *out,
+                   const CUtensorMap &mc, const uint8_t *mask, int Wl, int Hl, float *out,
                    float *out_ldr, const ToneArgs &tm, int32_t *status, cudaStream_t stream) {
-    using S = Stage<C, TEMP>;
+    using S = Stage<C, UP, TEMP>;
     const size_t smem =
-        128 + 256 + static_cast<size_t>(NS) * S::kBytes + 2u * 5u * kPixels * sizeof(float);
+        128 + 256 + static_cast<size_t>(NS) * S::kFloats * 4u + 2u * 5u * kPixels * sizeof(float);
     auto kern = recon_tma_kernel<C, UP, TEMP, TONE, NS>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(smem)) != cudaSuccess)
@@ -476,8 +478,8 @@ int launch_variant(const CUtensorMap &ml, const CUtensorMap &mn, const CUtensorM
     g.num_tiles = g.tiles_x * tiles_y;
     int grid = sm_count();
     if (grid > g.num_tiles) grid = g.num_tiles;
-    launch_dependent(kern, dim3(grid), dim3(kThreads), smem, stream, ml, mn, mw, coarse, mask, Wl,
-                     Hl, g, out, out_ldr, tm, status);
+    launch_dependent(kern, dim3(grid), dim3(kThreads), smem, stream, ml, mn, mw, mc, mask, Wl, Hl,
+                     g, out, out_ldr, tm, status);
     count_launch();
     return launch_status();
 }
@@ -502,7 +504,9 @@ bool launch_recon_tma(const float *noisy, const float *logits, int C_total, int 
     if (!temp && C_used == 54) return false;
     if (!up && C_used != 25) return false;
     if (up && !temp && C_used != 29) return false;
-    CUtensorMap ml, mn, mw;
+    // the coarse level's map needs 16-byte row strides
+    if (up && (((Wl >> 1) % 4) != 0 || !aligned16(coarse))) return false;
+    CUtensorMap ml, mn, mw, mc;
     if (!make_map(&ml, logits, Wl, Hl, C_total, kPX, kPY, C_used)) return false;
     if (!make_map(&mn, noisy, Wl, Hl, 3, kBoxX, kBoxY, 3)) return false;
     if (temp) {
@@ -510,21 +514,26 @@ bool launch_recon_tma(const float *noisy, const float *logits, int C_total, int 
     } else {
         mw = mn;  // unused
     }
+    if (up) {
+        if (!make_map(&mc, coarse, Wl >> 1, Hl >> 1, 3, kCoarseX, kCoarseY, 3)) return false;
+    } else {
+        mc = mn;  // unused
+    }
     const bool tone = out_ldr != nullptr;
     if (temp) {
-        *rc = tone ? launch_variant<54, true, true, true, 3>(ml, mn, mw, coarse, mask, Wl, Hl, out,
+        *rc = tone ? launch_variant<54, true, true, true, 3>(ml, mn, mw, mc, mask, Wl, Hl, out,
                                                              out_ldr, tm, status, stream)
-                   : launch_variant<54, true, true, false, 3>(ml, mn, mw, coarse, mask, Wl, Hl, out,
+                   : launch_variant<54, true, true, false, 3>(ml, mn, mw, mc, mask, Wl, Hl, out,
                                                               out_ldr, tm, status, stream);
     } else if (up) {
-        *rc = tone ? launch_variant<29, true, false, true, 5>(ml, mn, mw, coarse, mask, Wl, Hl, out,
+        *rc = tone ? launch_variant<29, true, false, true, 5>(ml, mn, mw, mc, mask, Wl, Hl, out,
                                                               out_ldr, tm, status, stream)
-                   : launch_variant<29, true, false, false, 5>(ml, mn, mw, coarse, mask, Wl, Hl,
+                   : launch_variant<29, true, false, false, 5>(ml, mn, mw, mc, mask, Wl, Hl,
                                                                out, out_ldr, tm, status, stream);
     } else {
-        *rc = tone ? launch_variant<25, false, false, true, 5>(ml, mn, mw, coarse, mask, Wl, Hl,
+        *rc = tone ? launch_variant<25, false, false, true, 5>(ml, mn, mw, mc, mask, Wl, Hl,
                                                                out, out_ldr, tm, status, stream)
-                   : launch_variant<25, false, false, false, 5>(ml, mn, mw, coarse, mask, Wl, Hl,
+                   : launch_variant<25, false, false, false, 5>(ml, mn, mw, mc, mask, Wl, Hl,
                                                                 out, out_ldr, tm, status, stream);
     }
     return true;

@@ -45,6 +45,15 @@ def test_status_strings_and_version():
     assert spp.spp_strerror(-99) == "unknown status code"
 
 
+def test_dependent_launch_switch():
+    import paper_2602_08642_gb300._binding as B
+    assert B.spp_get_dependent_launch()  # on by default
+    assert B.spp_set_dependent_launch(False) is True
+    assert B.spp_get_dependent_launch() is False
+    assert B.spp_set_dependent_launch(True) is False
+    assert B.spp_get_dependent_launch()
+
+
 def test_workspace_queries():
     import paper_2602_08642_gb300 as spp
     assert spp.spp_alloc_workspace_bytes(1920, 1080) == 256 + 8 * ((1920 * 1080 + 2047) // 2048)

@@ -412,6 +412,38 @@ def test_two_frame_sequence_feeds_back(spp):
         prev_gpu, prev_ref = out, ref["hdr"]
 
 
+def test_dependent_launch_gives_identical_frames(spp):
+    """Programmatic dependent launch changes only when the kernels are
+    scheduled: a sequence of frames run back to back (no host sync between
+    kernels) is bit for bit the same with it on and off."""
+    from paper_2602_08642_gb300 import _binding as Bnd
+    W, H, L, B = 640, 360, 3, 0.25
+    xs = [inp.frame_inputs(W, H, L, frame=t, temporal=True) for t in range(3)]
+    xs = [dict(d=dev(x["d"]), clean=dev(x["clean"]), logits=[dev(a) for a in x["logits"]],
+               mv=dev(x["mv"]), mask=dev(x["mask"])) for x in xs]
+    outs = {}
+    was = Bnd.spp_get_dependent_launch()
+    try:
+        for on in (True, False):
+            Bnd.spp_set_dependent_launch(on)
+            fr = spp.Frame(W, H, L, max_budget=B)
+            fr.clear_status()
+            prev, got = None, []
+            for t, x in enumerate(xs):
+                out = fr.run(x["d"], x["clean"], x["logits"], spp.make_params(B, frame=t),
+                             prev=prev, mv=x["mv"], mask=x["mask"])
+                got.append((fr.counts.clone(), out.clone(), fr.ldr.clone()))
+                prev = out
+            torch.cuda.synchronize()
+            assert fr.check_status() == 0
+            outs[on] = got
+    finally:
+        Bnd.spp_set_dependent_launch(was)
+    for a, b in zip(outs[True], outs[False]):
+        for u, v in zip(a, b):
+            assert torch.equal(u, v)
+
+
 # ---------------------------------------------------------------------------
 # Blue-noise dithered discretisation (Sec. 6.3)
 # ---------------------------------------------------------------------------
