@@ -45,11 +45,11 @@ UNIT = "Mpix/s"
 # which the hash checks.
 LEVEL0_TRAFFIC = {
     "workload": "1080p",
-    "bytes_per_launch": 546_155_264,  # median of three captured launches
+    "bytes_per_launch": 546_265_088,  # median of three captured launches
     "sources": ("paper_2602_08642_gb300/csrc/reconstruct_tma.cu",
                 "paper_2602_08642_gb300/csrc/recon_common.cuh",
                 "paper_2602_08642_gb300/csrc/spp_internal.cuh"),
-    "sha256": "70fad2727aef0926b6d83ae414f3f894ee677dca82f9ca35db45e1fb687b34cc",
+    "sha256": "9e6a466866af4ff0592fa57326241559f8e4a070433668755fd150fa2987543c",
 }
 
 
