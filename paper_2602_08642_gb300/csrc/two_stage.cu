@@ -83,6 +83,9 @@ __global__ void latent_tanh_kernel(const float *__restrict__ raw, int64_t n,
 }
 
 // W_t of C planes (the previous-frame warp of Appendix A on every channel).
+// CC > 0 fixes the channel count at compile time, so that the 4 CC tap
+// loads of a pixel are all in flight at once; CC = 0 takes C at run time.
+template <int CC>
 __global__ void warp_channels_kernel(const float *__restrict__ src, int C,
                                      const float *__restrict__ mv, int W, int H,
                                      float *__restrict__ out) {
@@ -91,10 +94,16 @@ __global__ void warp_channels_kernel(const float *__restrict__ src, int C,
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int x = static_cast<int>(i % W), y = static_cast<int>(i / W);
         const Taps t = warp_taps(mv, N, W, H, x, y, i);
-        for (int c = 0; c < C; ++c) {
+        auto warp_one = [&](int c) {
             const float *p = src + c * N;
-            out[c * N + i] = (1.0f - t.fy) * ((1.0f - t.fx) * p[t.i00] + t.fx * p[t.i01]) +
-                             t.fy * ((1.0f - t.fx) * p[t.i10] + t.fx * p[t.i11]);
+            out[c * N + i] = (1.0f - t.fy) * ((1.0f - t.fx) * __ldg(p + t.i00) + t.fx * __ldg(p + t.i01)) +
+                             t.fy * ((1.0f - t.fx) * __ldg(p + t.i10) + t.fx * __ldg(p + t.i11));
+        };
+        if constexpr (CC > 0) {
+#pragma unroll
+            for (int c = 0; c < CC; ++c) warp_one(c);
+        } else {
+            for (int c = 0; c < C; ++c) warp_one(c);
         }
     }
 }
@@ -323,7 +332,11 @@ extern "C" int spp_warp_channels(const float *src, int C, const float *mv, int W
     if (!aligned16(src) || !aligned16(mv) || !aligned16(out)) return SPP_ERR_ALIGN;
     const int64_t n = static_cast<int64_t>(W) * H;
     if (n == 0) return SPP_OK;
-    spp::warp_channels_kernel<<<grid_for(n), 256, 0, stream>>>(src, C, mv, W, H, out);
+    if (C == spp::kLatent)
+        spp::warp_channels_kernel<spp::kLatent><<<grid_for(n), 256, 0, stream>>>(src, C, mv, W, H,
+                                                                                out);
+    else
+        spp::warp_channels_kernel<0><<<grid_for(n), 256, 0, stream>>>(src, C, mv, W, H, out);
     count_launch();
     return launch_status();
 }

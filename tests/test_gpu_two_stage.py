@@ -234,6 +234,10 @@ def test_feature_assembly_and_latent_warp_parity(spp, W, H):
     lat2 = torch.empty(TS.N_LATENT, H, W, device="cuda")
     bnd.check(bnd.spp_warp_channels(th, TS.N_LATENT, dev(mv), W, H, lat2))
     assert np.allclose(host(lat2), ref_lat, rtol=2e-6, atol=1e-6)
+    # a channel count other than the latents' (the run-time loop)
+    lat3 = torch.empty(3, H, W, device="cuda")
+    bnd.check(bnd.spp_warp_channels(th[:3].contiguous(), 3, dev(mv), W, H, lat3))
+    assert np.allclose(host(lat3), ref_lat[:3], rtol=2e-6, atol=1e-6)
     lat_np = host(lat)
     x19 = torch.empty(19, H, W, device="cuda")
     bnd.check(bnd.spp_assemble_sampler_features(g["albedo"], g["normal"], g["depth"], dev(mv),
