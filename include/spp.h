@@ -585,9 +585,12 @@ int spp_net_pack(int net, const float *theta, int with_backward, void *packed,
                  size_t packed_bytes, cudaStream_t stream);
 /* Forward workspace bytes (activations kept for the backward). */
 size_t spp_net_workspace_bytes(int net, int B, int W, int H);
-/* Forward on B frames (W, H divisible by 4): in [B][cin][H][W] FP32;
- * head0 [B][h0][H][W], head1 [B][h1][H/2][W/2], head2 [B][h2][H/4][W/4]
- * FP32 planar (NULL allowed for an absent head). */
+/* Forward on B frames (W, H divisible by 4, else SPP_ERR_SHAPE): in
+ * [B][cin][H][W] FP32; head0 [B][h0][H][W], head1 [B][h1][H/2][W/2], head2
+ * [B][h2][H/4][W/4] FP32 planar (NULL allowed for an absent head, required
+ * for a present one: SPP_ERR_ARG).  packed and ws 256-byte aligned
+ * (SPP_ERR_ALIGN); ws at least spp_net_workspace_bytes (SPP_ERR_WORKSPACE);
+ * unknown net: SPP_ERR_ARG. */
 int spp_net_forward(int net, const void *packed, const float *in, int B, int W, int H,
                     float *head0, float *head1, float *head2, void *ws, size_t ws_bytes,
                     int32_t *status, cudaStream_t stream);
@@ -596,7 +599,9 @@ int spp_net_forward(int net, const void *packed, const float *in, int B, int W, 
  * offset + b H W channels 2 bytes).  spp_assemble_sampler_input /
  * spp_assemble_denoiser_input write it there directly, and
  * spp_net_forward_prepared then runs the network without the FP32 input
- * (the same results as spp_net_forward on the FP32 features). */
+ * (the same results as spp_net_forward on the FP32 features; the same
+ * argument checks).  spp_net_input_layout: SPP_ERR_ARG for an unknown net,
+ * a negative size or a NULL output pointer. */
 int spp_net_input_layout(int net, int B, int W, int H, size_t *offset, int *channels);
 int spp_net_forward_prepared(int net, const void *packed, int B, int W, int H, float *head0,
                              float *head1, float *head2, void *ws, size_t ws_bytes,
