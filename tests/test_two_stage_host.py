@@ -38,3 +38,17 @@ def test_invalid_network_arguments(B):
         B.spp_net_layer(1, 13)
     assert B.SPP_DEMOD_PLANE == 54 and B.SPP_LATENT_PLANE == 57 and B.SPP_LATENT_CHANNELS == 7
     assert B.SPP_LATENT_PLANE + B.SPP_LATENT_CHANNELS == U.SPECS["denoiser"][1][0]
+
+
+@pytest.mark.parametrize("spec", sorted(NETS))
+@pytest.mark.parametrize("Bn,W,H", [(1, 32, 32), (2, 48, 36), (8, 128, 128), (1, 3840, 2160)])
+def test_input_copy_lies_inside_the_forward_workspace(B, spec, Bn, W, H):
+    """The BF16 NHWC input copy the assembly entries write in place: aligned
+    for the 16-byte vector stores, padded to 16 or 32 channels, and wholly
+    inside the forward workspace."""
+    net = NETS[spec]
+    off, ch = B.spp_net_input_layout(net, Bn, W, H)
+    cin, _ = B.spp_net_spec(net)
+    assert ch == (16 if cin <= 16 else 32) and ch >= cin
+    assert off % 256 == 0
+    assert off + Bn * H * W * ch * 2 <= B.spp_net_workspace_bytes(net, Bn, W, H)
