@@ -486,6 +486,24 @@ def test_tau_c1_joins_and_bounds(orc, s, h):
     assert np.all(dt <= 0.5 + 1e-9) and np.all(dt >= 0)
 
 
+def test_tau_limits_and_symmetry(orc):
+    """Sec. 5's limits of the curve: at s = h = 1 no linear segment is left and
+    tau(ln L) is L/2 below L = 1 and 1 - 1/(2L) above (a sigmoid in log
+    radiance, symmetric about L = 1); as s, h -> 0 the toe and shoulder
+    sharpen to the clamped line (1 + x)/2 on [-1, 1].  Equal shadow and
+    highlight make tau point-symmetric about (0, 1/2)."""
+    for L in (1e-3, 0.2, 0.5, 1.0, 2.0, 7.0, 1e3):
+        t = orc.tau(math.log(L), 1.0, 1.0)
+        assert abs(t - (L / 2 if L <= 1 else 1 - 1 / (2 * L))) < 1e-15
+    eps = 1e-6
+    for x in np.linspace(-3, 3, 121):
+        t = orc.tau(float(x), eps, eps)
+        assert abs(t - min(max(0.5 * (1 + x), 0.0), 1.0)) <= eps / 2 + 1e-15
+    for sh in (0.1, 0.5, 0.9):
+        for x in np.linspace(-4, 4, 81):
+            assert abs(orc.tau(float(x), sh, sh) + orc.tau(float(-x), sh, sh) - 1) < 1e-15
+
+
 def test_tonemap_derivative_bounds(orc):
     """0 < dtau/dlogL < 1/2 and 0 < dtau/dL < e/2 (Sec. 5), alpha = beta = 1."""
     Ls = np.exp(np.linspace(-12, 8, 2001))
