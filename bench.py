@@ -214,21 +214,28 @@ def level0_algorithmic_bytes(W, H, mask: np.ndarray) -> int:
 # --------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and --impl reference)
 # --------------------------------------------------------------------------
+def oracle_inputs(W, H, L):
+    """One frame of the workload's inputs for the oracle (FP64 logits, a
+    previous output), prepared outside the timed calls."""
+    import spp_inputs as inp
+    x = inp.frame_inputs(W, H, L, frame=1, temporal=True)
+    x["logits64"] = [a.astype(np.float64) for a in x["logits"]]
+    return x, np.random.default_rng(1).random((3, H, W))
+
+
 def oracle_frame_seconds(W, H, L, B, x, prev):
     import oracle
     t0 = time.perf_counter()
-    oracle.frame(x["d"], x["clean"], [a.astype(np.float64) for a in x["logits"]], W, H, L, B,
-                 prev=prev, mv=x["mv"], mask=x["mask"], frame_index=1)
+    oracle.frame(x["d"], x["clean"], x["logits64"], W, H, L, B, prev=prev, mv=x["mv"],
+                 mask=x["mask"], frame_index=1)
     return time.perf_counter() - t0
 
 
 def cpu_sample(W, H, L, B, budget_s):
     """Runs the oracle on band crops of the workload's frame (full width,
     H/8 rows, same per-pixel work) until budget_s of CPU time is spent."""
-    import spp_inputs as inp
     Hs = max(H // 8 // (1 << (L - 1)) * (1 << (L - 1)), 1 << (L - 1))
-    x = inp.frame_inputs(W, Hs, L, frame=1, temporal=True)
-    prev = np.random.default_rng(1).random((3, Hs, W))
+    x, prev = oracle_inputs(W, Hs, L)
     spent, pix = 0.0, 0
     while spent < budget_s:
         spent += oracle_frame_seconds(W, Hs, L, B, x, prev)
@@ -237,16 +244,35 @@ def cpu_sample(W, H, L, B, budget_s):
         f"workload), {pix // (W * Hs)} runs, {spent:.1f} s, 1 thread"
 
 
+REFERENCE_SECONDS = 90.0  # about this much CPU time for the timed reference steps
+REFERENCE_MIN_ROWS = 32   # a band small enough to make per-call overhead count is not run
+
+
+def reference_band_rows(W, H, L, steps, seconds_per_pixel, target_s=REFERENCE_SECONDS):
+    """Rows of the full-width band one reference step runs: as many as let
+    `steps` steps take about target_s, a multiple of 2^(L-1) (one block of the
+    coarsest level), between REFERENCE_MIN_ROWS (or H/8 if smaller) and H/8."""
+    q = 1 << (L - 1)
+    hmax = max(H // 8 // q * q, q)
+    hmin = min(max(REFERENCE_MIN_ROWS // q * q, q), hmax)
+    rows = int(target_s / max(steps, 1) / (seconds_per_pixel * W))
+    return min(max(rows // q * q, hmin), hmax)
+
+
 def run_reference(args, rank, world):
     W, H, F, B, L = WORKLOADS[args.workload]
     if rank != 0:
         return
     import oracle
     oracle.build()
-    import spp_inputs as inp
+    # one calibration frame on the largest band sets the band of the steps
     Hs = max(H // 8 // (1 << (L - 1)) * (1 << (L - 1)), 1 << (L - 1))
-    x = inp.frame_inputs(W, Hs, L, frame=1, temporal=True)
-    prev = np.random.default_rng(1).random((3, Hs, W))
+    x, prev = oracle_inputs(W, Hs, L)
+    per_pixel = oracle_frame_seconds(W, Hs, L, B, x, prev) / (W * Hs)
+    rows = reference_band_rows(W, H, L, args.steps, per_pixel)
+    if rows != Hs:
+        Hs = rows
+        x, prev = oracle_inputs(W, Hs, L)
     for _ in range(args.warmup):
         oracle_frame_seconds(W, Hs, L, B, x, prev)
     t = [oracle_frame_seconds(W, Hs, L, B, x, prev) for _ in range(args.steps)]

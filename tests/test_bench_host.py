@@ -99,3 +99,17 @@ def test_measured_peaks_or_fallback(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, kind = bench.measured_peaks()
     assert kind == "fallback" and peaks == {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def test_reference_band_scales_with_the_step_count():
+    """The reference arm's per-step band shrinks as the step count grows so
+    that the run stays near its time target, within [2^(L-1), H/8] rows."""
+    W, H, L = 1920, 1080, 3
+    spp = 0.164 / (1920 * 132)  # seconds per pixel of the FP64 oracle, one core
+    assert bench.reference_band_rows(W, H, L, 20, spp) == 132          # the whole band
+    r = bench.reference_band_rows(W, H, L, 2000, spp)
+    assert r % 4 == 0 and bench.REFERENCE_MIN_ROWS <= r < 132
+    assert 2000 * r * W * spp <= bench.REFERENCE_SECONDS
+    assert bench.reference_band_rows(W, H, L, 10 ** 7, spp) == bench.REFERENCE_MIN_ROWS
+    assert bench.reference_band_rows(64, 64, 2, 1, 1e-9) == 8          # H/8 for a small frame
+    assert bench.reference_band_rows(64, 64, 2, 10 ** 7, 1e-3) == 8    # the floor capped at H/8
