@@ -193,3 +193,30 @@ def test_features_layout():
     assert np.array_equal(f[:3], alb) and np.array_equal(f[3:6], nrm)
     assert f[6, 0, 0] == 0.0 and abs(f[6, 1, 1] - 1.0) < 1e-15
     assert np.all(f[7:9] == 1.0) and np.array_equal(f[9:], prev)
+
+
+def test_conv_of_upsampled_input_is_four_phase_convolutions():
+    """The decoder's upsampled half: a 3x3 convolution of a nearest-x2
+    upsampled tensor equals, at output phase (a, b), a 2x2 convolution of the
+    coarse tensor with merged taps (phase 0: taps 0 and +1 onto offset 0, tap
+    -1 onto offset -1; phase 1: taps -1 and 0 onto offset 0, tap +1 onto
+    offset +1), zero padding on both sides.  Checked in FP64 on random data,
+    including the borders."""
+    rng = np.random.default_rng(31)
+    C, O, h, w = 3, 4, 5, 7
+    x = rng.standard_normal((C, h, w))
+    wt = rng.standard_normal((O, C, 3, 3))
+    b = rng.standard_normal(O)
+    full = U.conv3x3(U.up2(x), wt, b)
+    xp = np.zeros((C, h + 2, w + 2))
+    xp[:, 1:-1, 1:-1] = x
+    # merged taps per phase and axis: offset (-1, 0, +1) -> which 3x3 taps
+    merge = {0: {-1: [0], 0: [1, 2]}, 1: {0: [0, 1], 1: [2]}}
+    for a in (0, 1):
+        for c in (0, 1):
+            out = np.broadcast_to(b[:, None, None], (O, h, w)).copy()
+            for oy, tys in merge[a].items():
+                for ox, txs in merge[c].items():
+                    wm = sum(wt[:, :, ty, tx] for ty in tys for tx in txs)
+                    out += np.einsum("oi,ihw->ohw", wm, xp[:, 1 + oy:1 + oy + h, 1 + ox:1 + ox + w])
+            assert np.allclose(full[:, a::2, c::2], out, rtol=1e-12, atol=1e-12)
