@@ -102,6 +102,16 @@ uint64_t spp_launch_count(void);
 int spp_set_dependent_launch(int on);
 int spp_get_dependent_launch(void);
 
+/* Test of the bounded waits of the pipelined reconstruction: the next
+ * launch of the pipelined kernel (spp_reconstruct_level, or a level of
+ * spp_reconstruct_frame, whose width is a multiple of 4) issues no copies
+ * for its tile number `tile` (tiles of 64 x 4 pixels, row-major), so the
+ * waits for that tile run out after about 100 ms; that launch then records
+ * SPP_ERR_TIMEOUT in its status word, the tiles after it in the same CTA
+ * stay unwritten, and later calls are unaffected.  One-shot and
+ * process-wide; -1 (the default) cancels.  SPP_ERR_ARG for tile < -1. */
+int spp_test_stall_reconstruction(int tile);
+
 /* Copies the device status word to the host (synchronises the stream) and
  * returns it (SPP_OK or an SPP_ERR_* code); SPP_ERR_CUDA if the copy fails. */
 int spp_get_status(const int32_t *status, cudaStream_t stream);

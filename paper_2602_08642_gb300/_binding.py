@@ -69,6 +69,7 @@ _SIGS = {
     "spp_launch_count": (_U64, []),
     "spp_set_dependent_launch": (_I, [_I]),
     "spp_get_dependent_launch": (_I, []),
+    "spp_test_stall_reconstruction": (_I, [_I]),
     "spp_get_status": (_I, [_P, _P]),
     "spp_clear_status": (_I, [_P, _P]),
     "spp_alloc_workspace_bytes": (_SZ, [_I, _I]),
@@ -214,6 +215,12 @@ def spp_set_dependent_launch(on: bool) -> bool:
 
 def spp_get_dependent_launch() -> bool:
     return bool(lib.spp_get_dependent_launch())
+
+
+def spp_test_stall_reconstruction(tile: int) -> int:
+    """Test of the bounded waits: the next pipelined reconstruction launch
+    issues no copies for tile `tile` (-1 cancels)."""
+    return lib.spp_test_stall_reconstruction(tile)
 
 
 def spp_get_status(status: torch.Tensor, stream=None) -> int:

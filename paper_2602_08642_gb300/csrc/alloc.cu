@@ -1147,8 +1147,11 @@ void *static_scratch_address(int *rc) {
     static std::mutex mu;
     constexpr int kMaxDevices = 64;
     static void *addr[kMaxDevices] = {nullptr};
+    // a failed runtime call's error is taken off the thread's error state
+    // here, so that this call reports it and the next, unrelated call does not
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        (void)cudaGetLastError();
         *rc = SPP_ERR_CUDA;
         return nullptr;
     }
@@ -1156,6 +1159,7 @@ void *static_scratch_address(int *rc) {
     if (!addr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, spp_static_scratch) != cudaSuccess || !p) {
+            (void)cudaGetLastError();
             *rc = SPP_ERR_CUDA;
             return nullptr;
         }

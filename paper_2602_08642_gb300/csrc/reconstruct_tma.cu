@@ -22,8 +22,11 @@
 // Halo cells outside the image arrive zero-filled and are never read: tiles
 // whose 5 x 5 footprint crosses the border index their clamp-to-edge source
 // cells.  The disocclusion mask is a plain load issued one tile ahead.
-// Every mbarrier wait is bounded: on expiry the CTA records SPP_ERR_TIMEOUT,
-// waits (bounded) for its copies still in flight and exits.
+// Every mbarrier wait is bounded in time (kWaitNs of %globaltimer): on expiry
+// the CTA records SPP_ERR_TIMEOUT, waits (bounded the same way) for the
+// copies it has issued and exits.  Those copies read in-bounds boxes of this
+// kernel's own inputs and complete without help from any other CTA, so the
+// drain wait runs out only if the memory system itself has failed.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -45,7 +48,7 @@ constexpr int kBoxX = kPX + 8;     // noisy / warped box width, x from x0 - 4
 constexpr int kBoxY = kPY + 4;     // rows y0 - 2 .. y0 + kPY + 1
 constexpr int kCoarseX = kPX / 2 + 8;  // coarse columns x0/2 - 4 .. x0/2 + kPX/2 + 3
 constexpr int kCoarseY = kPY / 2 + 1;  // coarse rows y0/2 .. y0/2 + kPY/2
-constexpr int kWaitLimit = 1 << 20;
+constexpr unsigned long long kWaitNs = 100000000ull;  // 100 ms per wait
 
 template <int C, bool UP, bool TEMP>
 struct Stage {
@@ -101,10 +104,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Gives up (returns false) once kWaitNs have passed since the first poll.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
 }
 
 __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, uint64_t *bar,
@@ -133,7 +146,7 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
                  const __grid_constant__ CUtensorMap map_coarse, const uint8_t *__restrict__ mask,
                  int Wl, int Hl, TileGeom geom,
                  float *__restrict__ out, float *__restrict__ out_ldr, ToneArgs tm,
-                 int32_t *status) {
+                 int32_t *status, int stall_tile) {
     using S = Stage<C, UP, TEMP>;
     static_assert(!TEMP || UP, "temporal term only at full resolution below a coarser level");
     static_assert(NS <= 8, "stage bookkeeping holds 8 stages");
@@ -185,6 +198,9 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
         const int s = k % NS;
         int x0, y0;
         tile_xy(k, x0, y0);
+        // test of the bounded waits: this tile's stage is never filled (and
+        // keeps its previous use, whose copies have all landed)
+        if (blockIdx.x + k * G == stall_tile) return;
         uses[s] = k / NS + 1;
         fence_proxy_async();
         mbar_expect_tx(&full[s], S::kBytes);
@@ -197,8 +213,8 @@ recon_tma_kernel(const __grid_constant__ CUtensorMap map_logits,
         for (int k = 0; k < NS && k < my_tiles; ++k) issue(k);
     __syncthreads();
 
-    // After a wait gave up: record it, wait (bounded) for the copies still in
-    // flight on every stage, and let the caller return.  Every wait in this
+    // After a wait gave up: record it, wait (bounded) for the copies this CTA
+    // issued on every stage, and let the caller return.  Every wait in this
     // kernel is bounded, so the other warps reach the same point.
     auto abort = [&]() {
         set_status(status, SPP_ERR_TIMEOUT);
@@ -469,7 +485,8 @@ bool make_map(CUtensorMap *map, const float *base, int W, int H, int planes, int
 template <int C, bool UP, bool TEMP, bool TONE, int NS>
 int launch_variant(const CUtensorMap &ml, const CUtensorMap &mn, const CUtensorMap &mw,
                    const CUtensorMap &mc, const uint8_t *mask, int Wl, int Hl, float *out,
-                   float *out_ldr, const ToneArgs &tm, int32_t *status, cudaStream_t stream) {
+                   float *out_ldr, const ToneArgs &tm, int32_t *status, int stall_tile,
+                   cudaStream_t stream) {
     using S = Stage<C, UP, TEMP>;
     const size_t smem =
         128 + 256 + static_cast<size_t>(NS) * S::kFloats * 4u + 2u * 5u * kPixels * sizeof(float);
@@ -484,7 +501,7 @@ int launch_variant(const CUtensorMap &ml, const CUtensorMap &mn, const CUtensorM
     int grid = sm_count();
     if (grid > g.num_tiles) grid = g.num_tiles;
     launch_dependent(kern, dim3(grid), dim3(kThreads), smem, stream, ml, mn, mw, mc, mask, Wl, Hl,
-                     g, out, out_ldr, tm, status);
+                     g, out, out_ldr, tm, status, stall_tile);
     count_launch();
     return launch_status();
 }
@@ -525,21 +542,22 @@ bool launch_recon_tma(const float *noisy, const float *logits, int C_total, int 
         mc = mn;  // unused
     }
     const bool tone = out_ldr != nullptr;
+    const int stall = g_recon_stall_tile.exchange(-1);
     if (temp) {
         *rc = tone ? launch_variant<54, true, true, true, 3>(ml, mn, mw, mc, mask, Wl, Hl, out,
-                                                             out_ldr, tm, status, stream)
+                                                             out_ldr, tm, status, stall, stream)
                    : launch_variant<54, true, true, false, 3>(ml, mn, mw, mc, mask, Wl, Hl, out,
-                                                              out_ldr, tm, status, stream);
+                                                              out_ldr, tm, status, stall, stream);
     } else if (up) {
         *rc = tone ? launch_variant<29, true, false, true, 5>(ml, mn, mw, mc, mask, Wl, Hl, out,
-                                                              out_ldr, tm, status, stream)
+                                                              out_ldr, tm, status, stall, stream)
                    : launch_variant<29, true, false, false, 5>(ml, mn, mw, mc, mask, Wl, Hl,
-                                                               out, out_ldr, tm, status, stream);
+                                                               out, out_ldr, tm, status, stall, stream);
     } else {
         *rc = tone ? launch_variant<25, false, false, true, 5>(ml, mn, mw, mc, mask, Wl, Hl,
-                                                               out, out_ldr, tm, status, stream)
+                                                               out, out_ldr, tm, status, stall, stream)
                    : launch_variant<25, false, false, false, 5>(ml, mn, mw, mc, mask, Wl, Hl,
-                                                                out, out_ldr, tm, status, stream);
+                                                                out, out_ldr, tm, status, stall, stream);
     }
     return true;
 }

@@ -19,6 +19,10 @@ inline void count_launch(uint64_t n = 1) { g_launches.fetch_add(n, std::memory_o
 // spp_set_dependent_launch).
 extern std::atomic<int> g_dependent_launch;
 
+// Test of the reconstruction's bounded waits: the tile whose copies the next
+// pipelined reconstruction launch skips (-1: none; spp_test_stall_reconstruction).
+extern std::atomic<int> g_recon_stall_tile;
+
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Streaming multiprocessor count of the current device (cached per device).

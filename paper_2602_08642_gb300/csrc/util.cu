@@ -1,8 +1,6 @@
 // Status codes, launch counter and small utilities of the C ABI.
 #include <mutex>
 
-#include <mutex>
-
 #include "spp_internal.cuh"
 #include "tma_host.cuh"
 
@@ -10,6 +8,7 @@ namespace spp {
 
 std::atomic<uint64_t> g_launches{0};
 std::atomic<int> g_dependent_launch{1};
+std::atomic<int> g_recon_stall_tile{-1};
 
 int sm_count() {
     static std::mutex mu;
@@ -66,6 +65,12 @@ uint64_t spp_launch_count(void) { return spp::g_launches.load(std::memory_order_
 int spp_set_dependent_launch(int on) { return spp::g_dependent_launch.exchange(on ? 1 : 0); }
 
 int spp_get_dependent_launch(void) { return spp::g_dependent_launch.load(); }
+
+int spp_test_stall_reconstruction(int tile) {
+    if (tile < -1) return SPP_ERR_ARG;
+    spp::g_recon_stall_tile.store(tile);
+    return SPP_OK;
+}
 
 int spp_get_status(const int32_t *status, cudaStream_t stream) {
     if (!status) return SPP_ERR_ARG;

@@ -321,6 +321,40 @@ def test_reconstruct_level_intermediate_parity(spp):
     assert_rel(host(out), ref, what="mid level")
 
 
+def test_reconstruct_bounded_wait_reports_timeout(spp):
+    """A tile whose copies are never issued makes its CTA's pipeline waits
+    run out (about 100 ms): the launch returns, the status says
+    SPP_ERR_TIMEOUT, the tiles of the other CTAs are still right, and the
+    next call is unaffected."""
+    W, H = 960, 540  # level 1 of a 1080p frame: 15 x 135 tiles of 64 x 4
+    rng = np.random.default_rng(43)
+    noisy = (rng.random((3, H, W)) * 2).astype(np.float32)
+    coarse = (rng.random((3, H // 2, W // 2)) * 2).astype(np.float32)
+    lg = rng.standard_normal((29, H, W)).astype(np.float32) * 3
+    ref = oracle.reconstruct_level(noisy, lg, coarse=coarse)
+    tiles_x, tiles = W // 64, (W // 64) * ((H + 3) // 4)
+    G = min(torch.cuda.get_device_properties(0).multi_processor_count, tiles)
+    stalled = G + 7  # the second tile of CTA 7 (issued in the pipeline's prologue)
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")[:1]
+    out = torch.full((3, H, W), -1.0, device="cuda")
+    assert spp.binding.spp_test_stall_reconstruction(stalled) == 0
+    spp.check(spp.spp_reconstruct_level(dev(noisy), dev(lg), 29, dev(coarse), None, None, W, H,
+                                        None, out, None, st))
+    assert spp.spp_get_status(st) == spp.binding.SPP_ERR_TIMEOUT
+    got = host(out)
+    t = np.arange(tiles)
+    mine = (t % G == 7) & (t >= stalled)  # CTA 7 stops at the stalled tile
+    tile_of = (np.arange(H)[:, None] // 4) * tiles_x + np.arange(W)[None, :] // 64
+    keep = ~mine[tile_of]
+    assert_rel(got[:, keep], ref[:, keep], what="tiles of the other CTAs")
+    # the hook is one-shot: the next call runs every tile
+    spp.spp_clear_status(st)
+    spp.check(spp.spp_reconstruct_level(dev(noisy), dev(lg), 29, dev(coarse), None, None, W, H,
+                                        None, out, None, st))
+    assert spp.spp_get_status(st) == 0
+    assert_rel(host(out), ref, what="after the timeout")
+
+
 def test_reconstruct_invariants_on_gpu(spp):
     """Constant layers and previous frame give the constant back; one-hot
     centre logits give the identity; zero motion makes W_t the identity."""

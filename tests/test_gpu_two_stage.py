@@ -405,6 +405,13 @@ def test_demodulated_frame_backward_parity(spp, W, H, temporal):
     bnd.check(bnd.spp_demodulate_backward(out["hdr"], g_t, out["layers"][0], g_n[0], out["wd"],
                                           g_wd, dev(c), out["m"], W, H, g_L0, g_c))
     r_lg, r_L0, r_c = TS.reconstruct_demod_backward(L0, c, logits, g, warped, mask, L)
+
+    def ratio(got, ref, rtol, afrac):  # worst error in units of the bound
+        bound = rtol * np.abs(ref) + afrac * max(float(np.abs(ref).max()), 1e-30)
+        return float((np.abs(got - ref) / bound).max())
+    print("worst error / (1e-4 |ref| + 1e-5 max|ref|): logits",
+          [ratio(host(g_lg[l]), r_lg[l], 1e-4, 1e-5) for l in range(L)],
+          "c", ratio(host(g_c), r_c, 1e-4, 1e-5))
     for l in range(L):
         assert_grad(host(g_lg[l]), r_lg[l], f"logits {l}", rtol=3e-4, afrac=3e-5)
     assert_grad(host(g_L0), r_L0, "L0", rtol=1e-4, afrac=1e-5)
