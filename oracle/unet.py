@@ -135,14 +135,15 @@ def features(albedo, normal, depth, mv, prev_ldr):
 # ------------------------------------------------------------ primitives
 def conv3x3(x, w, b):
     """y[o][y][x] = b[o] + sum_{i,dy,dx} w[o][i][dy][dx] x[i][y+dy-1][x+dx-1],
-    zero outside the image.  Written as the nine shifted tap products."""
+    zero outside the image.  Written as the nine shifted tap products, each
+    a matrix product over the input channels (np.tensordot, FP64)."""
     C, H, W = x.shape
     xp = np.zeros((C, H + 2, W + 2))
     xp[:, 1:-1, 1:-1] = x
     y = np.broadcast_to(np.asarray(b, np.float64)[:, None, None], (w.shape[0], H, W)).copy()
     for dy in range(3):
         for dx in range(3):
-            y += np.einsum("oi,ihw->ohw", w[:, :, dy, dx], xp[:, dy:dy + H, dx:dx + W])
+            y += np.tensordot(w[:, :, dy, dx], xp[:, dy:dy + H, dx:dx + W], axes=1)
     return y
 
 
@@ -155,8 +156,8 @@ def conv3x3_backward(x, w, g):
     gw = np.empty_like(w)
     for dy in range(3):
         for dx in range(3):
-            gw[:, :, dy, dx] = np.einsum("ohw,ihw->oi", g, xp[:, dy:dy + H, dx:dx + W])
-            gxp[:, dy:dy + H, dx:dx + W] += np.einsum("oi,ohw->ihw", w[:, :, dy, dx], g)
+            gw[:, :, dy, dx] = np.tensordot(g, xp[:, dy:dy + H, dx:dx + W], axes=([1, 2], [1, 2]))
+            gxp[:, dy:dy + H, dx:dx + W] += np.tensordot(w[:, :, dy, dx].T, g, axes=1)
     return gxp[:, 1:-1, 1:-1], gw, g.sum(axis=(1, 2))
 
 
