@@ -52,8 +52,15 @@ e w S_f) / s per pixel (Eq. stoch_rnoisy), f = floor(s), p = s - f:
                     ln(u / (1 - u)))), lambda the inverse temperature;
                     backward: dw/dp = lambda w (1 - w) / (p (1 - p)); at test
                     time the hard rule, w > 1/2 iff u > 1 - p
-DASR's surrogate (Kuznetsov et al. 2018) is not defined in the paper and is
-not built.
+  DASR              the deterministic rounding of Sec. 4.1 (Eq. kuz_fw,
+                    after Kuznetsov et al. 2018): n = round(s) samples,
+                    L^0 = (sum_{j<n} S_j) / n for s >= 1/2, else 0; its
+                    surrogate gradient (Eq. kuz_grad) dL^0/ds = (L^ref - L^0)
+                    / round(s) for s >= 1/2, else L^ref, with L^ref the
+                    reference radiance of the pixel.  round() takes halves
+                    up (n = floor(s) + [s - floor(s) >= 1/2]): the equation's
+                    branch s >= 1/2 divides by round(s), which must then be at
+                    least one.  The same rule serves training and test time.
 
 Pins (tests/test_oracle_variants_pins.py): block-constant images are fixed
 points, the sum is preserved (FP64), symmetry, agreement with a library
@@ -64,7 +71,10 @@ constant density, and agreement with the C oracle's independent stochastic
 assignment at u = a_i; for the estimators: the Gumbel relaxation's gradient
 against finite differences of its forward, its hard limit (lambda -> inf) is
 the stochastic map, and the straight-through gradient against its closed
-form on one pixel.
+form on one pixel; for DASR hand-computed counts at and around the
+half-integers, |n - s| <= 1/2 with exact rational arithmetic, the forward's
+sample mean and its zero below the threshold, the budget's total within N/2,
+and hand-computed surrogate gradients on both sides of the threshold.
 """
 from __future__ import annotations
 
@@ -205,3 +215,58 @@ def splat_backward_estimator(a, rgb, L0, grad_L0, estimator: str, lam: float = 1
     else:
         raise ValueError(estimator)
     return out
+
+
+# ------------------------------------- DASR: deterministic rounding (Sec. 4.1)
+def dasr_counts(s) -> np.ndarray:
+    """n_i = round(s_i) of Eq. kuz_fw, halves up: floor(s) + [s - floor(s) >= 1/2]
+    (s - floor(s) is exact in FP64, so the comparison is exact)."""
+    s = np.asarray(s, np.float64)
+    f = np.floor(s)
+    return (f + ((s - f) >= 0.5)).astype(np.int64)
+
+
+def alloc_dasr(d, B: float, phi: float = 0.125):
+    """Deterministic sample map of the FP32 density d [N]: the s_i of the
+    budget normalisation (Sec. 3), n_i = round(s_i), offsets, and the
+    normaliser of Eq. kuz_fw, max(n_i, 1) (a pixel without samples has
+    L^0 = 0 whatever it is divided by)."""
+    import oracle
+    rc, S, a, c = oracle.budget_coeffs(d, B, phi)
+    if rc != 0:
+        raise ValueError(f"budget rc={rc}")
+    d64 = np.asarray(d, np.float32).astype(np.float64).ravel()
+    s = a + c * d64                                   # FP64, product then sum
+    n = dasr_counts(s)
+    offsets = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+    return SystematicAlloc(counts=n, offsets=offsets, s=s, norm=np.maximum(n, 1),
+                           T=int(offsets[-1]))
+
+
+def splat_dasr(counts, rgb, W: int, H: int, L: int) -> list[np.ndarray]:
+    """Eq. kuz_fw per pixel, L^0_i = (sum_{j<n_i} S_ij) / n_i (0 when n_i = 0),
+    with the samples of pixel i consecutive in rgb [T][3] (pixel order), then
+    the 2^l x 2^l block means of Eq. app-pyramid."""
+    n = np.asarray(counts, np.int64).ravel()
+    rgb = np.asarray(rgb, np.float64).reshape(-1, 3)
+    offsets = np.concatenate([[0], np.cumsum(n)])
+    L0 = np.zeros((W * H, 3))
+    for i in np.flatnonzero(n):
+        L0[i] = rgb[offsets[i]:offsets[i + 1]].sum(axis=0) / n[i]
+    L0 = L0.T.reshape(3, H, W)
+    layers = [L0]
+    for l in range(1, L):
+        f = 1 << l
+        layers.append(L0.reshape(3, H // f, f, W // f, f).mean(axis=(2, 4)))
+    return layers
+
+
+def splat_backward_dasr(counts, L0, grad_L0, ref) -> np.ndarray:
+    """dLoss/ds_i through Eq. kuz_grad: sum_c g_ic (L^ref_ic - L^0_ic) / n_i
+    where n_i = round(s_i) >= 1 (s_i >= 1/2), else sum_c g_ic L^ref_ic."""
+    n = np.asarray(counts, np.int64).ravel()
+    L0 = np.asarray(L0, np.float64).reshape(3, -1)
+    g = np.asarray(grad_L0, np.float64).reshape(3, -1)
+    ref = np.asarray(ref, np.float64).reshape(3, -1)
+    sampled = (g * (ref - L0)).sum(axis=0) / np.maximum(n, 1)
+    return np.where(n >= 1, sampled, (g * ref).sum(axis=0))

@@ -167,3 +167,66 @@ def test_straight_through_uses_the_renderers_sample(orc):
     S_f = orc.render(clean, off2, 0xBEEF, 3)[off2[i + 1] - 1]
     expect = float(g[:, i] @ (S_f - L0[:, i])) / a.s[i]
     assert abs(grad[i] - expect) <= 1e-12 * max(1.0, abs(expect))
+
+
+# ------------------------------------------------ DASR (Sec. 4.1, Eq. kuz_fw / kuz_grad)
+def test_dasr_counts_at_and_around_the_half_integers():
+    """round(s) of Eq. kuz_fw by hand: halves go up, so s >= 1/2 gives at
+    least one sample and s < 1/2 none."""
+    below = lambda x: np.nextafter(x, 0.0)  # noqa: E731
+    s = [0.0, 1e-300, 0.25, below(0.5), 0.5, 0.51, 1.0, 1.49, below(1.5), 1.5, 2.5, 3.0,
+         7.49, 7.5]
+    want = [0, 0, 0, 0, 1, 1, 1, 1, 1, 2, 3, 3, 7, 8]
+    assert V.dasr_counts(s).tolist() == want
+
+
+def test_dasr_counts_are_the_nearest_integer_exactly():
+    """|n - s| <= 1/2 in exact rational arithmetic, and a tie goes up."""
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    s = np.concatenate([rng.lognormal(-1.0, 1.5, 2000), np.arange(0, 40) * 0.5,
+                        np.nextafter(np.arange(1, 40) * 0.5, 0.0)])
+    for si, ni in zip(s, V.dasr_counts(s)):
+        e = Fraction(int(ni)) - Fraction(float(si))
+        assert abs(e) <= Fraction(1, 2)
+        if abs(e) == Fraction(1, 2):
+            assert e > 0
+
+
+def test_dasr_forward_is_the_sample_mean_and_zero_without_samples():
+    """Eq. kuz_fw on a 2 x 2 frame by hand, and the level-1 block mean."""
+    counts = [0, 1, 3, 2]
+    rgb = [(1, 2, 3),                                   # pixel 1
+           (1, 0, 0), (2, 0, 0), (6, 3, 0),             # pixel 2
+           (4, 4, 4), (0, 2, 8)]                        # pixel 3
+    l0, l1 = V.splat_dasr(counts, rgb, 2, 2, 2)
+    want = np.array([[0, 0, 0], [1, 2, 3], [3, 1, 0], [2, 3, 6]], np.float64).T.reshape(3, 2, 2)
+    assert np.array_equal(l0, want)
+    assert np.allclose(l1.ravel(), [1.5, 1.5, 2.25], rtol=0, atol=1e-15)
+
+
+def test_dasr_alloc_budget_and_threshold():
+    """round() moves each pixel by at most 1/2, so the total is within N/2
+    of B N (Sec. 3 fixes sum s = B N); a pixel is sampled iff s >= 1/2."""
+    W, H, B = 64, 48, 0.75
+    d = np.random.default_rng(4).lognormal(size=W * H).astype(np.float32)
+    a = V.alloc_dasr(d, B)
+    assert np.array_equal(a.counts, V.dasr_counts(a.s))
+    assert abs(a.T - B * W * H) <= W * H / 2
+    assert np.array_equal(a.counts >= 1, a.s >= 0.5)
+    assert np.array_equal(np.diff(a.offsets), a.counts)
+    assert np.array_equal(a.norm, np.maximum(a.counts, 1))
+    # a uniform density puts s = B on every pixel (exact here): B = 2.5 rounds up
+    u = V.alloc_dasr(np.ones(256, np.float32), 2.5)
+    assert np.all(u.s == 2.5) and np.all(u.counts == 3) and u.T == 768
+
+
+def test_dasr_surrogate_gradient_by_hand():
+    """Eq. kuz_grad: (L^ref - L^0) / round(s) where sampled, L^ref where not,
+    each dotted with the loss gradient of the pixel's three channels."""
+    counts = [2, 0]
+    L0 = np.array([[3, 3, 3], [0, 0, 0]], np.float64).T
+    ref = np.array([[2, 2, 2], [1, 2, 3]], np.float64).T
+    g = np.array([[1, 0, 2], [1, 1, 1]], np.float64).T
+    got = V.splat_backward_dasr(counts, L0, g, ref)
+    assert got.tolist() == [(1 * -1 + 0 + 2 * -1) / 2, 1 + 2 + 3]
