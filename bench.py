@@ -120,6 +120,8 @@ def rank_frame(t: int, rank: int) -> int:
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
+CLOCK_WINDOW_S = 0.5  # the clocks are read over at least this much of the same load
+
 class ClockSampler:
     FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -135,7 +137,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -163,9 +165,10 @@ class ClockSampler:
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         t0 = getattr(self, "t_start", 0.0)
-        t1 = getattr(self, "t_end", float("inf"))
-        window = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.15]
-        if not window:  # region shorter than the sampling period: nearest samples after it
+        # the timed region plus the tail of the same steps that follows it
+        t1 = max(getattr(self, "t_end", float("inf")), getattr(self, "t_tail_end", 0.0))
+        window = [ln for (t, ln) in self.lines if t0 <= t <= t1 + 0.06]
+        if not window:  # no sample in the window: the nearest ones after it
             window = [ln for (t, ln) in self.lines if t >= t0][:2]
         for ln in window:
             parts = [p.strip() for p in ln.split(",")]
@@ -181,7 +184,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "window_s": (t1 - t0) if t1 != float("inf") else None}
 
 
 # --------------------------------------------------------------------------
@@ -402,6 +406,16 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     clocks.mark("t_end")
     launches = spp.spp_launch_count() - launches0
+    # a timed region shorter than the sampler's period holds no clock sample
+    # of its own: the same steps keep running, untimed, until CLOCK_WINDOW_S
+    # have passed since it began, and the clocks are read over both
+    k = args.warmup + args.steps
+    while time.time() - clocks.t_start < CLOCK_WINDOW_S:
+        for _ in range(16):
+            step(k)
+            k += 1
+        torch.cuda.synchronize()
+    clocks.mark("t_tail_end")
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
@@ -611,8 +625,9 @@ def run_learned(args, spp, Bnd, dev, rank):
 def run_estimator_ablation(args, spp, rank):
     """The gradient estimators of the discretisation (Sec. 4.3 and the
     ablation of Sec. 7): the joint predictor trained from the same start
-    with the relaxed ramp, the straight-through estimator and the
-    Gumbel-softmax relaxation; held-out PSNR at 0.25 spp on 128 x 128
+    with the relaxed ramp, the straight-through estimator, the
+    Gumbel-softmax relaxation and the DASR surrogate of Sec. 4.1
+    (deterministic rounding); held-out PSNR at 0.25 spp on 128 x 128
     two-frame samples (each model with its own test-time rule)."""
     import torch
 
@@ -626,7 +641,7 @@ def run_estimator_ablation(args, spp, rank):
     fixed = [torch.from_numpy(a).cuda() for a in inp.fixed_logits(size, size, 3, True)]
     res = {"steps": steps, "crop": size, "batch": 8, "spp": budget,
            "plain_psnr_db": float(np.mean(Lm.evaluate(held, budget, None, fixed)))}
-    for est in ("relaxed", "straight_through", "gumbel"):
+    for est in ("relaxed", "straight_through", "gumbel", "dasr"):
         theta0 = torch.from_numpy(inp.unet_params(Lm.layer_table(), seed=5,
                                                   head_bias=inp.fixed_head_bias()))
         tr = Lm.Trainer(theta0, 8, size, budget, lr=1e-3, estimator=est)

@@ -51,6 +51,14 @@ extern "C" {
  * temperature; the count map then exceeds B N (capacity for about N (1 + B)
  * samples).  Not with the systematic map. */
 #define SPP_HOLDOUT_GUMBEL 2
+/* the deterministic rounding of DASR (Sec. 4.1, Eq. kuz_fw, after Kuznetsov
+ * et al. 2018), the ablation of Sec. 7: n_i = round(s_i) with halves going
+ * up (floor(s_i) + [s_i - floor(s_i) >= 1/2], decided in FP64), no uniform
+ * and no holdout weight (holdout_w = 1).  s_out then receives max(n_i, 1),
+ * so that spp_splat_samples computes Eq. kuz_fw, L0_i = (sum_{j<n_i}
+ * S_ij) / n_i and 0 without samples.  The same rule serves training and
+ * test time.  Not with the systematic map. */
+#define SPP_HOLDOUT_DASR 3
 
 /* spp_params.flags */
 #define SPP_FLAG_EXACT_FP64 1u /* evaluate every pixel on the FP64 path (no FP32 filter) */
@@ -66,7 +74,7 @@ typedef struct spp_params {
     double lambda;           /* ramp temperature, >= 1; the paper uses 10 */
     uint64_t seed;           /* seed of the per-pixel uniforms u_i */
     uint32_t frame;          /* frame index t (selects the uniform stream) */
-    int32_t holdout_mode;    /* SPP_HOLDOUT_RAMP, SPP_HOLDOUT_HARD or SPP_HOLDOUT_GUMBEL */
+    int32_t holdout_mode;    /* SPP_HOLDOUT_RAMP, _HARD, _GUMBEL or _DASR */
     uint32_t flags;          /* SPP_FLAG_* */
     uint32_t reserved;       /* must be 0 */
 } spp_params;
@@ -753,11 +761,20 @@ int spp_alloc_sample_map_systematic(const float *d, int W, int H, const spp_para
  *   SPP_ESTIMATOR_GUMBEL            forward with SPP_HOLDOUT_GUMBEL; dw/dp =
  *                                   lambda w (1 - w) / (p (1 - p)) with w =
  *                                   holdout_w of the forward
+ *   SPP_ESTIMATOR_DASR              forward with SPP_HOLDOUT_DASR (Sec. 4.1);
+ *                                   the surrogate of Eq. kuz_grad,
+ *                                   sum_c g_c (ref_c - L^0_c) / n where
+ *                                   n = counts_i >= 1, sum_c g_c ref_c where
+ *                                   n = 0, with ref ([3][H][W], passed as
+ *                                   `clean`) the reference radiance L^ref;
+ *                                   reads counts, layer0, grad_layer0 and
+ *                                   clean only
  * Other arguments as spp_splat_backward; clean is read by the
- * straight-through estimator only. */
+ * straight-through and DASR estimators only. */
 #define SPP_ESTIMATOR_RELAXED 0
 #define SPP_ESTIMATOR_STRAIGHT_THROUGH 1
 #define SPP_ESTIMATOR_GUMBEL 2
+#define SPP_ESTIMATOR_DASR 3
 int spp_splat_backward_estimator(const int32_t *offsets, const int32_t *counts, const float *rgb,
                                  const float *s, const float *layer0, const float *grad_layer0,
                                  const float *holdout_w, int64_t capacity, int W, int H,

@@ -36,9 +36,11 @@ SPP_ERR_CUDA = -8
 SPP_HOLDOUT_RAMP = 0
 SPP_HOLDOUT_HARD = 1
 SPP_HOLDOUT_GUMBEL = 2
+SPP_HOLDOUT_DASR = 3
 SPP_ESTIMATOR_RELAXED = 0
 SPP_ESTIMATOR_STRAIGHT_THROUGH = 1
 SPP_ESTIMATOR_GUMBEL = 2
+SPP_ESTIMATOR_DASR = 3
 SPP_FLAG_EXACT_FP64 = 1
 SPP_FLAG_TEST_STALL_TILE1 = 1 << 31
 
@@ -237,8 +239,9 @@ def spp_alloc_workspace_bytes(W: int, H: int) -> int:
 
 def make_params(budget: float, *, uniform_fraction: float = 0.125, lam: float = 10.0,
                 seed: int = 0x5EED, frame: int = 0, hard: bool = False, gumbel: bool = False,
-                exact_fp64: bool = False) -> spp_params:
-    mode = SPP_HOLDOUT_GUMBEL if gumbel else (SPP_HOLDOUT_HARD if hard else SPP_HOLDOUT_RAMP)
+                dasr: bool = False, exact_fp64: bool = False) -> spp_params:
+    mode = (SPP_HOLDOUT_DASR if dasr else SPP_HOLDOUT_GUMBEL if gumbel
+            else SPP_HOLDOUT_HARD if hard else SPP_HOLDOUT_RAMP)
     return spp_params(budget, uniform_fraction, lam, seed & 0xFFFFFFFFFFFFFFFF, frame, mode,
                       SPP_FLAG_EXACT_FP64 if exact_fp64 else 0, 0)
 

@@ -61,8 +61,10 @@ struct BudgetArgs {
 };
 
 // Holdout modes of the assignment (SPP_HOLDOUT_*): 0 ramp, 1 hard, 2 the
-// training forward of the Gumbel-softmax estimator.
+// training forward of the Gumbel-softmax estimator, 3 the deterministic
+// rounding of DASR (Sec. 4.1).
 constexpr int kModeGumbel = 2;
+constexpr int kModeDasr = 3;
 
 // ---------------------------------------------------------------- K1
 // Every finite FP32 x >= 0 is m 2^(pos - 149) with an integer m < 2^24 and
@@ -340,6 +342,15 @@ __device__ __noinline__ PixelOut assign_exact(float d, uint64_t bits, double ka,
     const double f = floor(sd);
     const double p = __dsub_rn(sd, f);
     const double t = __dsub_rn(1.0, p);
+    if (hard == kModeDasr) {
+        // Eq. kuz_fw: round(s) samples, halves up (p is exact); the splat
+        // divides by max(n, 1), which s_out carries in this mode
+        PixelOut r;
+        r.n = static_cast<int>(f) + (p >= 0.5 ? 1 : 0);
+        r.w = 1.0f;
+        r.s = static_cast<float>(r.n > 1 ? r.n : 1);
+        return r;
+    }
     if (hard == kModeGumbel) {
         // binary concrete relaxation: the extra sample is always traced,
         // weighted by sigma(lambda (ln(p / (1 - p)) + ln(u / (1 - u))))
@@ -993,8 +1004,9 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     if (!(p->budget > 0.0) || !(p->budget < 1e30)) return SPP_ERR_ARG;
     if (!(p->uniform_fraction >= 0.0) || !(p->uniform_fraction <= 1.0)) return SPP_ERR_ARG;
     if (p->holdout_mode != SPP_HOLDOUT_RAMP && p->holdout_mode != SPP_HOLDOUT_HARD &&
-        p->holdout_mode != SPP_HOLDOUT_GUMBEL)
+        p->holdout_mode != SPP_HOLDOUT_GUMBEL && p->holdout_mode != SPP_HOLDOUT_DASR)
         return SPP_ERR_ARG;
+    if (p->holdout_mode == SPP_HOLDOUT_DASR && systematic) return SPP_ERR_ARG;
     if (p->holdout_mode == SPP_HOLDOUT_RAMP && !(p->lambda >= 1.0 && p->lambda < 1e30))
         return SPP_ERR_ARG;
     if (p->holdout_mode == SPP_HOLDOUT_GUMBEL &&
@@ -1019,12 +1031,18 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     BudgetArgs args;
     args.budget = p->budget;
     args.phi = p->uniform_fraction;
-    args.lambda = p->holdout_mode == SPP_HOLDOUT_HARD ? 1.0 : p->lambda;
-    args.hard = p->holdout_mode == SPP_HOLDOUT_HARD ? 1
+    const bool no_ramp = p->holdout_mode == SPP_HOLDOUT_HARD || p->holdout_mode == SPP_HOLDOUT_DASR;
+    args.lambda = no_ramp ? 1.0 : p->lambda;
+    args.hard = p->holdout_mode == SPP_HOLDOUT_HARD     ? 1
                 : p->holdout_mode == SPP_HOLDOUT_GUMBEL ? kModeGumbel
+                : p->holdout_mode == SPP_HOLDOUT_DASR   ? kModeDasr
                                                         : 0;
-    // the Gumbel forward decides every pixel in FP64 (no float-float filter)
-    args.force_exact = ((p->flags & SPP_FLAG_EXACT_FP64) || args.hard == kModeGumbel) ? 1 : 0;
+    // the Gumbel forward and the deterministic rounding decide every pixel in
+    // FP64 (no float-float filter)
+    args.force_exact =
+        ((p->flags & SPP_FLAG_EXACT_FP64) || args.hard == kModeGumbel || args.hard == kModeDasr)
+            ? 1
+            : 0;
 
     // 8 values per thread and pass: enough blocks to fill every SM several
     // times over (the per-element carry chain is latency-bound)

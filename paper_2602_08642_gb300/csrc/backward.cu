@@ -465,6 +465,28 @@ splat_backward_est_kernel(const int32_t *__restrict__ offsets, const int32_t *__
     grad_s[i] = acc;
 }
 
+// The DASR surrogate (Sec. 4.1, Eq. kuz_grad): (ref - L0) / n dotted with
+// the loss gradient where the pixel has n >= 1 samples, ref dotted with it
+// where it has none.
+__global__ void __launch_bounds__(256)
+splat_backward_dasr_kernel(const int32_t *__restrict__ counts, const float *__restrict__ L0,
+                           const float *__restrict__ gL0, const float *__restrict__ ref,
+                           long long N, float *__restrict__ grad_s) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int n = counts[i];
+    float acc = 0.0f;
+    if (n >= 1) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc = fmaf(gL0[c * N + i], ref[c * N + i] - L0[c * N + i], acc);
+        acc /= static_cast<float>(n);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc = fmaf(gL0[c * N + i], ref[c * N + i], acc);
+    }
+    grad_s[i] = acc;
+}
+
 // Density backward, pass 1: sum d and sum d g (FP64 accumulation).
 __global__ void __launch_bounds__(256)
 density_reduce_kernel(const float *__restrict__ d, const float *__restrict__ g, long long N,
@@ -688,6 +710,19 @@ int spp_splat_backward_estimator(const int32_t *offsets, const int32_t *counts, 
     if (estimator == SPP_ESTIMATOR_RELAXED)
         return spp_splat_backward(offsets, counts, rgb, s, layer0, grad_layer0, capacity, W, H, p,
                                   grad_s, stream);
+    if (estimator == SPP_ESTIMATOR_DASR) {
+        if (W < 0 || H < 0 || !counts || !layer0 || !grad_layer0 || !clean || !grad_s)
+            return SPP_ERR_ARG;
+        if (!aligned16(counts) || !aligned16(layer0) || !aligned16(grad_layer0) ||
+            !aligned16(clean) || !aligned16(grad_s))
+            return SPP_ERR_ALIGN;
+        const long long N = static_cast<long long>(W) * H;
+        if (N == 0) return SPP_OK;
+        splat_backward_dasr_kernel<<<static_cast<unsigned>((N + 255) / 256), 256, 0, stream>>>(
+            counts, layer0, grad_layer0, clean, N, grad_s);
+        count_launch();
+        return launch_status();
+    }
     if (estimator != SPP_ESTIMATOR_STRAIGHT_THROUGH && estimator != SPP_ESTIMATOR_GUMBEL)
         return SPP_ERR_ARG;
     if (!p || W < 0 || H < 0 || capacity < 0 || !offsets || !counts || !s || !layer0 ||

@@ -177,7 +177,8 @@ class FrameData:
 
 ESTIMATORS = {"relaxed": B.SPP_ESTIMATOR_RELAXED,
               "straight_through": B.SPP_ESTIMATOR_STRAIGHT_THROUGH,
-              "gumbel": B.SPP_ESTIMATOR_GUMBEL}
+              "gumbel": B.SPP_ESTIMATOR_GUMBEL,
+              "dasr": B.SPP_ESTIMATOR_DASR}
 GUMBEL_LAMBDA = 10.0  # inverse temperature of the Gumbel-softmax relaxation
 
 
@@ -186,9 +187,11 @@ class Renderer:
 
     estimator selects the gradient of the discretisation (Sec. 4.3, and the
     ablation of Sec. 7): "relaxed" (the ramp), "straight_through" (hard
-    forward) or "gumbel" (relaxed forward that traces every extra sample).
-    With train=False the straight-through and Gumbel models run the hard
-    test-time rule."""
+    forward), "gumbel" (relaxed forward that traces every extra sample) or
+    "dasr" (deterministic rounding with the surrogate gradient of Sec. 4.1,
+    whose reference radiance is the clean image).  With train=False the
+    straight-through and Gumbel models run the hard test-time rule; DASR
+    keeps its deterministic rounding."""
 
     def __init__(self, B_: int, W: int, H: int, budget: float, dither_mask=None,
                  estimator: str = "relaxed", train: bool = True):
@@ -198,8 +201,10 @@ class Renderer:
         self.estimator, self.train = estimator, train
         # blue-noise rank mask (device int16 [T][T]) or None for white noise
         self.dither = dither_mask
-        # the Gumbel forward traces the extra sample of every pixel
-        cap_budget = budget + 1.0 if (estimator == "gumbel" and train) else budget
+        # the Gumbel forward traces the extra sample of every pixel; rounding
+        # to the nearest integer adds at most half a sample per pixel
+        cap_budget = (budget + 1.0 if (estimator == "gumbel" and train)
+                      else budget + 0.5 if estimator == "dasr" else budget)
         self.frames = [Frame(W, H, LEVELS, max_budget=cap_budget) for _ in range(B_)]
         self.cur_clean = [None] * B_
         self.cur_seed = [0] * B_
@@ -235,10 +240,11 @@ class Renderer:
             fr.alloc(d, params)
 
     def params(self, frame: int, seed: int):
+        dasr = self.estimator == "dasr"
         gumbel = self.estimator == "gumbel" and self.train
-        hard = self.estimator != "relaxed" and not gumbel
+        hard = self.estimator != "relaxed" and not gumbel and not dasr
         return B.make_params(self.budget, uniform_fraction=PHI, seed=seed, frame=frame, hard=hard,
-                             gumbel=gumbel, lam=GUMBEL_LAMBDA if gumbel else 10.0)
+                             gumbel=gumbel, dasr=dasr, lam=GUMBEL_LAMBDA if gumbel else 10.0)
 
     def previous_frame(self, b: int, d, logits, clean, seed: int, frame: int):
         """Frame t-1 of sample b (no temporal term); its output goes to hdr_prev[b]."""

@@ -79,6 +79,20 @@ def test_clock_summary_short_region_takes_the_next_samples():
     assert out["reasons"] == ["hw_slowdown"]
 
 
+def test_clock_summary_reads_the_tail_of_the_same_load():
+    """A short timed region is followed by a tail of the same steps: the
+    samples of both count, later ones do not."""
+    cs = bench.ClockSampler(0)
+    cs.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout: 0})()
+    cs.t_start, cs.t_end, cs.t_tail_end = 10.0, 10.004, 10.5
+    cs.lines = [(9.9, _line(900, 2070)), (10.05, _line(2070, 2070)),
+                (10.3, _line(2055, 2070)), (10.49, _line(2070, 2070)),
+                (11.0, _line(600, 2070, hwt="Active"))]
+    out = cs.stop()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["reasons"] == []
+    assert out["window_s"] == pytest.approx(0.5)
+
+
 def test_clock_summary_without_nvidia_smi():
     cs = bench.ClockSampler(0)
     out = cs.stop()

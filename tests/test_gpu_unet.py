@@ -87,6 +87,78 @@ def test_conv3x3_forward_parity(spp, cin, cout, B, H, W):
     assert np.all(np.abs(got - exact) <= 2.0 ** -8 * np.abs(exact) + acc + 1e-30)
 
 
+def _tr(n):
+    """Rows per tile of the persistent convolution for an output width n."""
+    return 4 if n <= 64 else 2 if n <= 128 else 1
+
+
+def _multitile_shape(n, min_per_cta=3.2):
+    """(B, H, W) for which the persistent convolution (grid = one CTA per
+    SM, tiles of TR rows x 128 pixels) gives every CTA at least three tiles:
+    W = 200 (a full and a ragged 72-pixel tile per row), B = 2, H a ragged
+    multiple of TR."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    tr = _tr(n)
+    rows = int(np.ceil(min_per_cta * sms / (2 * 2)))  # tile rows per image
+    H = rows * tr - (1 if tr > 1 else 0)
+    return 2, H, 200
+
+
+def _resident(n, k):
+    """Whether the packed weights of a layer (k input channels of the GEMM,
+    n output channels) stay in shared memory (80 KB or less)."""
+    return 18 * n * ((k + 15) // 16 * 16) <= 80 * 1024
+
+
+# every N template of the kernel with its weights resident and streamed
+MULTITILE = [(32, 16), (288, 16), (32, 32), (160, 32), (64, 64), (96, 64), (32, 96), (64, 96),
+             (32, 128), (128, 128), (16, 192), (64, 192)]
+
+
+def test_multitile_cases_cover_both_weight_modes():
+    modes = {}
+    for cin, cout in MULTITILE:
+        modes.setdefault(cout, set()).add(_resident(cout, cin))
+    assert sorted(modes) == [16, 32, 64, 96, 128, 192]
+    assert all(m == {True, False} for m in modes.values()), modes
+
+
+@pytest.mark.parametrize("cin,cout", MULTITILE)
+def test_conv3x3_forward_parity_multitile(spp, cin, cout):
+    """The one-ulp criterion of test_conv3x3_forward_parity where every CTA
+    of the persistent kernel runs three or more tiles: both TMEM
+    accumulator buffers, the accumulator hand-back and the stage reuse
+    across tiles are exercised."""
+    B, H, W = _multitile_shape(cout)
+    test_conv3x3_forward_parity(spp, cin, cout, B, H, W)
+
+
+def test_conv3x3_forward_parity_1080p_slice(spp):
+    """A 16-row slice of a 1080p layer (15 full 128-pixel tiles per row)."""
+    test_conv3x3_forward_parity(spp, 96, 32, 1, 16, 1920)
+
+
+# data gradient: the output width of the call is cin (every N template, both
+# weight modes, masked and not)
+MULTITILE_DGRAD = [(16, 32, False), (16, 304, True), (32, 32, True), (32, 160, False),
+                   (64, 64, False), (64, 192, True), (96, 32, True), (96, 64, False),
+                   (128, 32, False), (128, 128, True), (192, 16, True), (192, 64, False)]
+
+
+def test_multitile_dgrad_cases_cover_both_weight_modes():
+    modes = {}
+    for cin, cout, _ in MULTITILE_DGRAD:
+        modes.setdefault(cin, set()).add(_resident(cin, cout))
+    assert sorted(modes) == [16, 32, 64, 96, 128, 192]
+    assert all(m == {True, False} for m in modes.values()), modes
+
+
+@pytest.mark.parametrize("cin,cout,masked", MULTITILE_DGRAD)
+def test_conv3x3_backward_data_parity_multitile(spp, cin, cout, masked):
+    B, H, W = _multitile_shape(cin)
+    test_conv3x3_backward_data_parity(spp, cin, cout, B, H, W, masked)
+
+
 @pytest.mark.parametrize("cin,cout,B,H,W", [(32, 32, 2, 5, 140), (64, 128, 1, 4, 128),
                                             (192, 64, 1, 3, 200), (96, 32, 1, 4, 64),
                                             (32, 64, 1, 6, 33), (128, 25 + 7, 1, 4, 96)])
@@ -199,12 +271,14 @@ def _predict(spp, theta, x, B, W, H, return_ws=False):
     return (res, ws) if return_ws else res
 
 
-def test_predict_layerwise_parity(spp):
+@pytest.mark.parametrize("B,W,H", [(2, 48, 32), (10, 640, 256)])
+def test_predict_layerwise_parity(spp, B, W, H):
     """Each layer of the network, fed the GPU's own BF16 inputs (read back
     from the workspace), against the oracle layer with the same rounding:
     covers the fused pooling, upsample + concatenation, FP32 input and FP32
-    planar head paths of the convolution."""
-    B, W, H = 2, 48, 32
+    planar head paths of the convolution.  At 10 x 640 x 256 every layer,
+    the level-2 head included, has more than twice as many tiles as a GB300
+    has SMs, so every CTA of the persistent kernel runs several tiles."""
     theta = _theta(weight_noise=0.05)
     x = _features(B, W, H, seed=30)
     (d, l0, l1, l2), ws = _predict(spp, theta, x, B, W, H, return_ws=True)

@@ -73,6 +73,27 @@ def test_conv3x3_backward_weights_parity(spp, cin, cout, B, H, W):
     assert np.all(np.abs(got_b - ref_b) <= tol * abs_b + 1e-30)
 
 
+def _wgrad_multistage_shape(cin, min_chunks_per_cta=12):
+    """(B, H, W) for which every CTA of the weight gradient (grid: M tiles of
+    128 rows x pixel splits, one split per SM / M tiles) runs at least
+    min_chunks_per_cta K chunks of 64 pixels, so that its 4 stages are
+    reused three times over: W = 200 (three full chunks and a ragged one per
+    row)."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cin_pad = (cin + 15) // 16 * 16
+    mtiles = (9 * cin_pad + 127) // 128
+    splits = max(1, sms // mtiles)
+    H = int(np.ceil(min_chunks_per_cta * splits / 4))
+    return 1, H, 200
+
+
+@pytest.mark.parametrize("cin,cout", [(32, 32), (96, 32), (64, 128), (192, 64), (128, 128),
+                                      (16, 64)])
+def test_conv3x3_backward_weights_parity_multistage(spp, cin, cout):
+    B, H, W = _wgrad_multistage_shape(cin)
+    test_conv3x3_backward_weights_parity(spp, cin, cout, B, H, W)
+
+
 def test_adamw_parity(spp):
     rng = np.random.default_rng(3)
     n = 100_003
