@@ -43,7 +43,10 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
            "-ffp-contract=off", "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP over pixels / rows when the compiler has it (results do not
+    # depend on the thread count); one thread otherwise
+    if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -63,6 +66,8 @@ def _load():
             return _lib
         lib = ctypes.CDLL(build())
         sig = {
+            "orc_set_threads": (None, [_I]),
+            "orc_get_threads": (_I, []),
             "orc_splitmix64_mix": (_U64, [_U64]),
             "orc_splitmix64_next": (_U64, [_P]),
             "orc_pixel_bits": (_U64, [_U64, _U32, _U64]),
@@ -98,6 +103,15 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (n <= 0: all cores)."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def _ptr(a: np.ndarray | None):

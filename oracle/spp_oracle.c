@@ -34,6 +34,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_ERR_ARG -1
@@ -45,6 +48,25 @@
 /* output mix.                                                               */
 /* ------------------------------------------------------------------------ */
 static const uint64_t ORC_GOLDEN_GAMMA = 0x9E3779B97F4A7C15ULL;
+
+/* Threads of the parallel loops (OpenMP over pixels or rows; every pixel is
+ * computed alone, so the results do not depend on the count).  n <= 0
+ * restores the default; without OpenMP everything runs on one thread. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 uint64_t orc_splitmix64_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -224,7 +246,7 @@ int orc_alloc(const float *d, int64_t N, double B, double phi, double lambda, in
     int rc = orc_budget_coeffs(d, N, B, phi, &S, &a, &c);
     if (rc != ORC_OK) return rc;
     if (coeffs_out) { coeffs_out[0] = S; coeffs_out[1] = a; coeffs_out[2] = c; }
-    int64_t run = 0;
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         double m = c * (double)d[i];
         double s = a + m;
@@ -235,8 +257,11 @@ int orc_alloc(const float *d, int64_t N, double B, double phi, double lambda, in
         counts[i] = n;
         w_out[i] = w;
         if (extra_out) extra_out[i] = extra;
+    }
+    int64_t run = 0;
+    for (int64_t i = 0; i < N; ++i) {
         offsets[i] = run;
-        run += n;
+        run += counts[i];
     }
     offsets[N] = run;
     return ORC_OK;
@@ -298,6 +323,7 @@ double orc_sample_noise(uint64_t seed, uint32_t frame, uint64_t i, uint64_t k) {
 /* rgb: [T][3]; clean: planar [3][N]. */
 void orc_render(const double *clean, const int64_t *offsets, int64_t N,
                 uint64_t seed, uint32_t frame, double *rgb) {
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         for (int64_t t = offsets[i]; t < offsets[i + 1]; ++t) {
             double z = orc_sample_noise(seed, frame, (uint64_t)i, (uint64_t)(t - offsets[i]));
@@ -317,6 +343,7 @@ int orc_splat(const int64_t *offsets, const double *rgb, const double *s, const 
     if (W < 0 || H < 0 || L < 1) return ORC_ERR_ARG;
     int64_t N = (int64_t)W * H;
     double *L0 = layers[0];
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         int64_t n = offsets[i + 1] - offsets[i];
         int64_t f = n - extra[i];
@@ -331,6 +358,7 @@ int orc_splat(const int64_t *offsets, const double *rgb, const double *s, const 
         int Wl = W >> l, Hl = H >> l, b = 1 << l;
         int64_t Nl = (int64_t)Wl * Hl;
         double inv = 1.0 / (double)((int64_t)b * b);
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int ch = 0; ch < 3; ++ch)
             for (int y = 0; y < Hl; ++y)
                 for (int x = 0; x < Wl; ++x) {
@@ -376,6 +404,7 @@ static void orc_warp_at(const double *prev, const float *mv, int W, int H, int x
 /* The warped previous frame W_t L_{t-1} over the whole image. */
 void orc_warp(const double *prev, const float *mv, int W, int H, double *out) {
     int64_t N = (int64_t)W * H;
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
             double v[3];
@@ -405,6 +434,7 @@ int orc_reconstruct_level(const double *noisy, const double *logits, int C,
     int64_t Nl = (int64_t)Wl * Hl;
     int Wc = Wl / 2, Hc = Hl / 2;
     int64_t Nc = (int64_t)Wc * Hc;
+    #pragma omp parallel for schedule(static)
     for (int y = 0; y < Hl; ++y)
         for (int x = 0; x < Wl; ++x) {
             int64_t idx = (int64_t)y * Wl + x;
@@ -474,6 +504,7 @@ double orc_srgb_encode(double v) {
 
 void orc_tonemap(const double *hdr, int64_t N, double alpha, double beta, double kexp,
                  double s, double h, double *ldr) {
+    #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < N; ++i) {
         double lg[3];
         for (int ch = 0; ch < 3; ++ch) {

@@ -413,9 +413,9 @@ def test_demodulated_frame_backward_parity(spp, W, H, temporal):
           [ratio(host(g_lg[l]), r_lg[l], 1e-4, 1e-5) for l in range(L)],
           "c", ratio(host(g_c), r_c, 1e-4, 1e-5))
     for l in range(L):
-        assert_grad(host(g_lg[l]), r_lg[l], f"logits {l}", rtol=3e-4, afrac=3e-5)
+        assert_grad(host(g_lg[l]), r_lg[l], f"logits {l}", rtol=1e-4, afrac=1e-5)
     assert_grad(host(g_L0), r_L0, "L0", rtol=1e-4, afrac=1e-5)
-    assert_grad(host(g_c), r_c, "c", rtol=3e-4, afrac=3e-5)
+    assert_grad(host(g_c), r_c, "c", rtol=1e-4, afrac=1e-5)
     assert np.all(host(g_c)[0, 0, :4] == 0)
 
 
