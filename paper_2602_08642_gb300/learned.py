@@ -162,17 +162,57 @@ class Predictor:
         return [l0, self.heads[1][b], self.heads[2][b]]
 
 
+REF_SPP = 64  # samples per pixel of the rendered references
+_REF_FRAMES: dict = {}
+
+
+def render_reference(clean: torch.Tensor, seed: int, frame: int = 0,
+                     spp: int = REF_SPP) -> torch.Tensor:
+    """HDR reference of one frame: the mean of `spp` samples per pixel of the
+    renderer stand-in (the paper trains against converged renders of each
+    frame; this is their synthetic counterpart), rendered by the library's
+    own sample map (a uniform density at budget `spp` gives every pixel
+    exactly `spp` samples and no extra one), renderer and splat."""
+    H, W = clean.shape[1:]
+    key = (W, H, spp)
+    if key not in _REF_FRAMES:
+        _REF_FRAMES.clear()  # one reference size at a time keeps memory bounded
+        _REF_FRAMES[key] = (Frame(W, H, 1, max_budget=float(spp), capacity=spp * W * H),
+                            torch.ones(H, W, device="cuda"))
+    fr, ones = _REF_FRAMES[key]
+    fr.alloc(ones, B.make_params(float(spp), uniform_fraction=PHI, seed=seed, frame=frame,
+                                 hard=True))
+    fr.render(clean, seed, frame)
+    fr.splat()
+    return fr.layers[0].clone()
+
+
 class FrameData:
     """Device copies of one training / evaluation sample: two consecutive
-    frames (clean radiance and G-buffer) and the motion of the second."""
+    frames (clean radiance and G-buffer) and the motion of the second.
+    reference() gives the HDR target of either frame: the clean image (the
+    exact expectation of the renderer stand-in) or the 64-spp mean of the
+    stand-in, rendered once per sample and kept."""
 
-    def __init__(self, pair: dict):
+    def __init__(self, pair: dict, seed: int = 0):
         c = lambda a: torch.from_numpy(a).contiguous().cuda()
         self.clean_prev, self.clean = c(pair["clean_prev"]), c(pair["clean"])
         self.gprev = {k: c(v) for k, v in pair["gbuf_prev"].items()}
         self.g = {k: c(v) for k, v in pair["gbuf"].items()}
         self.mv = c(pair["mv"])
         self.H, self.W = self.clean.shape[1:]
+        self.seed = seed
+        self._ref64 = {}
+
+    def reference(self, kind: str = "clean", prev: bool = False) -> torch.Tensor:
+        if kind == "clean":
+            return self.clean_prev if prev else self.clean
+        if kind != "spp64":
+            raise ValueError(f"unknown reference {kind}")
+        if prev not in self._ref64:
+            self._ref64[prev] = render_reference(self.clean_prev if prev else self.clean,
+                                                 seed=0x64000000 + self.seed, frame=int(not prev))
+        return self._ref64[prev]
 
 
 ESTIMATORS = {"relaxed": B.SPP_ESTIMATOR_RELAXED,
@@ -280,15 +320,16 @@ class Renderer:
                                         self.warped[b], self.mask, self.W, self.H, self.tm,
                                         self.hdr[b], self.ldr[b]), "level 0")
 
-    def reference(self, b: int, clean):
-        B.check(B.spp_tonemap_image(clean, self.W, self.H, self.tm, self.ref[b]), "tonemap")
+    def reference(self, b: int, hdr_ref):
+        """The tone-mapped target of sample b from its HDR reference."""
+        B.check(B.spp_tonemap_image(hdr_ref, self.W, self.H, self.tm, self.ref[b]), "tonemap")
 
-    def temporal_references(self, b: int, clean_prev, mv):
+    def temporal_references(self, b: int, hdr_ref_prev, mv):
         """W(I_{t-1}) and W(I_ref,{t-1}) of Eq. loss_temporal: the previous
         tone-mapped output and reference warped to frame t."""
         B.check(B.spp_warp_previous(self.ldr_prev[b], mv, self.W, self.H, self.wldr_prev[b]),
                 "warp")
-        B.check(B.spp_tonemap_image(clean_prev, self.W, self.H, self.tm, self.tmp), "tonemap")
+        B.check(B.spp_tonemap_image(hdr_ref_prev, self.W, self.H, self.tm, self.tmp), "tonemap")
         B.check(B.spp_warp_previous(self.tmp, mv, self.W, self.H, self.wref_prev[b]), "warp")
 
     def backward(self, b: int, d, logits, g_logits, objective: str = "l1"):
@@ -352,13 +393,19 @@ class Trainer:
     loss_combined with the temporal term); random_tmo draws a tone map of
     the training family per step; total_steps enables cosine annealing of
     the learning rate; betas and weight_decay are AdamW's (the paper uses
-    (0.8, 0.985) and 0.02)."""
+    (0.8, 0.985) and 0.02); reference "clean" (the exact expectation of the
+    renderer stand-in) or "spp64" (its 64-spp mean) is the target of the
+    loss."""
 
     def __init__(self, theta: torch.Tensor, batch: int, size: int, budget: float = 0.25,
                  lr: float = 1e-3, weight_decay: float = 1e-4, objective: str = "l1",
                  betas=(0.9, 0.999), random_tmo: bool = False, total_steps: int | None = None,
-                 seed: int = 0, dither_mask=None, estimator: str = "relaxed"):
+                 seed: int = 0, dither_mask=None, estimator: str = "relaxed",
+                 reference: str = "clean"):
         import numpy as np
+        if reference not in ("clean", "spp64"):
+            raise ValueError(f"unknown reference {reference}")
+        self.reference = reference
         self.net = Predictor(theta, batch, size, size, train=True)
         self.rnd = Renderer(batch, size, size, budget, dither_mask, estimator=estimator)
         self.lr, self.wd = lr, weight_decay
@@ -392,9 +439,9 @@ class Trainer:
         for b, s in enumerate(samples):
             logits = net.frame_logits(b, True)
             rnd.current_frame(b, net.density[b], logits, s.clean, seed + b, f_cur)
-            rnd.reference(b, s.clean)
+            rnd.reference(b, s.reference(self.reference))
             if self.objective == "combined":
-                rnd.temporal_references(b, s.clean_prev, s.mv)
+                rnd.temporal_references(b, s.reference(self.reference, prev=True), s.mv)
             gl = [net.g_logits[0][b, :54], net.g_logits[1][b], net.g_logits[2][b],
                   net.g_logits[0][b, 54]]
             rnd.backward(b, net.density[b], logits, gl, self.objective)
