@@ -334,9 +334,10 @@ int spp_reconstruct_frame(const float *const *layers, const float *const *logits
  * end to end (Sec. 4.3, Sec. 5, Sec. 6.3).  Each call maps the gradient of
  * the loss with respect to a step's output to its inputs' gradients.  Unless
  * stated otherwise a gradient output is ACCUMULATED (+=): the caller zeroes
- * it, and several calls may add into one buffer.  Gradients scattered to
- * neighbouring pixels are summed with floating-point atomics, so their last
- * bits may differ from run to run.
+ * it, and several calls may add into one buffer.  Every gradient is summed
+ * in a fixed order (each output element has one writer), so the results are
+ * the same from run to run, except spp_warp_previous_backward's, which
+ * scatters with floating-point atomics.
  */
 
 /* Reconstruction level (Appendix A) given dLoss/d out (grad_out, [3][Hl][Wl]).

@@ -6,11 +6,12 @@
 // sampler output (Sec. 3).
 //
 // The reconstruction backward recomputes each pixel's softmax weights from
-// its logits instead of storing the K x K tap products.  Gradients that
-// scatter to neighbouring pixels (the gather taps, the bilinear warp) are
-// summed in shared memory over the block's tile and halo first and then
-// added to global memory with atomics, so their summation order (and the
-// last bits of those gradients) may vary from run to run.
+// its logits instead of storing the K x K tap products, and takes the
+// transpose of the gathers in gather form (each source pixel sums the
+// contributions of the pixels that read it, in a fixed order): its result
+// is the same from run to run.  The bilinear warp's backward scatters with
+// atomics (a source pixel's readers are not bounded for arbitrary motion),
+// and so may differ in its last bits from run to run.
 #include "recon_common.cuh"
 #include "render_common.cuh"
 
@@ -18,9 +19,52 @@ namespace spp {
 namespace {
 
 constexpr int kBX = 32, kBY = 8, kBH = 2;
-constexpr int kBHX = kBX + 2 * kBH, kBHY = kBY + 2 * kBH;
-constexpr int kCX = kBX / 2 + 1, kCY = kBY / 2 + 1;  // coarse footprint of a tile
+constexpr int kRX = kBX + 2 * kBH, kRY = kBY + 2 * kBH;  // consumer region 36 x 12
+constexpr int kRN = kRX * kRY;                           // 432 consumers
+constexpr int kHalo = kRN - kBX * kBY;                   // 176 of them outside the tile
+constexpr int kFX = kBX / 2 + 1, kFY = kBY / 2 + 1;      // coarse cells the tile's taps read
 
+// Shared memory of the backward of one 32 x 8 tile: per consumer pixel of
+// the tile and its 2-pixel halo the normalised weights of its kernels and
+// dLoss/d out; the tap values the tile's own pixels read.
+template <bool UP, bool TEMP>
+struct BwdSmem {
+    float wd[25][kRN];
+    float wu[UP ? 4 : 1][UP ? kRN : 1];
+    float wt[TEMP ? 25 : 1][TEMP ? kRN : 1];
+    float g[3][kRN];
+    float nz[3][kRN];
+    float wp[TEMP ? 3 : 1][TEMP ? kRN : 1];
+    float cv[UP ? 3 : 1][UP ? kFY * kFX : 1];
+};
+
+// Taps i in [lo, hi] of a consumer at q whose clamped source, clamp(q + i -
+// 2) to [0, n - 1], is p (the transpose of clamp-to-edge along one axis);
+// lo > hi when there is none.
+__device__ __forceinline__ void tap_range(int q, int p, int n, int &lo, int &hi) {
+    if (n == 1) {
+        lo = 0;
+        hi = 4;
+    } else if (p == 0) {
+        lo = 0;
+        hi = min(2 - q, 4);
+    } else if (p == n - 1) {
+        lo = max(n + 1 - q, 0);
+        hi = 4;
+    } else {
+        lo = hi = p - q + 2;
+        if (lo < 0 || lo > 4) hi = lo - 1;
+    }
+}
+
+// Backward of one reconstruction level in gather form: every output
+// gradient element has exactly one writer, which adds its consumers'
+// contributions in a fixed order, so the result does not depend on
+// scheduling.  A block owns a 32 x 8 tile: it computes the softmax weights
+// of the tile's pixels and of the 2-pixel halo around it (the consumers of
+// the tile's sources), dLoss/d logits of the tile's pixels, then for each
+// source pixel of the tile (and for each coarse cell under it) the sum of
+// w_k g over the consumers and taps that read it.
 template <bool UP, bool TEMP>
 __global__ void __launch_bounds__(kBX *kBY)
 recon_backward_kernel(const float *__restrict__ noisy, const float *__restrict__ logits, int C,
@@ -31,179 +75,243 @@ recon_backward_kernel(const float *__restrict__ noisy, const float *__restrict__
                       float *__restrict__ grad_warped) {
     constexpr int kSpatial = 25 + (UP ? 4 : 0);
     constexpr int kNK = kSpatial + (TEMP ? 25 : 0);
-    __shared__ float sN[3][kBHY][kBHX];
-    __shared__ float sW[TEMP ? 3 : 1][TEMP ? kBHY : 1][TEMP ? kBHX : 1];
-    __shared__ float aN[3][kBHY][kBHX];
-    __shared__ float aW[TEMP ? 3 : 1][TEMP ? kBHY : 1][TEMP ? kBHX : 1];
-    __shared__ float aC[UP ? 3 : 1][UP ? kCY : 1][UP ? kCX : 1];
+    extern __shared__ __align__(16) unsigned char bwd_smem_raw[];
+    BwdSmem<UP, TEMP> &sm = *reinterpret_cast<BwdSmem<UP, TEMP> *>(bwd_smem_raw);
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kBX + tx;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
     const int bx0 = blockIdx.x * kBX, by0 = blockIdx.y * kBY;
-    const int x = bx0 + tx, y = by0 + ty;
-    const bool inside = x < Wl && y < Hl;
-    const int xc = min(x, Wl - 1), yc = min(y, Hl - 1);
     const long long Nl = static_cast<long long>(Wl) * Hl;
-    const long long pix = static_cast<long long>(yc) * Wl + xc;
     const int Wc = Wl >> 1, Hc = Hl >> 1;
     const long long Nc = static_cast<long long>(Wc) * Hc;
-    const int cbx = bx0 >> 1, cby = by0 >> 1;  // first coarse cell of the footprint
+    const int cbx = bx0 >> 1, cby = by0 >> 1;  // first coarse cell under the tile
 
-    for (int idx = tid; idx < kBHX * kBHY; idx += kBX * kBY) {
-        const int hx = idx % kBHX, hy = idx / kBHX;
-        const int gx = clampi(bx0 + hx - kBH, 0, Wl - 1), gy = clampi(by0 + hy - kBH, 0, Hl - 1);
+    // tap values of the region (clamp-to-edge)
+    for (int idx = tid; idx < kRN; idx += kBX * kBY) {
+        const int rx = idx % kRX, ry = idx / kRX;
+        const int gx = clampi(bx0 + rx - kBH, 0, Wl - 1), gy = clampi(by0 + ry - kBH, 0, Hl - 1);
         const long long q = static_cast<long long>(gy) * Wl + gx;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            sN[c][hy][hx] = __ldg(noisy + c * Nl + q);
-            aN[c][hy][hx] = 0.0f;
-            if (TEMP) {
-                sW[c][hy][hx] = __ldg(warped + c * Nl + q);
-                aW[c][hy][hx] = 0.0f;
-            }
+            sm.nz[c][idx] = __ldg(noisy + c * Nl + q);
+            if (TEMP) sm.wp[c][idx] = __ldg(warped + c * Nl + q);
         }
     }
     if (UP)
-        for (int idx = tid; idx < kCX * kCY; idx += kBX * kBY)
+        for (int idx = tid; idx < kFX * kFY; idx += kBX * kBY) {
+            const int cx = min(cbx + idx % kFX, Wc - 1), cy = min(cby + idx / kFX, Hc - 1);
+            const long long q = static_cast<long long>(cy) * Wc + cx;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) aC[c][idx / kCX][idx % kCX] = 0.0f;
-    __syncthreads();
-
-    // recompute the joint softmax of this pixel
-    float lg[kNK];
-#pragma unroll
-    for (int k = 0; k < kSpatial; ++k) lg[k] = __ldg(logits + k * Nl + pix);
-    const bool use_t = TEMP && !(mask && mask[pix]);
-    if (TEMP) {
-#pragma unroll
-        for (int k = 0; k < 25; ++k) lg[kSpatial + k] = use_t ? __ldg(logits + (29 + k) * Nl + pix) : 0.0f;
-    }
-    float m = lg[0];
-#pragma unroll
-    for (int k = 1; k < kSpatial; ++k) m = fmaxf(m, lg[k]);
-    if (use_t) {
-#pragma unroll
-        for (int k = kSpatial; k < kNK; ++k) m = fmaxf(m, lg[k]);
-    }
-    float wsum = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kNK; ++k) {
-        const bool on = k < kSpatial || use_t;
-        lg[k] = on ? __expf(lg[k] - m) : 0.0f;  // lg now holds the unnormalised weights
-        wsum += lg[k];
-    }
-    const float inv = 1.0f / wsum;
-    const float g0 = inside ? __ldg(g + pix) : 0.0f;
-    const float g1 = inside ? __ldg(g + Nl + pix) : 0.0f;
-    const float g2 = inside ? __ldg(g + 2 * Nl + pix) : 0.0f;
-
-    // tap values and q_k = sum_c g_c v_kc
-    float q[kNK];
-    float cvv[UP ? 12 : 1];
-    int cidx[UP ? 4 : 1];
-#pragma unroll
-    for (int j = 0; j < 5; ++j)
-#pragma unroll
-        for (int i = 0; i < 5; ++i)
-            q[j * 5 + i] = g0 * sN[0][ty + j][tx + i] + g1 * sN[1][ty + j][tx + i] +
-                           g2 * sN[2][ty + j][tx + i];
-    if (UP) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int cx = min((xc + i) >> 1, Wc - 1), cy = min((yc + j) >> 1, Hc - 1);
-                const long long qq = static_cast<long long>(cy) * Wc + cx;
-                const int t = 2 * j + i;
-                cidx[t] = (cy - cby) * kCX + (cx - cbx);
-                cvv[3 * t] = __ldg(coarse + qq);
-                cvv[3 * t + 1] = __ldg(coarse + Nc + qq);
-                cvv[3 * t + 2] = __ldg(coarse + 2 * Nc + qq);
-                q[25 + t] = g0 * cvv[3 * t] + g1 * cvv[3 * t + 1] + g2 * cvv[3 * t + 2];
-            }
-    }
-    if (TEMP) {
-#pragma unroll
-        for (int j = 0; j < 5; ++j)
-#pragma unroll
-            for (int i = 0; i < 5; ++i)
-                q[kSpatial + j * 5 + i] = g0 * sW[0][ty + j][tx + i] + g1 * sW[1][ty + j][tx + i] +
-                                          g2 * sW[2][ty + j][tx + i];
-    }
-    float qbar = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kNK; ++k) qbar = fmaf(lg[k] * inv, q[k], qbar);
-
-    if (inside) {
-        // dLoss/dz_k = w_k (q_k - qbar); channels without a kernel get 0
-#pragma unroll
-        for (int k = 0; k < kSpatial; ++k) grad_logits[k * Nl + pix] = lg[k] * inv * (q[k] - qbar);
-        if (TEMP) {
-#pragma unroll
-            for (int k = 0; k < 25; ++k)
-                grad_logits[(29 + k) * Nl + pix] =
-                    use_t ? lg[kSpatial + k] * inv * (q[kSpatial + k] - qbar) : 0.0f;
+            for (int c = 0; c < 3; ++c) sm.cv[c][idx] = __ldg(coarse + c * Nc + q);
         }
-        for (int k = TEMP ? 54 : kSpatial; k < C; ++k) grad_logits[k * Nl + pix] = 0.0f;
-        // dLoss/dv_kc = w_k g_c, summed per source cell in shared memory
+
+    // the normalised weights and dLoss/d out of consumer (qx, qy) into its
+    // region cell; w receives them for the caller
+    auto consumer = [&](int qx, int qy, int cell, float (&w)[kNK], float (&gq)[3], bool &use_t) {
+        const bool in = qx >= 0 && qx < Wl && qy >= 0 && qy < Hl;
+        use_t = false;
+        if (!in) {  // not a pixel: reads nothing, contributes nothing
 #pragma unroll
-        for (int j = 0; j < 5; ++j)
+            for (int k = 0; k < kNK; ++k) w[k] = 0.0f;
+            gq[0] = gq[1] = gq[2] = 0.0f;
+        } else {
+            const long long pix = static_cast<long long>(qy) * Wl + qx;
+            use_t = TEMP && !(mask && mask[pix]);
 #pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                const float w = lg[j * 5 + i] * inv;
-                atomicAdd(&aN[0][ty + j][tx + i], w * g0);
-                atomicAdd(&aN[1][ty + j][tx + i], w * g1);
-                atomicAdd(&aN[2][ty + j][tx + i], w * g2);
+            for (int k = 0; k < kSpatial; ++k) w[k] = __ldg(logits + k * Nl + pix);
+            if (TEMP) {
+#pragma unroll
+                for (int k = 0; k < 25; ++k)
+                    w[kSpatial + k] = use_t ? __ldg(logits + (29 + k) * Nl + pix) : 0.0f;
             }
+            float m = w[0];
+#pragma unroll
+            for (int k = 1; k < kSpatial; ++k) m = fmaxf(m, w[k]);
+            if (use_t) {
+#pragma unroll
+                for (int k = kSpatial; k < kNK; ++k) m = fmaxf(m, w[k]);
+            }
+            float wsum = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kNK; ++k) {
+                const bool on = k < kSpatial || use_t;
+                w[k] = on ? __expf(w[k] - m) : 0.0f;
+                wsum += w[k];
+            }
+            const float inv = 1.0f / wsum;
+#pragma unroll
+            for (int k = 0; k < kNK; ++k) w[k] *= inv;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) gq[c] = __ldg(g + c * Nl + pix);
+        }
+#pragma unroll
+        for (int k = 0; k < 25; ++k) sm.wd[k][cell] = w[k];
         if (UP) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const float w = lg[25 + t] * inv;
-                float *a = &aC[0][0][0];
-                atomicAdd(a + cidx[t], w * g0);
-                atomicAdd(a + kCX * kCY + cidx[t], w * g1);
-                atomicAdd(a + 2 * kCX * kCY + cidx[t], w * g2);
-            }
+            for (int k = 0; k < 4; ++k) sm.wu[k][cell] = w[25 + k];
         }
-        if (use_t) {
+        if (TEMP) {
+#pragma unroll
+            for (int k = 0; k < 25; ++k) sm.wt[k][cell] = w[kSpatial + k];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sm.g[c][cell] = gq[c];
+    };
+    __syncthreads();
+
+    // the tile's own pixel: its weights, then dLoss/d logits
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int px = bx0 + tx, py = by0 + ty;
+    const bool inside = px < Wl && py < Hl;
+    {
+        float w[kNK], gq[3];
+        bool use_t;
+        const int cell = (ty + kBH) * kRX + tx + kBH;
+        consumer(px, py, cell, w, gq, use_t);
+        if (inside) {
+            const long long pix = static_cast<long long>(py) * Wl + px;
+            float q[kNK];
 #pragma unroll
             for (int j = 0; j < 5; ++j)
 #pragma unroll
                 for (int i = 0; i < 5; ++i) {
-                    const float w = lg[kSpatial + j * 5 + i] * inv;
-                    atomicAdd(&aW[0][ty + j][tx + i], w * g0);
-                    atomicAdd(&aW[1][ty + j][tx + i], w * g1);
-                    atomicAdd(&aW[2][ty + j][tx + i], w * g2);
+                    const int o = (ty + j) * kRX + tx + i;
+                    q[j * 5 + i] =
+                        gq[0] * sm.nz[0][o] + gq[1] * sm.nz[1][o] + gq[2] * sm.nz[2][o];
+                    if (TEMP)
+                        q[kSpatial + j * 5 + i] =
+                            gq[0] * sm.wp[0][o] + gq[1] * sm.wp[1][o] + gq[2] * sm.wp[2][o];
                 }
+            if (UP) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const int cx = min((px + i) >> 1, Wc - 1) - cbx;
+                        const int cy = min((py + j) >> 1, Hc - 1) - cby;
+                        const int o = cy * kFX + cx;
+                        q[25 + 2 * j + i] =
+                            gq[0] * sm.cv[0][o] + gq[1] * sm.cv[1][o] + gq[2] * sm.cv[2][o];
+                    }
+            }
+            float qbar = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kNK; ++k) qbar = fmaf(w[k], q[k], qbar);
+            // dLoss/dz_k = w_k (q_k - qbar); channels without a kernel get 0
+#pragma unroll
+            for (int k = 0; k < kSpatial; ++k) grad_logits[k * Nl + pix] = w[k] * (q[k] - qbar);
+            if (TEMP) {
+#pragma unroll
+                for (int k = 0; k < 25; ++k)
+                    grad_logits[(29 + k) * Nl + pix] =
+                        use_t ? w[kSpatial + k] * (q[kSpatial + k] - qbar) : 0.0f;
+            }
+            for (int k = TEMP ? 54 : kSpatial; k < C; ++k) grad_logits[k * Nl + pix] = 0.0f;
         }
+    }
+    // the halo's consumers (rows 0-1 and 10-11, then columns 0-1 and 34-35)
+    if (tid < kHalo) {
+        int rx, ry;
+        if (tid < 2 * kRX) {
+            rx = tid % kRX;
+            ry = tid / kRX;
+        } else if (tid < 4 * kRX) {
+            rx = (tid - 2 * kRX) % kRX;
+            ry = kRY - 2 + (tid - 2 * kRX) / kRX;
+        } else {
+            const int h = tid - 4 * kRX;
+            ry = kBH + h / 4;
+            rx = (h % 4) < 2 ? (h % 4) : kBX + (h % 4);
+        }
+        float w[kNK], gq[3];
+        bool use_t;
+        consumer(bx0 + rx - kBH, by0 + ry - kBH, ry * kRX + rx, w, gq, use_t);
     }
     __syncthreads();
-    // halo cells beyond the image hold the clamped pixels' contributions:
-    // adding them at the clamped coordinate is the clamp-to-edge transpose
-    for (int idx = tid; idx < kBHX * kBHY; idx += kBX * kBY) {
-        const int hx = idx % kBHX, hy = idx / kBHX;
-        const int gx = clampi(bx0 + hx - kBH, 0, Wl - 1), gy = clampi(by0 + hy - kBH, 0, Hl - 1);
-        const long long qq = static_cast<long long>(gy) * Wl + gx;
+
+    // sources of the tile: the sum of w_k g over the taps that read them
+    if (inside && (grad_noisy || (TEMP && grad_warped))) {
+        float an[3] = {0.0f, 0.0f, 0.0f}, aw[3] = {0.0f, 0.0f, 0.0f};
+        // CTA-uniform: every source of the tile is 2 or more pixels from the
+        // border, so each consumer reads it through exactly one tap
+        const bool inner = bx0 >= 2 && bx0 + kBX + 2 <= Wl && by0 >= 2 && by0 + kBY + 2 <= Hl;
+        if (inner) {
+#pragma unroll
+            for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int cell = (ty + kBH + dy) * kRX + tx + kBH + dx;
+                    const int k = (2 - dy) * 5 + (2 - dx);
+                    const float wk = sm.wd[k][cell];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) an[c] = fmaf(wk, sm.g[c][cell], an[c]);
+                    if (TEMP) {
+                        const float wt = sm.wt[k][cell];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) aw[c] = fmaf(wt, sm.g[c][cell], aw[c]);
+                    }
+                }
+        } else {
+            for (int dy = -2; dy <= 2; ++dy) {
+                const int qy = py + dy;
+                if (qy < 0 || qy >= Hl) continue;
+                int jlo, jhi;
+                tap_range(qy, py, Hl, jlo, jhi);
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int qx = px + dx;
+                    if (qx < 0 || qx >= Wl) continue;
+                    int ilo, ihi;
+                    tap_range(qx, px, Wl, ilo, ihi);
+                    const int cell = (ty + kBH + dy) * kRX + tx + kBH + dx;
+                    for (int j = jlo; j <= jhi; ++j)
+                        for (int i = ilo; i <= ihi; ++i) {
+                            const float wk = sm.wd[j * 5 + i][cell];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) an[c] = fmaf(wk, sm.g[c][cell], an[c]);
+                            if (TEMP) {
+                                const float wt = sm.wt[j * 5 + i][cell];
+#pragma unroll
+                                for (int c = 0; c < 3; ++c)
+                                    aw[c] = fmaf(wt, sm.g[c][cell], aw[c]);
+                            }
+                        }
+                }
+            }
+        }
+        const long long pix = static_cast<long long>(py) * Wl + px;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float v = aN[c][hy][hx];
-            if (v != 0.0f && grad_noisy) atomicAdd(grad_noisy + c * Nl + qq, v);
-            if (TEMP) {
-                const float vw = aW[c][hy][hx];
-                if (vw != 0.0f && grad_warped) atomicAdd(grad_warped + c * Nl + qq, vw);
-            }
+            if (grad_noisy) grad_noisy[c * Nl + pix] += an[c];
+            if (TEMP && grad_warped) grad_warped[c * Nl + pix] += aw[c];
         }
     }
-    if (UP && grad_coarse)
-        for (int idx = tid; idx < kCX * kCY; idx += kBX * kBY) {
-            const int cx = cbx + idx % kCX, cy = cby + idx / kCX;
-            if (cx >= Wc || cy >= Hc) continue;
-            const long long qq = static_cast<long long>(cy) * Wc + cx;
+    // coarse cells under the tile: the upsampling taps of the full-resolution
+    // pixels 2c - 1 .. 2c + 1 that read them
+    if (UP && grad_coarse && tid < (kBX / 2) * (kBY / 2)) {
+        const int cx = cbx + tid % (kBX / 2), cy = cby + tid / (kBX / 2);
+        if (cx < Wc && cy < Hc) {
+            float ac[3] = {0.0f, 0.0f, 0.0f};
+            for (int qy = 2 * cy - 1; qy <= 2 * cy + 1; ++qy) {
+                if (qy < 0 || qy >= Hl) continue;
+                for (int qx = 2 * cx - 1; qx <= 2 * cx + 1; ++qx) {
+                    if (qx < 0 || qx >= Wl) continue;
+                    const int cell = (qy - by0 + kBH) * kRX + qx - bx0 + kBH;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float v = aC[c][idx / kCX][idx % kCX];
-                if (v != 0.0f) atomicAdd(grad_coarse + c * Nc + qq, v);
+                    for (int j = 0; j < 2; ++j)
+#pragma unroll
+                        for (int i = 0; i < 2; ++i) {
+                            if (min((qx + i) >> 1, Wc - 1) != cx || min((qy + j) >> 1, Hc - 1) != cy)
+                                continue;
+                            const float wk = sm.wu[2 * j + i][cell];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) ac[c] = fmaf(wk, sm.g[c][cell], ac[c]);
+                        }
+                }
             }
+            const long long q = static_cast<long long>(cy) * Wc + cx;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) grad_coarse[c * Nc + q] += ac[c];
         }
+    }
 }
 
 // W_t backward: each pixel's bilinear weights scatter its gradient to the
@@ -487,10 +595,14 @@ splat_backward_dasr_kernel(const int32_t *__restrict__ counts, const float *__re
     grad_s[i] = acc;
 }
 
-// Density backward, pass 1: sum d and sum d g (FP64 accumulation).
+// Density backward, pass 1: per block, sum d and sum d g (FP64), written to
+// the block's own slot; pass 1b adds the slots in index order.  No atomics:
+// the sums, and the gradient, are the same from run to run.
+constexpr int kDensityMaxBlocks = 2048;
+
 __global__ void __launch_bounds__(256)
 density_reduce_kernel(const float *__restrict__ d, const float *__restrict__ g, long long N,
-                      double *__restrict__ sums) {
+                      double *__restrict__ partial) {
     double a = 0.0, b = 0.0;
     for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < N;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -515,8 +627,37 @@ density_reduce_kernel(const float *__restrict__ d, const float *__restrict__ g, 
             ta += pa[w];
             tb += pb[w];
         }
-        atomicAdd(sums, ta);
-        atomicAdd(sums + 1, tb);
+        partial[2 * blockIdx.x] = ta;
+        partial[2 * blockIdx.x + 1] = tb;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+density_sum_kernel(const double *__restrict__ partial, int blocks, double *__restrict__ sums) {
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < blocks; k += blockDim.x) {
+        a += partial[2 * k];
+        b += partial[2 * k + 1];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    __shared__ double pa[8], pb[8];
+    if ((threadIdx.x & 31) == 0) {
+        pa[threadIdx.x >> 5] = a;
+        pb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            ta += pa[w];
+            tb += pb[w];
+        }
+        sums[0] = ta;
+        sums[1] = tb;
     }
 }
 
@@ -546,6 +687,27 @@ ToneArgs tone_args_bwd(const spp_tonemap *tm) {
     return t;
 }
 
+template <bool UP, bool TEMP>
+int launch_recon_backward(dim3 grid, dim3 block, cudaStream_t stream, const float *noisy,
+                          const float *logits, int C, const float *coarse, const float *warped,
+                          const uint8_t *mask, int Wl, int Hl, const float *g, float *grad_logits,
+                          float *grad_noisy, float *grad_coarse, float *grad_warped) {
+    constexpr int kSmem = static_cast<int>(sizeof(BwdSmem<UP, TEMP>));
+    static int configured_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPP_ERR_CUDA;
+    if (configured_dev != dev) {
+        if (cudaFuncSetAttribute(recon_backward_kernel<UP, TEMP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem) != cudaSuccess)
+            return SPP_ERR_CUDA;
+        configured_dev = dev;
+    }
+    recon_backward_kernel<UP, TEMP><<<grid, block, kSmem, stream>>>(
+        noisy, logits, C, coarse, warped, mask, Wl, Hl, g, grad_logits, grad_noisy, grad_coarse,
+        grad_warped);
+    return SPP_OK;
+}
+
 }  // namespace
 }  // namespace spp
 
@@ -571,20 +733,21 @@ int spp_reconstruct_level_backward(const float *noisy, const float *logits, int 
     if (static_cast<long long>(Wl) * Hl == 0) return SPP_OK;
     dim3 block(kBX, kBY);
     dim3 grid((Wl + kBX - 1) / kBX, (Hl + kBY - 1) / kBY);
+    int rc;
     if (!coarse)
-        recon_backward_kernel<false, false><<<grid, block, 0, stream>>>(
-            noisy, logits, C, coarse, warped_prev, mask, Wl, Hl, grad_out, grad_logits, grad_noisy,
-            grad_coarse, grad_warped);
+        rc = launch_recon_backward<false, false>(grid, block, stream, noisy, logits, C, coarse,
+                                                 warped_prev, mask, Wl, Hl, grad_out, grad_logits,
+                                                 grad_noisy, grad_coarse, grad_warped);
     else if (!warped_prev)
-        recon_backward_kernel<true, false><<<grid, block, 0, stream>>>(
-            noisy, logits, C, coarse, warped_prev, mask, Wl, Hl, grad_out, grad_logits, grad_noisy,
-            grad_coarse, grad_warped);
+        rc = launch_recon_backward<true, false>(grid, block, stream, noisy, logits, C, coarse,
+                                                warped_prev, mask, Wl, Hl, grad_out, grad_logits,
+                                                grad_noisy, grad_coarse, grad_warped);
     else
-        recon_backward_kernel<true, true><<<grid, block, 0, stream>>>(
-            noisy, logits, C, coarse, warped_prev, mask, Wl, Hl, grad_out, grad_logits, grad_noisy,
-            grad_coarse, grad_warped);
+        rc = launch_recon_backward<true, true>(grid, block, stream, noisy, logits, C, coarse,
+                                               warped_prev, mask, Wl, Hl, grad_out, grad_logits,
+                                               grad_noisy, grad_coarse, grad_warped);
     count_launch();
-    return launch_status();
+    return rc != SPP_OK ? rc : launch_status();
 }
 
 int spp_warp_previous_backward(const float *mv, int W, int H, const float *grad_warped,
@@ -745,7 +908,9 @@ int spp_splat_backward_estimator(const int32_t *offsets, const int32_t *counts, 
     return launch_status();
 }
 
-size_t spp_density_backward_workspace_bytes(void) { return 256; }
+size_t spp_density_backward_workspace_bytes(void) {
+    return 256 + static_cast<size_t>(spp::kDensityMaxBlocks) * 2 * sizeof(double);
+}
 
 int spp_density_backward(const float *d, int64_t N, double budget, double uniform_fraction,
                          const float *grad_s, float *grad_z, void *ws, size_t ws_bytes,
@@ -756,16 +921,19 @@ int spp_density_backward(const float *d, int64_t N, double budget, double unifor
     if (!aligned16(d) || !aligned16(grad_s) || !aligned16(grad_z) || !aligned16(ws))
         return SPP_ERR_ALIGN;
     if (N == 0) return SPP_OK;
-    if (cudaMemsetAsync(ws, 0, 2 * sizeof(double), stream) != cudaSuccess) return SPP_ERR_CUDA;
     double *sums = static_cast<double *>(ws);
+    double *partial = reinterpret_cast<double *>(static_cast<unsigned char *>(ws) + 256);
     long long blocks = (N + 255) / 256;
-    const long long cap = static_cast<long long>(sm_count()) * 8;
-    density_reduce_kernel<<<static_cast<unsigned>(blocks < cap ? blocks : cap), 256, 0, stream>>>(
-        d, grad_s, N, sums);
+    long long rblocks = static_cast<long long>(sm_count()) * 8;
+    if (rblocks > blocks) rblocks = blocks;
+    if (rblocks > kDensityMaxBlocks) rblocks = kDensityMaxBlocks;
+    density_reduce_kernel<<<static_cast<unsigned>(rblocks), 256, 0, stream>>>(d, grad_s, N,
+                                                                           partial);
+    density_sum_kernel<<<1, 256, 0, stream>>>(partial, static_cast<int>(rblocks), sums);
     const double K = (1.0 - uniform_fraction) * budget * static_cast<double>(N);
     density_grad_kernel<<<static_cast<unsigned>(blocks), 256, 0, stream>>>(d, grad_s, N, sums, K,
                                                                            grad_z);
-    count_launch(2);
+    count_launch(3);
     return launch_status();
 }
 

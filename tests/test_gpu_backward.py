@@ -69,9 +69,14 @@ def _level_inputs(W, H, variant, seed):
     return noisy, logits, coarse, warped, mask, g
 
 
-@pytest.mark.parametrize("W,H", [(64, 48), (100, 36), (1920, 1080)])
+@pytest.mark.parametrize("W,H", [(64, 48), (100, 36), (1920, 1080), (2, 2), (6, 4), (36, 10),
+                                 (4, 130)])
 @pytest.mark.parametrize("variant", ["coarsest", "mid", "full", "full_masked"])
 def test_reconstruct_level_backward_parity(spp, W, H, variant):
+    """Frames of every size class: several tiles of 32 x 8 with ragged
+    edges, tiny frames whose clamp-to-edge folds many taps onto one
+    border pixel (width or height 2), a tile exactly one consumer halo
+    wider than the frame."""
     noisy, logits, coarse, warped, mask, g = _level_inputs(W, H, variant, W + H)
     C = logits.shape[0]
     gl = torch.empty((C, H, W), device="cuda")
@@ -91,6 +96,31 @@ def test_reconstruct_level_backward_parity(spp, W, H, variant):
         assert_grad(host(gc), rc, "grad coarse")
     if warped is not None:
         assert_grad(host(gw), rw, "grad warped")
+
+
+def test_reconstruct_level_backward_coarsest_1x1(spp):
+    """A 1 x 1 level: every tap clamps to the one pixel."""
+    test_reconstruct_level_backward_parity(spp, 1, 1, "coarsest")
+    test_reconstruct_level_backward_parity(spp, 3, 1, "coarsest")
+
+
+def test_reconstruct_level_backward_is_deterministic(spp):
+    """Each gradient element has one writer summing in a fixed order: two
+    calls give the same bits."""
+    W, H = 640, 360
+    noisy, logits, coarse, warped, mask, g = _level_inputs(W, H, "full_masked", 7)
+    outs = []
+    for _ in range(2):
+        gl = torch.empty((54, H, W), device="cuda")
+        gn = torch.zeros((3, H, W), device="cuda")
+        gc = torch.zeros((3, H // 2, W // 2), device="cuda")
+        gw = torch.zeros((3, H, W), device="cuda")
+        spp.check(spp.binding.spp_reconstruct_level_backward(
+            dev(noisy), dev(logits), 54, dev(coarse), dev(warped), dev(mask), W, H, dev(g), gl,
+            gn, gc, gw))
+        outs.append((gl, gn, gc, gw))
+    for a, b in zip(*outs):
+        assert torch.equal(a, b)
 
 
 def test_warp_backward_parity(spp):
@@ -178,9 +208,18 @@ def test_density_backward_parity(spp):
     d = np.exp(z - z.max()).astype(np.float32)
     g = rng.standard_normal(N).astype(np.float32)
     gz = torch.empty(N, device="cuda")
-    ws = torch.empty(256, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(spp.binding.spp_density_backward_workspace_bytes(), dtype=torch.uint8,
+                     device="cuda")
     spp.check(spp.binding.spp_density_backward(dev(d), N, 0.25, 0.125, dev(g), gz, ws))
     assert_grad(host(gz), oracle.density_backward(z, g, 0.25), "grad z")
+    # the sums are taken in a fixed order: a second call gives the same bits
+    gz2 = torch.empty(N, device="cuda")
+    spp.check(spp.binding.spp_density_backward(dev(d), N, 0.25, 0.125, dev(g), gz2, ws))
+    assert torch.equal(gz, gz2)
+    # a workspace below the stated size is refused
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    assert spp.binding.spp_density_backward(dev(d), N, 0.25, 0.125, dev(g), gz, small) == \
+        spp.binding.SPP_ERR_WORKSPACE
 
 
 def test_autograd_chain_matches_oracle_chain(spp):

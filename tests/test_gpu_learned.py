@@ -83,3 +83,23 @@ def test_full_objective_training(spp):
     # than the L1-trained network, a much smaller temporal error
     assert learned > plain + 0.25
     assert np.mean(t_learned) < 0.5 * np.mean(t_plain)
+
+
+def test_training_is_bitwise_reproducible(spp):
+    """Two short trainings from the same start and seeds end with the same
+    parameters bit for bit: every gradient of the step (the reconstruction
+    backward in gather form, the density backward's fixed-order sums, the
+    weight gradients' fixed-order split reduction) is summed in a fixed
+    order."""
+    from paper_2602_08642_gb300 import learned as Lm
+    size = 64
+    train = [Lm.FrameData(inp.training_pair(size, seed=300 + i)) for i in range(8)]
+    theta = torch.from_numpy(inp.unet_params(U.LAYERS, seed=5, head_bias=inp.fixed_head_bias()))
+    finals = []
+    for _ in range(2):
+        tr = Lm.Trainer(theta, 4, size, 0.25, lr=1e-3, objective="combined")
+        for k in range(6):
+            tr.step([train[(4 * k + b) % 8] for b in range(4)], seed=1000 + 17 * k)
+        torch.cuda.synchronize()
+        finals.append(tr.net.theta.clone())
+    assert torch.equal(finals[0], finals[1])

@@ -538,3 +538,24 @@ def test_tonemap_gray_and_saturation(orc):
     a = orc.tonemap(hdr * math.exp(0.7), 1.0, 1.0, 0.0, 0.5, 0.5)
     b = orc.tonemap(hdr, 1.0, 1.0, 0.7, 0.5, 0.5)
     assert np.allclose(a, b, rtol=1e-12)
+
+
+def test_oracle_results_do_not_depend_on_the_thread_count(orc):
+    """The C oracle's parallel loops compute every pixel alone: one thread
+    and several give the same bits."""
+    import spp_inputs as inp
+    W, H, L = 96, 64, 3
+    x = inp.frame_inputs(W, H, L, frame=1, temporal=True)
+    lg = [a.astype(np.float64) for a in x["logits"]]
+    prev = np.random.default_rng(2).random((3, H, W))
+    out = []
+    for n in (1, 4):
+        orc.set_threads(n)
+        r = orc.frame(x["d"], x["clean"], lg, W, H, L, 0.5, prev=prev, mv=x["mv"],
+                         mask=x["mask"], frame_index=1)
+        out.append(r)
+    orc.set_threads(0)
+    assert np.array_equal(out[0]["alloc"].counts, out[1]["alloc"].counts)
+    assert np.array_equal(out[0]["rgb"], out[1]["rgb"])
+    assert np.array_equal(out[0]["hdr"], out[1]["hdr"])
+    assert np.array_equal(out[0]["ldr"], out[1]["ldr"])
