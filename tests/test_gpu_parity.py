@@ -96,6 +96,78 @@ def test_alloc_bit_exact(spp, W, H, B, hard):
     check_alloc(fr, oracle_alloc(d, params), f"{W}x{H} B={B}")
 
 
+def test_alloc_bit_exact_4k(spp):
+    """The 4K frame: many pixels per CTA of the one-launch sample map."""
+    W, H = 3840, 2160
+    d = inp.density_lognormal(W, H, seed=44)
+    params = spp.make_params(0.125, seed=0x5EED, frame=9)
+    fr = run_alloc(spp, d, W, H, params)
+    assert fr.check_status() == 0
+    check_alloc(fr, oracle_alloc(d, params), "4K")
+
+
+def test_alloc_workspace_in_any_prior_state(spp):
+    """The sample map clears what it needs: a workspace filled with random
+    bytes, then reused call after call (with different frame sizes), gives
+    the oracle's map every time."""
+    fr = spp.Frame(1920, 1080, 1, max_budget=0.5)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    fr.alloc_ws.copy_(torch.randint(0, 256, fr.alloc_ws.shape, generator=g, device="cuda",
+                                    dtype=torch.int32).to(torch.uint8))
+    for k, (W, H) in enumerate([(1920, 1080), (300, 200), (1920, 1080), (64, 64)]):
+        d = inp.density_lognormal(W, H, seed=90 + k)
+        params = spp.make_params(0.5, frame=k)
+        small = spp.Frame(W, H, 1, max_budget=0.5)
+        small.alloc_ws = fr.alloc_ws  # one workspace for every call
+        small.clear_status()
+        small.alloc(dev(d), params)
+        torch.cuda.synchronize()
+        assert small.check_status() == 0
+        check_alloc(small, oracle_alloc(d, params), f"reused workspace, call {k}")
+
+
+def test_alloc_without_count_map(spp):
+    """counts = NULL: the offsets and the sample list come from the same
+    decisions taken again."""
+    W, H = 1000, 700
+    d = inp.density_lognormal(W, H, seed=12)
+    params = spp.make_params(0.6, frame=2)
+    ref = run_alloc(spp, d, W, H, params)
+    fr = spp.Frame(W, H, 1, max_budget=0.6)
+    fr.clear_status()
+    spp.check(spp.spp_alloc_sample_map(dev(d), W, H, params, None, fr.offsets, fr.sample_pixel,
+                                       fr.capacity, fr.s, fr.holdout_w, fr.total, fr.status,
+                                       fr.alloc_ws))
+    torch.cuda.synchronize()
+    assert fr.check_status() == 0
+    T = ref.sample_count()
+    assert fr.sample_count() == T
+    assert torch.equal(fr.offsets, ref.offsets)
+    assert torch.equal(fr.sample_pixel[:T], ref.sample_pixel[:T])
+    assert torch.equal(fr.s, ref.s) and torch.equal(fr.holdout_w, ref.holdout_w)
+
+
+def test_alloc_interleaved_with_systematic_map(spp):
+    """The stochastic and the systematic map share one workspace, call
+    after call, and each stays exact."""
+    import oracle.variants as V
+    W, H = 960, 540
+    fr = spp.Frame(W, H, 1, max_budget=0.5)
+    for k in range(3):
+        d = inp.density_lognormal(W, H, seed=60 + k)
+        params = spp.make_params(0.25, frame=k)
+        fr.clear_status()
+        fr.alloc(dev(d), params)
+        torch.cuda.synchronize()
+        assert fr.check_status() == 0
+        check_alloc(fr, oracle_alloc(d, params), f"stochastic {k}")
+        fr.alloc_systematic(dev(d), params)
+        torch.cuda.synchronize()
+        assert fr.check_status() == 0
+        ref = V.alloc_systematic(d.ravel(), 0.25, seed=params.seed, frame=k)
+        assert np.array_equal(host(fr.counts), ref.counts)
+
+
 def test_alloc_fp64_path_agrees_with_filter(spp):
     W, H = 640, 480
     d = inp.density_lognormal(W, H, seed=5)
