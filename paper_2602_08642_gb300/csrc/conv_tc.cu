@@ -72,7 +72,13 @@ struct Cfg {
     static constexpr int kZeroBytes = (N == 32) ? 4096 : 0;
     static constexpr int kWOff = kZeroOff + kZeroBytes;          // resident weights
     static constexpr int kStagesOff = kWOff + kWRegion;
-    static constexpr int kNS0 = (kSmemBudget - kStagesOff - kEpiBytes) / kStage;
+    // BF16 NHWC outputs leave through a per-warp staging row buffer, so that
+    // each warp store writes contiguous 512-byte runs ([32 px][kCBs ch] with
+    // a 16-byte pad per pixel: conflict-free 16-byte shared accesses)
+    static constexpr int kCBs = N < 32 ? N : 32;
+    static constexpr int kStageRow = 2 * kCBs + 16;
+    static constexpr int kStoreBytes = 4 * 32 * kStageRow;
+    static constexpr int kNS0 = (kSmemBudget - kStagesOff - kEpiBytes - kStoreBytes) / kStage;
     static constexpr int kNS = kNS0 > 8 ? 8 : kNS0;
     // a stage is published kLag stages after its copies were issued; kLag <=
     // kNS - 2 lets the MMAs of one stage run while the next is published
@@ -90,7 +96,8 @@ struct Cfg {
     // FP32 planar outputs leave through two 8 KB staging buffers ([16 ch][128 px])
     // and TMA tensor stores (resident-weight variants; the heads are)
     static constexpr int kEpiOff = (kStagesOff + kNS * kStage + 127) / 128 * 128;
-    static constexpr int kSmem = kEpiOff + kEpiBytes + 128;  // + alignment slack
+    static constexpr int kStoreOff = kEpiOff + kEpiBytes;
+    static constexpr int kSmem = kStoreOff + kStoreBytes + 128;  // + alignment slack
     static_assert(kSmem <= kSmemLimit, "shared memory over the per-CTA limit");
     static_assert(kNS >= 2, "stage does not fit twice");
 };
@@ -468,53 +475,53 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             };
             if (TR % 2 == 0 && a.pool_out) {
                 // ReLU rows in pairs, plus the 2x2 average of their BF16 values
-                // (lanes x and x^1 hold horizontal neighbours); 32 columns of
-                // both rows per TMEM round trip
-                constexpr int kCB = N < 32 ? N : 32;
-#pragma unroll 1
-                for (int r = 0; r < TR; r += 2) {
+                // (lanes x and x^1 hold horizontal neighbours); 16 columns of
+                // both rows per TMEM round trip, the next pair's read in flight
+                // while this one is stored
+                constexpr int kPB = 16;
+                constexpr int kRowBlocks = N / kPB;
+                constexpr int kBlocks = (TR / 2) * kRowBlocks;
+                uint32_t pbuf[2][2][kPB];
+                auto tmem_read2 = [&](int k, uint32_t (&v0)[kPB], uint32_t (&v1)[kPB]) {
+                    const int r = 2 * (k / kRowBlocks), j0 = (k % kRowBlocks) * kPB;
+                    tc::tmem_ld16(abase + r * N + j0, v0);
+                    tc::tmem_ld16(abase + (r + 1) * N + j0, v1);
+                };
+                tmem_read2(0, pbuf[0][0], pbuf[0][1]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int kb = 0; kb < kBlocks; ++kb) {
+                    if (kb + 1 < kBlocks)
+                        tmem_read2(kb + 1, pbuf[(kb + 1) & 1][0], pbuf[(kb + 1) & 1][1]);
+                    const uint32_t (&v0)[kPB] = pbuf[kb & 1][0];
+                    const uint32_t (&v1)[kPB] = pbuf[kb & 1][1];
+                    const int r = 2 * (kb / kRowBlocks), j = (kb % kRowBlocks) * kPB;
                     const int y = y0 + r;
                     const bool in0 = (x < a.W) && (y < a.H), in1 = (x < a.W) && (y + 1 < a.H);
                     const size_t pix0 = (static_cast<size_t>(b) * a.H + y) * a.W + x;
                     const size_t pix1 = pix0 + a.W;
-#pragma unroll 1
-                    for (int j0 = 0; j0 < N; j0 += kCB) {
-                        uint32_t v0[kCB], v1[kCB];
+                    float f0[16], f1[16], sum[16];
 #pragma unroll
-                        for (int q = 0; q < kCB / 16; ++q) {
-                            tc::tmem_ld16(abase + r * N + j0 + 16 * q,
-                                          *reinterpret_cast<uint32_t(*)[16]>(v0 + 16 * q));
-                            tc::tmem_ld16(abase + (r + 1) * N + j0 + 16 * q,
-                                          *reinterpret_cast<uint32_t(*)[16]>(v1 + 16 * q));
-                        }
-                        tc::tmem_wait_ld();
-#pragma unroll
-                        for (int q = 0; q < kCB / 16; ++q) {
-                            const int j = j0 + 16 * q;
-                            float f0[16], f1[16], sum[16];
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const float bb = sbias[j + e];
-                                f0[e] = __bfloat162float(__float2bfloat16_rn(
-                                    fmaxf(__uint_as_float(v0[16 * q + e]) + bb, 0.f)));
-                                f1[e] = __bfloat162float(__float2bfloat16_rn(
-                                    fmaxf(__uint_as_float(v1[16 * q + e]) + bb, 0.f)));
-                                sum[e] = f0[e] + f1[e];
-                            }
-#pragma unroll
-                            for (int e = 0; e < 16; ++e)
-                                sum[e] += __shfl_xor_sync(0xffffffffu, sum[e], 1);
-                            if (in0) store16(a.out + pix0 * N + j, f0);
-                            if (in1) store16(a.out + pix1 * N + j, f1);
-                            if (in1 && !(lane & 1)) {
-                                const size_t pp = (static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) *
-                                                      (a.W >> 1) + (x >> 1);
-#pragma unroll
-                                for (int e = 0; e < 16; ++e) sum[e] *= 0.25f;
-                                store16(a.pool_out + pp * N + j, sum);
-                            }
-                        }
+                    for (int e = 0; e < 16; ++e) {
+                        const float bb = sbias[j + e];
+                        f0[e] = __bfloat162float(
+                            __float2bfloat16_rn(fmaxf(__uint_as_float(v0[e]) + bb, 0.f)));
+                        f1[e] = __bfloat162float(
+                            __float2bfloat16_rn(fmaxf(__uint_as_float(v1[e]) + bb, 0.f)));
+                        sum[e] = f0[e] + f1[e];
                     }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) sum[e] += __shfl_xor_sync(0xffffffffu, sum[e], 1);
+                    if (in0) store16(a.out + pix0 * N + j, f0);
+                    if (in1) store16(a.out + pix1 * N + j, f1);
+                    if (in1 && !(lane & 1)) {
+                        const size_t pp =
+                            (static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) * (a.W >> 1) + (x >> 1);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) sum[e] *= 0.25f;
+                        store16(a.pool_out + pp * N + j, sum);
+                    }
+                    tc::tmem_wait_ld();
                 }
                 release_acc();
                 continue;
@@ -526,15 +533,22 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 float *ebuf = reinterpret_cast<float *>(base + C::kEpiOff);
                 const int px = warp * 32 + lane;
                 const int x0 = (rr % tiles_x) * kTileX;
-#pragma unroll 1
-                for (int r = 0; r < TR; ++r) {
-                    const int y = y0 + r;
-#pragma unroll 1
-                    for (int j0 = 0; j0 < N; j0 += 16) {
-                        uint32_t v[16];
-                        tc::tmem_ld16(abase + r * N + j0, v);
-                        tc::tmem_wait_ld();
-                        if (j0 >= a.cout) continue;  // padding columns
+                // 16 planes per round, the next round's TMEM read in flight
+                // while this one is staged and stored
+                constexpr int kRowBlocks = N / 16;
+                constexpr int kBlocks = TR * kRowBlocks;
+                uint32_t fbuf[2][16];
+                auto tmem_read16 = [&](int k, uint32_t (&vv)[16]) {
+                    tc::tmem_ld16(abase + (k / kRowBlocks) * N + (k % kRowBlocks) * 16, vv);
+                };
+                tmem_read16(0, fbuf[0]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int kb = 0; kb < kBlocks; ++kb) {
+                    if (kb + 1 < kBlocks) tmem_read16(kb + 1, fbuf[(kb + 1) & 1]);
+                    const uint32_t (&v)[16] = fbuf[kb & 1];
+                    const int y = y0 + kb / kRowBlocks, j0 = (kb % kRowBlocks) * 16;
+                    if (j0 < a.cout) {  // padding columns are not stored
                         float *buf = ebuf + (eblk & 1) * (16 * kTileX);
                         // bias into registers before the barrier, whose memory
                         // clobber would otherwise serialise these reads
@@ -544,49 +558,64 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                         if (tid == 0) tma_store_wait_read<1>();
                         named_bar_epilogue();
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) buf[e * kTileX + px] = __uint_as_float(v[e]) + bb[e];
+                        for (int e = 0; e < 16; ++e)
+                            buf[e * kTileX + px] = __uint_as_float(v[e]) + bb[e];
                         tc::fence_proxy_async();
                         named_bar_epilogue();
                         if (tid == 0 && y < a.H) tma_store_planes(&omap, buf, x0, y, j0, b);
                         ++eblk;
                     }
+                    tc::tmem_wait_ld();
                 }
                 release_acc();
                 continue;
             }
-            // one row at a time, up to 32 columns per TMEM round trip
+            // one row at a time, up to 32 columns per TMEM round trip; the
+            // next block's TMEM read is in flight while this one is stored
+            // (tcgen05.wait::ld waits for every outstanding read, so each
+            // wait covers exactly the one issued before the stores)
             constexpr int kCB = N < 32 ? N : 32;
-#pragma unroll 1
-            for (int r = 0; r < TR; ++r) {
+            constexpr int kRowBlocks = N / kCB;
+            constexpr int kBlocks = TR * kRowBlocks;
+            uint32_t vbuf[2][kCB];
+            auto tmem_read = [&](int k, uint32_t (&vv)[kCB]) {
+                const int r = k / kRowBlocks, j0 = (k % kRowBlocks) * kCB;
+#pragma unroll
+                for (int q = 0; q < kCB / 16; ++q)
+                    tc::tmem_ld16(abase + r * N + j0 + 16 * q,
+                                  *reinterpret_cast<uint32_t(*)[16]>(vv + 16 * q));
+            };
+            tmem_read(0, vbuf[0]);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int kb = 0; kb < kBlocks; ++kb) {
+                if (kb + 1 < kBlocks) tmem_read(kb + 1, vbuf[(kb + 1) & 1]);
+                const uint32_t (&v)[kCB] = vbuf[kb & 1];
+                const int r = kb / kRowBlocks, j0 = (kb % kRowBlocks) * kCB;
                 const int y = y0 + r;
                 const bool inside = (x < a.W) && (y < a.H);
                 const size_t pix = (static_cast<size_t>(b) * a.H + y) * a.W + x;
-#pragma unroll 1
-                for (int j0 = 0; j0 < N; j0 += kCB) {
-                    uint32_t v[kCB];
+                if (a.epi_mode == kEpiF32Planar) {
+                    if (inside) {
+                        const size_t plane = static_cast<size_t>(a.H) * a.W;
+                        float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
+                                   static_cast<size_t>(y) * a.W + x;
 #pragma unroll
-                    for (int q = 0; q < kCB / 16; ++q)
-                        tc::tmem_ld16(abase + r * N + j0 + 16 * q,
-                                      *reinterpret_cast<uint32_t(*)[16]>(v + 16 * q));
-                    tc::tmem_wait_ld();
-                    if (!inside) continue;
+                        for (int e = 0; e < kCB; ++e) {
+                            const int n = j0 + e;
+                            if (n < a.cout) __stcs(o + n * plane, __uint_as_float(v[e]) + sbias[n]);
+                        }
+                    }
+                } else {
+                    // BF16 values of this pixel's kCB channels into the warp's
+                    // staging row
+                    unsigned char *srow = base + C::kStoreOff + (warp * 32) * C::kStageRow;
 #pragma unroll
                     for (int q = 0; q < kCB / 16; ++q) {
                         const int j = j0 + 16 * q;
                         float f[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[16 * q + e]);
-                        if (a.epi_mode == kEpiF32Planar) {
-                            const size_t plane = static_cast<size_t>(a.H) * a.W;
-                            float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
-                                       static_cast<size_t>(y) * a.W + x;
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const int n = j + e;
-                                if (n < a.cout) __stcs(o + n * plane, f[e] + sbias[n]);
-                            }
-                            continue;
-                        }
                         if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
 #pragma unroll
                             for (int e = 0; e < 16; ++e) f[e] += sbias[j + e];
@@ -598,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             const uint4 *m = reinterpret_cast<const uint4 *>(a.act + pix * N + j);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
-                                const uint4 qq = __ldg(m + h);
+                                const uint4 qq = inside ? __ldg(m + h) : make_uint4(0, 0, 0, 0);
                                 const uint32_t *u = &qq.x;
 #pragma unroll
                                 for (int k = 0; k < 4; ++k) {
@@ -608,9 +637,31 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                                 }
                             }
                         }
-                        store16(a.out + pix * N + j, f);
+                        uint4 *d4 = reinterpret_cast<uint4 *>(srow + lane * C::kStageRow + 32 * q);
+                        d4[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                           pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+                        d4[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
+                                           pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
                     }
+                    __syncwarp();
+                    // the warp's 32 pixels x kCB channels as contiguous 16-byte
+                    // chunks: kCB / 8 chunks per pixel, one warp store per 32 chunks
+                    constexpr int kChunks = kCB / 8;
+                    const int xw = x - lane;  // the warp's first pixel
+#pragma unroll
+                    for (int i = 0; i < kChunks; ++i) {
+                        const int pp = i * (32 / kChunks) + lane / kChunks;
+                        const int ch = lane % kChunks;
+                        const uint4 val =
+                            *reinterpret_cast<const uint4 *>(srow + pp * C::kStageRow + 16 * ch);
+                        if (xw + pp < a.W && y < a.H) {
+                            const size_t q = (static_cast<size_t>(b) * a.H + y) * a.W + xw + pp;
+                            *reinterpret_cast<uint4 *>(a.out + q * N + j0 + 8 * ch) = val;
+                        }
+                    }
+                    __syncwarp();  // the staging row is rewritten by the next block
                 }
+                tc::tmem_wait_ld();
             }
             release_acc();
         }
