@@ -69,7 +69,13 @@ struct Cfg {
     static constexpr int kEpiBytes = RES ? 2 * 16 * kTileX * 4 : 0;
     static constexpr int kBiasOff = kHeader;                     // FP32 bias [N]
     static constexpr int kZeroOff = kBiasOff + 1024;             // zero operand (stacked)
-    static constexpr int kZeroBytes = (N == 32) ? 4096 : 0;
+    // N = 32 and 64: the three dy taps of a halo row are one MMA of 3 N columns
+    // whose output spans three neighbouring output rows (below)
+    static constexpr bool kStack = (N == 32 || N == 64);
+    // rows of the zero operand that resets the TR accumulator rows (at least
+    // the 128 rows of the A side), in both 8-channel groups
+    static constexpr int kZeroRows = TR * N > 128 ? TR * N : 128;
+    static constexpr int kZeroBytes = kStack ? 2 * kZeroRows * 16 : 0;
     static constexpr int kWOff = kZeroOff + kZeroBytes;          // resident weights
     static constexpr int kStagesOff = kWOff + kWRegion;
     // BF16 NHWC outputs leave through a per-warp staging row buffer, so that
@@ -83,14 +89,14 @@ struct Cfg {
     // a stage is published kLag stages after its copies were issued; kLag <=
     // kNS - 2 lets the MMAs of one stage run while the next is published
     static constexpr int kLag = kNS - 2;
-    // N = 32: the three dy taps of a halo row are one MMA of N = 96 whose
-    // output spans three neighbouring output rows; each accumulator then holds
-    // TR + 4 row slots (two spare slots at each end); one 0 x 0 MMA with
-    // accumulate off resets the TR real slots at the start of a tile, after
-    // which every MMA accumulates (the spare slots are never read)
-    static constexpr bool kStack = (N == 32);
-    static constexpr int kRowOff = kStack ? 2 : 0;
-    static constexpr int kAccCols = (kStack ? TR + 4 : TR) * N;
+    // Stacked MMAs: halo row h feeds output rows h - 2, h - 1, h (dy = 2, 1,
+    // 0); the first two and the last two halo rows of a tile feed only the
+    // output rows inside the tile, through the matching part of the stacked
+    // weights, so each accumulator holds exactly the TR rows; one 0 x 0 MMA
+    // with accumulate off resets them at the start of a tile, after which
+    // every MMA accumulates
+    static constexpr int kRowOff = 0;
+    static constexpr int kAccCols = TR * N;
     static constexpr int kCols = tc::pow2_cols(2 * kAccCols);
     static_assert(2 * kAccCols <= 512, "accumulators exceed TMEM");
     // FP32 planar outputs leave through two 8 KB staging buffers ([16 ch][128 px])
@@ -386,10 +392,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 tc::tc_fence_after();
                 const uint32_t d0 = tmem + acc * C::kAccCols;
                 if (C::kStack) {
-                    // reset the TR real row slots (the spare slots are never read)
-                    const uint64_t zd =
-                        tc::smem_desc(tc::smem_u32(base + C::kZeroOff), 2048, 128);
-                    tc::mma_bf16(d0 + C::kRowOff * N, zd, zd, tc::idesc_bf16_f32(128, TR * N), 0u);
+                    // reset the TR accumulator rows
+                    const uint64_t zd = tc::smem_desc(tc::smem_u32(base + C::kZeroOff),
+                                                      C::kZeroRows * 16, 128);
+                    tc::mma_bf16(d0, zd, zd, tc::idesc_bf16_f32(128, TR * N), 0u);
                 }
                 for (int c = 0; c < kchunks; ++c, ++it) {
                     const int s = static_cast<int>(it % NS);
@@ -406,17 +412,23 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                         RES ? tc::smem_u32(wres + c * C::kB) : a_base + C::kA;
                     if (C::kStack) {
                         // halo row h feeds output rows h-2, h-1, h through the
-                        // stacked weights [dy = 2; dy = 1; dy = 0] of its dx tap
-                        constexpr uint32_t idesc3 = tc::idesc_bf16_f32(128, 3 * N);
+                        // stacked weights [dy = 2; dy = 1; dy = 0] of its dx tap;
+                        // rows outside the tile are left out (the matching part of
+                        // the stacked weights, fewer MMA columns)
 #pragma unroll
                         for (int dx = 0; dx < 3; ++dx) {
-                            const uint64_t bd =
-                                tc::smem_desc(b_base + dx * 2 * 3 * N * 16, 3 * N * 16, 128);
+                            const uint32_t bdx = b_base + dx * 2 * 3 * N * 16;
 #pragma unroll
                             for (int h = 0; h < TR + 2; ++h) {
+                                const int rlo = h - 2 < 0 ? 0 : h - 2;   // first row fed
+                                const int rhi = h < TR - 1 ? h : TR - 1;  // last row fed
+                                const int k0 = rlo - (h - 2);             // its dy block
+                                const uint64_t bd =
+                                    tc::smem_desc(bdx + k0 * N * 16, 3 * N * 16, 128);
                                 const uint64_t ad = tc::smem_desc(
                                     a_base + (h * kPitch + dx) * 16, kLboA, 128);
-                                tc::mma_bf16(d0 + h * N, ad, bd, idesc3, 1u);
+                                tc::mma_bf16(d0 + rlo * N, ad, bd,
+                                             tc::idesc_bf16_f32(128, (rhi - rlo + 1) * N), 1u);
                             }
                         }
                     } else {
@@ -683,14 +695,15 @@ __global__ void pack_weights_kernel(const float *__restrict__ w, int cin, int co
          idx += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int e = static_cast<int>(idx % 8);
         int o, kg, c, dy, dx;
-        if (n == 32) {
-            // stacked: [chunk][dx][kg][96 = (dy = 2, 1, 0) x 32][8]
-            const int n3 = static_cast<int>((idx / 8) % 96);
-            kg = static_cast<int>((idx / 768) % 2);
-            dx = static_cast<int>((idx / 1536) % 3);
-            c = static_cast<int>(idx / 4608);
-            o = n3 % 32;
-            dy = 2 - n3 / 32;
+        if (n == 32 || n == 64) {
+            // stacked: [chunk][dx][kg][3 n = (dy = 2, 1, 0) x n][8]
+            const int64_t S = 3 * static_cast<int64_t>(n);
+            const int n3 = static_cast<int>((idx / 8) % S);
+            kg = static_cast<int>((idx / (8 * S)) % 2);
+            dx = static_cast<int>((idx / (16 * S)) % 3);
+            c = static_cast<int>(idx / (48 * S));
+            o = n3 % n;
+            dy = 2 - n3 / n;
         } else {
             // [chunk][tap][kg][n][8]
             o = static_cast<int>((idx / 8) % n);
