@@ -487,53 +487,98 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             };
             if (TR % 2 == 0 && a.pool_out) {
                 // ReLU rows in pairs, plus the 2x2 average of their BF16 values
-                // (lanes x and x^1 hold horizontal neighbours); 16 columns of
-                // both rows per TMEM round trip, the next pair's read in flight
-                // while this one is stored
-                constexpr int kPB = 16;
-                constexpr int kRowBlocks = N / kPB;
-                constexpr int kBlocks = (TR / 2) * kRowBlocks;
-                uint32_t pbuf[2][2][kPB];
-                auto tmem_read2 = [&](int k, uint32_t (&v0)[kPB], uint32_t (&v1)[kPB]) {
-                    const int r = 2 * (k / kRowBlocks), j0 = (k % kRowBlocks) * kPB;
-                    tc::tmem_ld16(abase + r * N + j0, v0);
-                    tc::tmem_ld16(abase + (r + 1) * N + j0, v1);
+                // (lanes x and x^1 hold horizontal neighbours), up to 32 columns
+                // of both rows per TMEM round trip; each of the two rows and the
+                // pooled row leaves through the warp's staging row buffer as
+                // contiguous runs
+                constexpr int kCB = N < 32 ? N : 32;
+                constexpr int kW = kCB / 2;  // packed BF16 pairs per pixel and block
+                unsigned char *srow = base + C::kStoreOff + (warp * 32) * C::kStageRow;
+                const int xw = x - lane;     // the warp's first pixel
+                // stages kW words per lane (or per listed pixel) and writes the
+                // pixels [0, npx) of the staging rows as 16-byte chunks to dst
+                auto flush = [&](int npx, auto valid, auto address) {
+                    __syncwarp();
+                    constexpr int kChunks = kCB / 8;
+#pragma unroll
+                    for (int i = 0; i < kChunks; ++i) {
+                        const int pp = i * (32 / kChunks) + lane / kChunks;
+                        const int ch = lane % kChunks;
+                        if (pp < npx && valid(pp)) {
+                            const uint4 val = *reinterpret_cast<const uint4 *>(
+                                srow + pp * C::kStageRow + 16 * ch);
+                            *reinterpret_cast<uint4 *>(address(pp) + 8 * ch) = val;
+                        }
+                    }
+                    __syncwarp();
                 };
-                tmem_read2(0, pbuf[0][0], pbuf[0][1]);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int kb = 0; kb < kBlocks; ++kb) {
-                    if (kb + 1 < kBlocks)
-                        tmem_read2(kb + 1, pbuf[(kb + 1) & 1][0], pbuf[(kb + 1) & 1][1]);
-                    const uint32_t (&v0)[kPB] = pbuf[kb & 1][0];
-                    const uint32_t (&v1)[kPB] = pbuf[kb & 1][1];
-                    const int r = 2 * (kb / kRowBlocks), j = (kb % kRowBlocks) * kPB;
+#pragma unroll 1
+                for (int r = 0; r < TR; r += 2) {
                     const int y = y0 + r;
-                    const bool in0 = (x < a.W) && (y < a.H), in1 = (x < a.W) && (y + 1 < a.H);
-                    const size_t pix0 = (static_cast<size_t>(b) * a.H + y) * a.W + x;
-                    const size_t pix1 = pix0 + a.W;
-                    float f0[16], f1[16], sum[16];
+#pragma unroll 1
+                    for (int j0 = 0; j0 < N; j0 += kCB) {
+                        uint32_t v0[kCB], v1[kCB];
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const float bb = sbias[j + e];
-                        f0[e] = __bfloat162float(
-                            __float2bfloat16_rn(fmaxf(__uint_as_float(v0[e]) + bb, 0.f)));
-                        f1[e] = __bfloat162float(
-                            __float2bfloat16_rn(fmaxf(__uint_as_float(v1[e]) + bb, 0.f)));
-                        sum[e] = f0[e] + f1[e];
+                        for (int q = 0; q < kCB / 16; ++q) {
+                            tc::tmem_ld16(abase + r * N + j0 + 16 * q,
+                                          *reinterpret_cast<uint32_t(*)[16]>(v0 + 16 * q));
+                            tc::tmem_ld16(abase + (r + 1) * N + j0 + 16 * q,
+                                          *reinterpret_cast<uint32_t(*)[16]>(v1 + 16 * q));
+                        }
+                        tc::tmem_wait_ld();
+                        uint32_t w1[kW], wp[kW];
+#pragma unroll
+                        for (int e = 0; e < kCB; e += 2) {
+                            float f0[2], f1[2], sm[2];
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                const float bb = sbias[j0 + e + t];
+                                f0[t] = __bfloat162float(__float2bfloat16_rn(
+                                    fmaxf(__uint_as_float(v0[e + t]) + bb, 0.f)));
+                                f1[t] = __bfloat162float(__float2bfloat16_rn(
+                                    fmaxf(__uint_as_float(v1[e + t]) + bb, 0.f)));
+                                sm[t] = f0[t] + f1[t];
+                                sm[t] += __shfl_xor_sync(0xffffffffu, sm[t], 1);
+                            }
+                            v0[e / 2] = pack_bf16x2(f0[0], f0[1]);  // row r, packed in place
+                            w1[e / 2] = pack_bf16x2(f1[0], f1[1]);
+                            wp[e / 2] = pack_bf16x2(0.25f * sm[0], 0.25f * sm[1]);
+                        }
+                        // row r
+#pragma unroll
+                        for (int q = 0; q < kW / 4; ++q)
+                            reinterpret_cast<uint4 *>(srow + lane * C::kStageRow)[q] =
+                                make_uint4(v0[4 * q], v0[4 * q + 1], v0[4 * q + 2], v0[4 * q + 3]);
+                        flush(32, [&](int pp) { return xw + pp < a.W && y < a.H; },
+                              [&](int pp) {
+                                  return a.out +
+                                         ((static_cast<size_t>(b) * a.H + y) * a.W + xw + pp) * N + j0;
+                              });
+                        // row r + 1
+#pragma unroll
+                        for (int q = 0; q < kW / 4; ++q)
+                            reinterpret_cast<uint4 *>(srow + lane * C::kStageRow)[q] =
+                                make_uint4(w1[4 * q], w1[4 * q + 1], w1[4 * q + 2], w1[4 * q + 3]);
+                        flush(32, [&](int pp) { return xw + pp < a.W && y + 1 < a.H; },
+                              [&](int pp) {
+                                  return a.out + ((static_cast<size_t>(b) * a.H + y + 1) * a.W +
+                                                  xw + pp) * N + j0;
+                              });
+                        // the pooled row: pixel pair k (lanes 2k, 2k+1) at staging row k
+                        if (!(lane & 1)) {
+#pragma unroll
+                            for (int q = 0; q < kW / 4; ++q)
+                                reinterpret_cast<uint4 *>(srow + (lane >> 1) * C::kStageRow)[q] =
+                                    make_uint4(wp[4 * q], wp[4 * q + 1], wp[4 * q + 2], wp[4 * q + 3]);
+                        }
+                        flush(16, [&](int pp) { return xw + 2 * pp + 1 < a.W + 1 &&
+                                                       xw + 2 * pp < a.W && y + 1 < a.H; },
+                              [&](int pp) {
+                                  return a.pool_out +
+                                         ((static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) *
+                                              (a.W >> 1) + (xw >> 1) + pp) * N + j0;
+                              });
                     }
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) sum[e] += __shfl_xor_sync(0xffffffffu, sum[e], 1);
-                    if (in0) store16(a.out + pix0 * N + j, f0);
-                    if (in1) store16(a.out + pix1 * N + j, f1);
-                    if (in1 && !(lane & 1)) {
-                        const size_t pp =
-                            (static_cast<size_t>(b) * (a.H >> 1) + (y >> 1)) * (a.W >> 1) + (x >> 1);
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) sum[e] *= 0.25f;
-                        store16(a.pool_out + pp * N + j, sum);
-                    }
-                    tc::tmem_wait_ld();
                 }
                 release_acc();
                 continue;
