@@ -187,7 +187,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         bars.abort = 0;
         tc::fence_mbar_init();
     }
-    for (int i = tid; i < N; i += kThreads) sbias[i] = (a.bias && i < a.cout) ? a.bias[i] : 0.f;
     if (C::kStack) {
         // the zero operand that resets an accumulator (0 x 0 with accumulate off)
         for (int i = tid; i < C::kZeroBytes / 16; i += kThreads)
@@ -195,6 +194,12 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         tc::fence_proxy_async();
     }
     if (warp == 8) tc::tmem_alloc(&bars.tmem_base, C::kCols);
+    // launched as a programmatic dependent: the set-up above touches no global
+    // memory; every global access below comes after the previous kernel of the
+    // stream has completed
+    pdl_wait();
+    pdl_trigger();
+    for (int i = tid; i < N; i += kThreads) sbias[i] = (a.bias && i < a.cout) ? a.bias[i] : 0.f;
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -840,7 +845,8 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             b.tma_in = a.src_mode == kSrcNHWC ? 1 : 2;
     }
-    conv3x3_kernel<N, RES><<<grid, kThreads, C::kSmem, stream>>>(b, omap, imap);
+    launch_dependent(conv3x3_kernel<N, RES>, dim3(grid), dim3(kThreads), C::kSmem, stream, b, omap,
+                     imap);
     count_launch();
     return launch_status();
 }
