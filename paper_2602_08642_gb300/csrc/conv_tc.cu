@@ -47,7 +47,8 @@ namespace {
 constexpr int kTileX = 128;  // output pixels per row tile (MMA M)
 constexpr int kPitch = 130;  // staged halo pixels per row
 constexpr int kThreads = 288;
-constexpr int kHeader = 256;  // barriers, TMEM slot, abort flag
+constexpr int kHeader = 384;  // barriers, TMEM slot, abort flag
+constexpr int kUpW = kTileX / 2 + 2;  // coarse pixels under a tile's halo (upsampling layers)
 constexpr int kSmemLimit = 227 * 1024;             // dynamic shared memory per CTA
 constexpr int kSmemBudget = kSmemLimit - 512;      // minus alignment slack
 
@@ -104,6 +105,15 @@ struct Cfg {
     static constexpr int kEpiOff = (kStagesOff + kNS * kStage + 127) / 128 * 128;
     static constexpr int kStoreOff = kEpiOff + kEpiBytes;
     static constexpr int kSmem = kStoreOff + kStoreBytes + 128;  // + alignment slack
+    // Upsampling layers (tma_in == 3): the coarse rows under a tile's halo,
+    // one TMA box per 8-channel group, in two buffers after the other areas
+    // (when they fit): [buffer 2][group 2][kUpRows][kUpW][8 ch]
+    static constexpr int kUpRows = TR / 2 + 2;
+    static constexpr int kUpBox = kUpRows * kUpW * 16;         // bytes of one box
+    static constexpr int kUpG = (kUpBox + 127) / 128 * 128;     // its 128-byte aligned slot
+    static constexpr int kUpOff = (kStoreOff + kStoreBytes + 127) / 128 * 128;
+    static constexpr int kSmemUp = kUpOff + 2 * 2 * kUpG + 128;
+    static constexpr bool kUpFits = kSmemUp <= kSmemLimit;
     static_assert(kSmem <= kSmemLimit, "shared memory over the per-CTA limit");
     static_assert(kNS >= 2, "stage does not fit twice");
 };
@@ -115,6 +125,8 @@ struct Bars {
     uint64_t accf[2];   // accumulator ready (tcgen05.commit)
     uint64_t acce[2];   // accumulator drained by the epilogue (128 arrivals)
     uint64_t drain;     // abort path: all issued MMAs complete
+    uint64_t upfull[2]; // coarse boxes of an upsampling layer landed (1 arrival + bytes)
+    uint64_t updone[2]; // coarse buffer expanded by every producer (128 arrivals)
     uint32_t tmem_base;
     int abort;
 };
@@ -156,7 +168,8 @@ __device__ __forceinline__ void tma_store_wait_all() {
 template <int N, bool RES>
 __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                                                              const __grid_constant__ CUtensorMap omap,
-                                                             const __grid_constant__ CUtensorMap imap) {
+                                                             const __grid_constant__ CUtensorMap imap,
+                                                             const __grid_constant__ CUtensorMap umap) {
     using C = Cfg<N, RES>;
     constexpr int TR = C::TR, NS = C::kNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -184,6 +197,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             tc::mbar_init(&bars.acce[i], 128);
         }
         tc::mbar_init(&bars.drain, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&bars.upfull[i], 1);
+            tc::mbar_init(&bars.updone[i], 128);
+        }
         bars.abort = 0;
         tc::fence_mbar_init();
     }
@@ -242,6 +259,27 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             tc::fence_proxy_async();
             tc::mbar_arrive(&bars.full[k % NS]);
         };
+        // tma_in == 3: the u-th upsampled chunk of this CTA (tile blockIdx.x +
+        // (u / nup) * gridDim.x, chunk c0 / 16 + u % nup) has its coarse box in
+        // buffer u & 1; the box of chunk u + 1 is requested while chunk u is
+        // expanded
+        const int nup = a.tma_in == 3 ? kchunks - a.c0 / 16 : 0;
+        uint32_t u_next = 0, u_issued = 0;
+        auto issue_up = [&](uint32_t u) {  // thread ptid 0
+            const int t = blockIdx.x + static_cast<int>(u / nup) * gridDim.x;
+            if (t >= ntiles) return;
+            const int b = t / per_img, r = t - b * per_img;
+            const int y0 = (r / tiles_x) * TR, x0 = (r % tiles_x) * kTileX;
+            const int g = 2 * static_cast<int>(u % nup);  // first 8-channel group in src1
+            uint64_t *bar = &bars.upfull[u & 1];
+            unsigned char *dst = base + C::kUpOff + (u & 1) * 2 * C::kUpG;
+            tc::mbar_arrive_expect_tx(bar, 2 * C::kUpBox);
+#pragma unroll
+            for (int kg = 0; kg < 2; ++kg)
+                tma_load_halo(&umap, dst + kg * C::kUpG, bar, (x0 >> 1) - 1, (y0 - 1) >> 1, g + kg, b);
+            u_issued = u + 1;
+        };
+        if (nup > 0 && ptid == 0) issue_up(0);
         if (RES && ptid == 0) {
             // the whole packed weight operand, once
             tc::mbar_arrive_expect_tx(&bars.wfull[0], static_cast<uint32_t>(kchunks * C::kB));
@@ -283,6 +321,59 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                         for (int kg = 0; kg < 2; ++kg)
                             tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
                                           2 * c + kg, b);
+                    }
+                    ++it;
+                    ++published;
+                } else if (a.tma_in == 3) {
+                    if (c * 16 < a.c0) {
+                        // skip-connection chunk: TMA as above, every producer arrives
+                        if (ptid == 0) {
+                            tc::mbar_arrive_expect_tx(&bars.full[s], 2 * 8 * kPitch * (TR + 2) * 2);
+#pragma unroll
+                            for (int kg = 0; kg < 2; ++kg)
+                                tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
+                                              2 * c + kg, b);
+                        } else {
+                            tc::mbar_arrive(&bars.full[s]);
+                        }
+                    } else {
+                        // upsampled chunk: request the next chunk's coarse box once
+                        // its buffer (used by chunk u_next - 1) is expanded, then
+                        // expand this one: halo pixel (x, y) <- coarse (x/2, y/2),
+                        // zero outside the output grid
+                        const uint32_t u = u_next++;
+                        if (ptid == 0) {
+                            if (u >= 1 && !tc::mbar_wait(&bars.updone[(u - 1) & 1], ((u - 1) >> 1) & 1u,
+                                                         abort_flag)) {
+                                fail();
+                                ok = false;
+                                break;
+                            }
+                            issue_up(u + 1);
+                        }
+                        if (!tc::mbar_wait(&bars.upfull[u & 1], (u >> 1) & 1u, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        const unsigned char *ub = base + C::kUpOff + (u & 1) * 2 * C::kUpG;
+                        const int cy0 = (y0 - 1) >> 1, cx0 = (x0 >> 1) - 1;
+#pragma unroll
+                        for (int k = 0; k < kPer; ++k) {
+                            if (tinfo[k] < 0) continue;
+                            const int row = tinfo[k] >> 10, px = (tinfo[k] >> 1) & 511,
+                                      kg = tinfo[k] & 1;
+                            const int y = y0 - 1 + row, x = x0 - 1 + px;
+                            uint4 v = make_uint4(0, 0, 0, 0);
+                            if (y >= 0 && y < a.H && x >= 0 && x < a.W)
+                                v = *reinterpret_cast<const uint4 *>(
+                                    ub + kg * C::kUpG +
+                                    (((y >> 1) - cy0) * kUpW + ((x >> 1) - cx0)) * 16);
+                            *reinterpret_cast<uint4 *>(As + kg * C::kKg + (row * kPitch + px) * 16) = v;
+                        }
+                        tc::fence_proxy_async();
+                        tc::mbar_arrive(&bars.full[s]);
+                        tc::mbar_arrive(&bars.updone[u & 1]);
                     }
                     ++it;
                     ++published;
@@ -367,6 +458,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 for (uint32_t k = first; k < it; ++k)
                     (void)tc::mbar_wait(&bars.full[k % NS], (k / NS) & 1u, nullptr);
             }
+            if (a.tma_in >= 2) {
+                // the skip-connection boxes (TMA) among the last stages
+                const uint32_t first = it > NS ? it - NS : 0;
+                for (uint32_t k = first; k < it; ++k)
+                    if (static_cast<int>(k % static_cast<uint32_t>(kchunks)) * 16 < a.c0)
+                        (void)tc::mbar_wait(&bars.full[k % NS], (k / NS) & 1u, nullptr);
+            }
+            // coarse boxes requested (the last two, one per buffer)
+            for (uint32_t k = u_issued > 2 ? u_issued - 2 : 0; k < u_issued; ++k)
+                (void)tc::mbar_wait(&bars.upfull[k & 1], (k >> 1) & 1u, nullptr);
             if (RES) {
                 if (issued) (void)tc::mbar_wait(&bars.wfull[0], 0, nullptr);
             } else {
@@ -794,7 +895,7 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
     if (configured_dev != dev) {
         if (cudaFuncSetAttribute(conv3x3_kernel<N, RES>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 C::kSmem) != cudaSuccess)
+                                 C::kUpFits ? C::kSmemUp : C::kSmem) != cudaSuccess)
             return SPP_ERR_CUDA;
         configured_dev = dev;
     }
@@ -845,8 +946,31 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             b.tma_in = a.src_mode == kSrcNHWC ? 1 : 2;
     }
-    launch_dependent(conv3x3_kernel<N, RES>, dim3(grid), dim3(kThreads), C::kSmem, stream, b, omap,
-                     imap);
+    CUtensorMap umap;
+    memset(&umap, 0, sizeof(umap));
+    if (b.tma_in == 2 && C::kUpFits && a.c1 % 8 == 0 && a.c1 > 0 && a.W % 2 == 0 &&
+        a.H % 2 == 0) {
+        // the coarse source [B][H/2][W/2][c1] as 5-D (channel in group, x, y, group,
+        // image); box 8 x kUpW x kUpRows x 1 x 1 = one 8-channel group of the coarse
+        // rows under a tile's halo
+        auto enc = tensor_map_encoder();
+        const int Wc = a.W / 2, Hc = a.H / 2;
+        cuuint64_t dims[5] = {8, static_cast<cuuint64_t>(Wc), static_cast<cuuint64_t>(Hc),
+                              static_cast<cuuint64_t>(a.c1 / 8), static_cast<cuuint64_t>(a.B)};
+        cuuint64_t strides[4] = {static_cast<cuuint64_t>(a.c1) * 2,
+                                 static_cast<cuuint64_t>(Wc) * a.c1 * 2, 16,
+                                 static_cast<cuuint64_t>(Hc) * Wc * a.c1 * 2};
+        cuuint32_t box[5] = {8, static_cast<cuuint32_t>(kUpW), static_cast<cuuint32_t>(C::kUpRows),
+                             1, 1};
+        cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        if (enc && enc(&umap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(a.src1),
+                       dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            b.tma_in = 3;
+    }
+    launch_dependent(conv3x3_kernel<N, RES>, dim3(grid), dim3(kThreads),
+                     b.tma_in == 3 ? C::kSmemUp : C::kSmem, stream, b, omap, imap, umap);
     count_launch();
     return launch_status();
 }

@@ -49,7 +49,9 @@ struct ConvArgs {
     __nv_bfloat16 *pool_out = nullptr;
     int tma_out = 0;  // set by the launcher: FP32 planar output through TMA stores
     int tma_in = 0;   // set by the launcher: NHWC halo through TMA loads (1), or only the
-                      // skip-connection chunks of an upsampling layer (2)
+                      // skip-connection chunks of an upsampling layer (2), or those and
+                      // the coarse rows of its upsampled chunks, expanded in shared
+                      // memory (3)
     int32_t *status = nullptr;
 };
 
