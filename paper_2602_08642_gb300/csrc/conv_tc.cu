@@ -11,16 +11,18 @@
 //   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //              lanes 32w..32w+31 = pixels), bias / ReLU / mask, stores;
 //   warps 4-7  producers: per K chunk of 16 input channels they stage the
-//              (TR+2) x 130 pixel halo of the tile in shared memory in the
-//              K-major core-matrix layout [kgroup 2][row][pixel][8 ch], with
-//              zero padding, fused 2x2 pooling, fused upsample + concat or
-//              FP32 -> BF16 conversion on the way; one elected thread
+//              (TR+2) x 130 pixel halo of the tile in shared memory as K-major
+//              rows of 32 bytes per pixel in the 32-byte swizzle ([row][pixel]
+//              [16 ch], a_off), with zero padding, fused 2x2 pooling, fused
+//              upsample + concat or FP32 -> BF16 conversion on the way (a TMA
+//              box writes the plain NHWC case directly); one elected thread
 //              bulk-copies the pre-packed weights of the chunk;
 //   warp 8     lane 0 issues the MMAs: for each row r and tap (dy, dx) the A
 //              operand is the halo window starting at row r+dy, pixel dx
-//              (a 16-byte-aligned start address; SBO = 128 B because the
-//              pixels of a row are consecutive 16-byte rows), the B operand
-//              the tap's weight block.  No im2col copy is made.
+//              (a start address moved by whole 32-byte pixel rows, which the
+//              swizzled descriptor allows because the swizzle follows the
+//              absolute address), the B operand the tap's weight block.  No
+//              im2col copy is made.
 //
 // Stages are recycled through full/empty mbarriers (producers -> MMA via
 // arrival counts and transaction bytes, MMA -> producers via
@@ -59,11 +61,9 @@ constexpr int kResidentMax = 80 * 1024;  // weights kept in shared memory up to 
 template <int N, bool RES>
 struct Cfg {
     static constexpr int TR = N <= 64 ? 4 : N <= 128 ? 2 : 1;  // rows per tile
-    // bytes between the two 8-channel groups of a stage (the A operand's LBO):
-    // one group rounded up to 128 bytes, so that each group's TMA box starts
-    // on a 128-byte boundary
-    static constexpr int kKg = ((TR + 2) * kPitch * 16 + 127) / 128 * 128;
-    static constexpr int kA = 2 * kKg;                          // halo bytes per stage
+    // halo bytes per stage: (TR+2) x 130 pixel rows of 32 bytes (16 channels),
+    // 32-byte swizzled (a_off), a multiple of the 256-byte swizzle period
+    static constexpr int kA = ((TR + 2) * kPitch * 32 + 255) / 256 * 256;
     static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per K chunk
     static constexpr int kStage = RES ? kA : kA + kB;
     static constexpr int kWRegion = RES ? kResidentMax : 0;
@@ -78,7 +78,7 @@ struct Cfg {
     static constexpr int kZeroRows = TR * N > 128 ? TR * N : 128;
     static constexpr int kZeroBytes = kStack ? 2 * kZeroRows * 16 : 0;
     static constexpr int kWOff = kZeroOff + kZeroBytes;          // resident weights
-    static constexpr int kStagesOff = kWOff + kWRegion;
+    static constexpr int kStagesOff = (kWOff + kWRegion + 255) / 256 * 256;
     // BF16 NHWC outputs leave through a per-warp staging row buffer, so that
     // each warp store writes contiguous 512-byte runs ([32 px][kCBs ch] with
     // a 16-byte pad per pixel: conflict-free 16-byte shared accesses)
@@ -104,15 +104,15 @@ struct Cfg {
     // and TMA tensor stores (resident-weight variants; the heads are)
     static constexpr int kEpiOff = (kStagesOff + kNS * kStage + 127) / 128 * 128;
     static constexpr int kStoreOff = kEpiOff + kEpiBytes;
-    static constexpr int kSmem = kStoreOff + kStoreBytes + 128;  // + alignment slack
+    static constexpr int kSmem = kStoreOff + kStoreBytes + 256;  // + alignment slack
     // Upsampling layers (tma_in == 3): the coarse rows under a tile's halo,
-    // one TMA box per 8-channel group, in two buffers after the other areas
-    // (when they fit): [buffer 2][group 2][kUpRows][kUpW][8 ch]
+    // one TMA box of 16 channels, in two buffers after the other areas (when
+    // they fit): [buffer 2][kUpRows][kUpW][16 ch], not swizzled
     static constexpr int kUpRows = TR / 2 + 2;
-    static constexpr int kUpBox = kUpRows * kUpW * 16;         // bytes of one box
+    static constexpr int kUpBox = kUpRows * kUpW * 32;         // bytes of one box
     static constexpr int kUpG = (kUpBox + 127) / 128 * 128;     // its 128-byte aligned slot
     static constexpr int kUpOff = (kStoreOff + kStoreBytes + 127) / 128 * 128;
-    static constexpr int kSmemUp = kUpOff + 2 * 2 * kUpG + 128;
+    static constexpr int kSmemUp = kUpOff + 2 * kUpG + 256;
     static constexpr bool kUpFits = kSmemUp <= kSmemLimit;
     static_assert(kSmem <= kSmemLimit, "shared memory over the per-CTA limit");
     static_assert(kNS >= 2, "stage does not fit twice");
@@ -131,6 +131,16 @@ struct Bars {
     int abort;
 };
 static_assert(sizeof(Bars) <= kHeader, "header");
+
+// Byte offset in a stage of the 8 channels kg (0, 1) of halo pixel (row, px):
+// rows of 32 bytes (one 16-channel K chunk) in the K-major 32-byte swizzle
+// (the 16-byte half kg of row q sits at half kg ^ bit 2 of q), the layout a
+// TMA box with CU_TENSOR_MAP_SWIZZLE_32B writes to a 256-byte aligned stage
+// and the one the MMA reads through a SWIZZLE_32B descriptor at any row start
+__device__ __forceinline__ int a_off(int row, int px, int kg) {
+    const int q = row * kPitch + px;
+    return q * 32 + 16 * (kg ^ ((q >> 2) & 1));
+}
 
 __device__ __forceinline__ void named_bar_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
     using C = Cfg<N, RES>;
     constexpr int TR = C::TR, NS = C::kNS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char *base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+    unsigned char *base = smem_raw + ((256u - (tc::smem_u32(smem_raw) & 255u)) & 255u);
     Bars &bars = *reinterpret_cast<Bars *>(base);
     unsigned char *wres = base + C::kWOff;              // resident weights (RES)
     unsigned char *stages = base + C::kStagesOff;
@@ -270,13 +280,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             if (t >= ntiles) return;
             const int b = t / per_img, r = t - b * per_img;
             const int y0 = (r / tiles_x) * TR, x0 = (r % tiles_x) * kTileX;
-            const int g = 2 * static_cast<int>(u % nup);  // first 8-channel group in src1
             uint64_t *bar = &bars.upfull[u & 1];
-            unsigned char *dst = base + C::kUpOff + (u & 1) * 2 * C::kUpG;
-            tc::mbar_arrive_expect_tx(bar, 2 * C::kUpBox);
-#pragma unroll
-            for (int kg = 0; kg < 2; ++kg)
-                tma_load_halo(&umap, dst + kg * C::kUpG, bar, (x0 >> 1) - 1, (y0 - 1) >> 1, g + kg, b);
+            tc::mbar_arrive_expect_tx(bar, C::kUpBox);
+            tma_load_halo(&umap, base + C::kUpOff + (u & 1) * C::kUpG, bar, (x0 >> 1) - 1,
+                          (y0 - 1) >> 1, static_cast<int>(u % nup), b);
             u_issued = u + 1;
         };
         if (nup > 0 && ptid == 0) issue_up(0);
@@ -311,16 +318,13 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     ++issued;
                 }
                 // task j -> 8-channel group j & 1 (fastest), then pixel, then row;
-                // shared-memory offset kg * kKg + (row * kPitch + px) * 16
+                // shared-memory offset a_off(row, px, kg)
                 if (a.tma_in == 1) {
                     // the halo of both 8-channel groups as two TMA boxes (zero fill
                     // outside the image and beyond the channels)
                     if (ptid == 0) {
-                        tc::mbar_arrive_expect_tx(&bars.full[s], 2 * 8 * kPitch * (TR + 2) * 2);
-#pragma unroll
-                        for (int kg = 0; kg < 2; ++kg)
-                            tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
-                                          2 * c + kg, b);
+                        tc::mbar_arrive_expect_tx(&bars.full[s], kPitch * (TR + 2) * 32);
+                        tma_load_halo(&imap, As, &bars.full[s], x0 - 1, y0 - 1, c, b);
                     }
                     ++it;
                     ++published;
@@ -328,11 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     if (c * 16 < a.c0) {
                         // skip-connection chunk: TMA as above, every producer arrives
                         if (ptid == 0) {
-                            tc::mbar_arrive_expect_tx(&bars.full[s], 2 * 8 * kPitch * (TR + 2) * 2);
-#pragma unroll
-                            for (int kg = 0; kg < 2; ++kg)
-                                tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
-                                              2 * c + kg, b);
+                            tc::mbar_arrive_expect_tx(&bars.full[s], kPitch * (TR + 2) * 32);
+                            tma_load_halo(&imap, As, &bars.full[s], x0 - 1, y0 - 1, c, b);
                         } else {
                             tc::mbar_arrive(&bars.full[s]);
                         }
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             ok = false;
                             break;
                         }
-                        const unsigned char *ub = base + C::kUpOff + (u & 1) * 2 * C::kUpG;
+                        const unsigned char *ub = base + C::kUpOff + (u & 1) * C::kUpG;
                         const int cy0 = (y0 - 1) >> 1, cx0 = (x0 >> 1) - 1;
 #pragma unroll
                         for (int k = 0; k < kPer; ++k) {
@@ -367,9 +368,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             uint4 v = make_uint4(0, 0, 0, 0);
                             if (y >= 0 && y < a.H && x >= 0 && x < a.W)
                                 v = *reinterpret_cast<const uint4 *>(
-                                    ub + kg * C::kUpG +
-                                    (((y >> 1) - cy0) * kUpW + ((x >> 1) - cx0)) * 16);
-                            *reinterpret_cast<uint4 *>(As + kg * C::kKg + (row * kPitch + px) * 16) = v;
+                                    ub + (((y >> 1) - cy0) * kUpW + ((x >> 1) - cx0)) * 32 + kg * 16);
+                            *reinterpret_cast<uint4 *>(As + a_off(row, px, kg)) = v;
                         }
                         tc::fence_proxy_async();
                         tc::mbar_arrive(&bars.full[s]);
@@ -382,11 +382,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     // producer arrives now; an empty copy group keeps the count of
                     // groups equal to the count of stages for the lagged ones
                     if (ptid == 0) {
-                        tc::mbar_arrive_expect_tx(&bars.full[s], 2 * 8 * kPitch * (TR + 2) * 2);
-#pragma unroll
-                        for (int kg = 0; kg < 2; ++kg)
-                            tma_load_halo(&imap, As + kg * C::kKg, &bars.full[s], x0 - 1, y0 - 1,
-                                          2 * c + kg, b);
+                        tc::mbar_arrive_expect_tx(&bars.full[s], kPitch * (TR + 2) * 32);
+                        tma_load_halo(&imap, As, &bars.full[s], x0 - 1, y0 - 1, c, b);
                     } else {
                         tc::mbar_arrive(&bars.full[s]);
                     }
@@ -405,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                         const int row = tinfo[u] >> 10, px = (tinfo[u] >> 1) & 511, kg = tinfo[u] & 1;
                         const __nv_bfloat16 *src = chunk_address(a, b, y0 - 1 + row, x0 - 1 + px,
                                                                  c * 16 + kg * 8);
-                        cp_async16(sbase + kg * C::kKg + (row * kPitch + px) * 16,
+                        cp_async16(sbase + a_off(row, px, kg),
                                    src ? src : a.src0, src ? 16u : 0u);
                     }
                     cp_async_commit();
@@ -435,8 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             const int j = j0 + u * 128 + ptid;
                             if (j < kTasks) {
                                 const int kg = j & 1, px = (j >> 1) % kPitch, row = (j >> 1) / kPitch;
-                                *reinterpret_cast<uint4 *>(As + kg * C::kKg +
-                                                           (row * kPitch + px) * 16) = v[u];
+                                *reinterpret_cast<uint4 *>(As + a_off(row, px, kg)) = v[u];
                             }
                         }
                     }
@@ -480,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         // -------------------------------------------------------- MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(128, N);
-            constexpr uint32_t kLboA = C::kKg, kLboB = N * 16;
+            constexpr uint32_t kLboB = N * 16;
             uint32_t it = 0, tl = 0;
             bool ok = true, pending = false;
             if (RES && ntiles > static_cast<int>(blockIdx.x) &&
@@ -531,8 +527,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                                 const int k0 = rlo - (h - 2);             // its dy block
                                 const uint64_t bd =
                                     tc::smem_desc(bdx + k0 * N * 16, 3 * N * 16, 128);
-                                const uint64_t ad = tc::smem_desc(
-                                    a_base + (h * kPitch + dx) * 16, kLboA, 128);
+                                const uint64_t ad =
+                                    tc::smem_desc_sw32(a_base + (h * kPitch + dx) * 32);
                                 tc::mma_bf16(d0 + rlo * N, ad, bd,
                                              tc::idesc_bf16_f32(128, (rhi - rlo + 1) * N), 1u);
                             }
@@ -545,8 +541,8 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                                 tc::smem_desc(b_base + tap * 2 * N * 16, kLboB, 128);
 #pragma unroll
                             for (int r = 0; r < TR; ++r) {
-                                const uint64_t ad = tc::smem_desc(
-                                    a_base + ((r + dy) * kPitch + dx) * 16, kLboA, 128);
+                                const uint64_t ad =
+                                    tc::smem_desc_sw32(a_base + ((r + dy) * kPitch + dx) * 32);
                                 tc::mma_bf16(d0 + r * N, ad, bd, idesc, (c | tap) != 0);
                             }
                         }
@@ -926,41 +922,42 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
     CUtensorMap imap;
     memset(&imap, 0, sizeof(imap));
     b.tma_in = 0;
-    if ((a.src_mode == kSrcNHWC || (a.src_mode == kSrcConcatUp && a.c0 % 16 == 0)) &&
-        a.c0 % 8 == 0 && !getenv_disable_tma_in()) {
-        // NHWC BF16 [B][H][W][c0] as 5-D (channel in group, x, y, group, image);
-        // box 8 x 130 x (TR+2) x 1 x 1 = one 8-channel group of the halo
+    if ((a.src_mode == kSrcNHWC || a.src_mode == kSrcConcatUp) && a.c0 % 16 == 0 &&
+        !getenv_disable_tma_in()) {
+        // NHWC BF16 [B][H][W][c0] as 5-D (channel in chunk, x, y, 16-channel chunk,
+        // image); box 16 x 130 x (TR+2) x 1 x 1 = one K chunk of the halo, written
+        // with the 32-byte swizzle of the A operand (32-byte pieces: about twice
+        // the TMA throughput of 16-byte ones)
         auto enc = tensor_map_encoder();
-        const int groups = a.c0 / 8;
-        cuuint64_t dims[5] = {8, static_cast<cuuint64_t>(a.W), static_cast<cuuint64_t>(a.H),
-                              static_cast<cuuint64_t>(groups), static_cast<cuuint64_t>(a.B)};
+        cuuint64_t dims[5] = {16, static_cast<cuuint64_t>(a.W), static_cast<cuuint64_t>(a.H),
+                              static_cast<cuuint64_t>(a.c0 / 16), static_cast<cuuint64_t>(a.B)};
         cuuint64_t strides[4] = {static_cast<cuuint64_t>(a.c0) * 2,
-                                 static_cast<cuuint64_t>(a.W) * a.c0 * 2, 16,
+                                 static_cast<cuuint64_t>(a.W) * a.c0 * 2, 32,
                                  static_cast<cuuint64_t>(a.H) * a.W * a.c0 * 2};
-        cuuint32_t box[5] = {8, static_cast<cuuint32_t>(kPitch), static_cast<cuuint32_t>(C::TR + 2),
+        cuuint32_t box[5] = {16, static_cast<cuuint32_t>(kPitch), static_cast<cuuint32_t>(C::TR + 2),
                              1, 1};
         cuuint32_t estr[5] = {1, 1, 1, 1, 1};
         if (enc && enc(&imap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(a.src0),
                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
             b.tma_in = a.src_mode == kSrcNHWC ? 1 : 2;
     }
     CUtensorMap umap;
     memset(&umap, 0, sizeof(umap));
-    if (b.tma_in == 2 && C::kUpFits && a.c1 % 8 == 0 && a.c1 > 0 && a.W % 2 == 0 &&
+    if (b.tma_in == 2 && C::kUpFits && a.c1 % 16 == 0 && a.c1 > 0 && a.W % 2 == 0 &&
         a.H % 2 == 0) {
-        // the coarse source [B][H/2][W/2][c1] as 5-D (channel in group, x, y, group,
-        // image); box 8 x kUpW x kUpRows x 1 x 1 = one 8-channel group of the coarse
-        // rows under a tile's halo
+        // the coarse source [B][H/2][W/2][c1] as 5-D (channel in chunk, x, y,
+        // 16-channel chunk, image); box 16 x kUpW x kUpRows x 1 x 1 = one K chunk of
+        // the coarse rows under a tile's halo
         auto enc = tensor_map_encoder();
         const int Wc = a.W / 2, Hc = a.H / 2;
-        cuuint64_t dims[5] = {8, static_cast<cuuint64_t>(Wc), static_cast<cuuint64_t>(Hc),
-                              static_cast<cuuint64_t>(a.c1 / 8), static_cast<cuuint64_t>(a.B)};
+        cuuint64_t dims[5] = {16, static_cast<cuuint64_t>(Wc), static_cast<cuuint64_t>(Hc),
+                              static_cast<cuuint64_t>(a.c1 / 16), static_cast<cuuint64_t>(a.B)};
         cuuint64_t strides[4] = {static_cast<cuuint64_t>(a.c1) * 2,
-                                 static_cast<cuuint64_t>(Wc) * a.c1 * 2, 16,
+                                 static_cast<cuuint64_t>(Wc) * a.c1 * 2, 32,
                                  static_cast<cuuint64_t>(Hc) * Wc * a.c1 * 2};
-        cuuint32_t box[5] = {8, static_cast<cuuint32_t>(kUpW), static_cast<cuuint32_t>(C::kUpRows),
+        cuuint32_t box[5] = {16, static_cast<cuuint32_t>(kUpW), static_cast<cuuint32_t>(C::kUpRows),
                              1, 1};
         cuuint32_t estr[5] = {1, 1, 1, 1, 1};
         if (enc && enc(&umap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16 *>(a.src1),
@@ -978,7 +975,11 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
 template <int N>
 int launch(const ConvArgs &a, cudaStream_t stream) {
     const int64_t wbytes = static_cast<int64_t>(a.cin_pad / 16) * Cfg<N, false>::kB;
-    if (wbytes <= kResidentMax) return launch_variant<N, true>(a, stream);
+    // N = 192 (data gradients of the 192-channel decoder input) always streams:
+    // its weights exceed the resident region at every cin_pad above 16
+    if constexpr (N != 192) {
+        if (wbytes <= kResidentMax) return launch_variant<N, true>(a, stream);
+    }
     return launch_variant<N, false>(a, stream);
 }
 

@@ -7,7 +7,9 @@
 // distance between core matrices that are adjacent along K, the stride byte
 // offset (SBO) the distance between core matrices adjacent along M (or N).
 // The start address only has to be 16-byte aligned, so shifting it by whole
-// 16-byte rows selects a window of rows (used for the 3x3 taps).
+// 16-byte rows selects a window of rows.  The convolution's A operand uses
+// the 32-byte swizzled form instead (smem_desc_sw32), which allows the same
+// row windows (used for the 3x3 taps).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -141,6 +143,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) |
            (static_cast<uint64_t>(lbo >> 4) << 16) | (static_cast<uint64_t>(sbo >> 4) << 32) |
            (1ull << 46);
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 32-byte swizzle
+// (layout type 6): rows of 32 bytes (K = 16 BF16 values), the 16-byte half h
+// of the row at address a stored at half h ^ bit 7 of a; 8-row groups 256
+// bytes apart (SBO); the LBO is not used for K = 16.  The swizzle is taken
+// from the absolute shared-memory address with base offset 0, so the start
+// may be any 32-byte row (measured: every row shift 0..15 reproduces the
+// unshifted product, and a TMA box with CU_TENSOR_MAP_SWIZZLE_32B into a
+// 256-byte aligned buffer writes this layout).
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+    return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (1ull << 16) |
+           (static_cast<uint64_t>(256 >> 4) << 32) | (1ull << 46) | (6ull << 61);
 }
 
 // Instruction descriptor of kind::f16: D in FP32, A and B in BF16, both
