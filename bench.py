@@ -849,9 +849,13 @@ def run_estimator_ablation(args, spp, rank):
         for k in range(steps):
             idx = rng.choice(len(train), 8, replace=False)
             losses.append(tr.step([train[i] for i in idx], seed=1000 + 17 * k))
+        cov = []
         res[est] = {"psnr_db": float(np.mean(Lm.evaluate(held, budget, tr.net.theta, None,
-                                                         estimator=est))),
-                    "loss_last20": float(np.mean(losses[-20:]))}
+                                                         estimator=est, coverage=cov))),
+                    "loss_first20": float(np.mean(losses[:20])),
+                    "loss_last20": float(np.mean(losses[-20:])),
+                    "test_spp": float(np.mean([c[0] for c in cov])),
+                    "test_pixels_without_sample": float(np.mean([c[1] for c in cov]))}
         del tr
     return res
 

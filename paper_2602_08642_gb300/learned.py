@@ -454,12 +454,13 @@ class Trainer:
 def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None,
              fixed_logits: list[torch.Tensor] | None = None, seed: int = 99,
              temporal: list | None = None, dither_mask=None,
-             estimator: str = "relaxed") -> list[float]:
+             estimator: str = "relaxed", coverage: list | None = None) -> list[float]:
     """PSNR (tone-mapped sRGB against the tone-mapped clean image) of frame
     t of each sample.  theta None runs the plain method: uniform density
     d = 1 and the fixed logits (54 / 29 / 25 channels).  If ``temporal`` is
     a list, the temporal error mean |dI - dI_ref| of Eq. loss_temporal of
-    each sample is appended to it."""
+    each sample is appended to it; if ``coverage`` is a list, the frame's
+    samples per pixel and its fraction of pixels without a sample are."""
     W, H = samples[0].W, samples[0].H
     rnd = Renderer(1, W, H, budget, dither_mask, estimator=estimator, train=False)
     net = Predictor(theta, 1, W, H) if theta is not None else None
@@ -483,6 +484,10 @@ def evaluate(samples: list[FrameData], budget: float, theta: torch.Tensor | None
         rnd.current_frame(0, d, lg, s.clean, seed + i, 1)
         rnd.reference(0, s.clean)
         out.append(rnd.psnr(0))
+        if coverage is not None:
+            fr = rnd.frames[0]
+            coverage.append((fr.sample_count() / (W * H),
+                             float((fr.counts == 0).float().mean().item())))
         if temporal is not None:
             # mean |dI - dI_ref|: the combined loss with the spatial weight 0
             rnd.temporal_references(0, s.clean_prev, s.mv)
