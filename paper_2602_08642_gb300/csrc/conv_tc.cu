@@ -67,7 +67,7 @@ struct Cfg {
     static constexpr int kB = 9 * 2 * N * 16;                   // weight bytes per K chunk
     static constexpr int kStage = RES ? kA : kA + kB;
     static constexpr int kWRegion = RES ? kResidentMax : 0;
-    static constexpr int kEpiBytes = RES ? 2 * 16 * kTileX * 4 : 0;
+    static constexpr int kEpiBytes = RES ? 4 * 2 * (N >= 32 ? 32 : 16) * 32 * 4 : 0;
     static constexpr int kBiasOff = kHeader;                     // FP32 bias [N]
     static constexpr int kZeroOff = kBiasOff + 1024;             // zero operand (stacked)
     // N = 32 and 64: the three dy taps of a halo row are one MMA of 3 N columns
@@ -85,7 +85,10 @@ struct Cfg {
     static constexpr int kCBs = N < 32 ? N : 32;
     static constexpr int kStageRow = 2 * kCBs + 16;
     static constexpr int kStoreBytes = 4 * 32 * kStageRow;
-    static constexpr int kNS0 = (kSmemBudget - kStagesOff - kEpiBytes - kStoreBytes) / kStage;
+    // the FP32 planar staging buffers and the BF16 staging rows share one
+    // region (a launch uses one of the two epilogues)
+    static constexpr int kOutBytes = kEpiBytes > kStoreBytes ? kEpiBytes : kStoreBytes;
+    static constexpr int kNS0 = (kSmemBudget - kStagesOff - kOutBytes) / kStage;
     static constexpr int kNS = kNS0 > 8 ? 8 : kNS0;
     // a stage is published kLag stages after its copies were issued; kLag <=
     // kNS - 2 lets the MMAs of one stage run while the next is published
@@ -103,8 +106,8 @@ struct Cfg {
     // FP32 planar outputs leave through two 8 KB staging buffers ([16 ch][128 px])
     // and TMA tensor stores (resident-weight variants; the heads are)
     static constexpr int kEpiOff = (kStagesOff + kNS * kStage + 127) / 128 * 128;
-    static constexpr int kStoreOff = kEpiOff + kEpiBytes;
-    static constexpr int kSmem = kStoreOff + kStoreBytes + 256;  // + alignment slack
+    static constexpr int kStoreOff = kEpiOff;
+    static constexpr int kSmem = kEpiOff + kOutBytes + 256;  // + alignment slack
     // Upsampling layers (tma_in == 3): the coarse rows under a tile's halo,
     // one TMA box of 16 channels, in two buffers after the other areas (when
     // they fit): [buffer 2][kUpRows][kUpW][16 ch], not swizzled
@@ -112,7 +115,9 @@ struct Cfg {
     static constexpr int kUpBox = kUpRows * kUpW * 32;         // bytes of one box
     static constexpr int kUpG = (kUpBox + 127) / 128 * 128;     // its 128-byte aligned slot
     static constexpr int kUpOff = (kStoreOff + kStoreBytes + 127) / 128 * 128;
-    static constexpr int kSmemUp = kUpOff + 2 * kUpG + 256;
+    // (upsampling layers have BF16 outputs: the buffers may overlap the FP32 area)
+    static constexpr int kSmemUp0 = kUpOff + 2 * kUpG + 256;
+    static constexpr int kSmemUp = kSmemUp0 > kSmem ? kSmemUp0 : kSmem;
     static constexpr bool kUpFits = kSmemUp <= kSmemLimit;
     static_assert(kSmem <= kSmemLimit, "shared memory over the per-CTA limit");
     static_assert(kNS >= 2, "stage does not fit twice");
@@ -686,42 +691,39 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 continue;
             }
             if (RES && a.epi_mode == kEpiF32Planar && a.tma_out) {
-                // stage 16 output planes of the row in shared memory, store them
-                // with one TMA tensor store of 128 pixels (clipped at W and at
-                // cout); 128-pixel rows store faster than per-warp 32-pixel ones
+                // each epilogue warp stages kPB output planes of its 32 pixels of
+                // the row in its own buffer and stores them with one TMA tensor
+                // store (clipped at W and at cout); two buffers per warp
+                constexpr int kPB = N >= 32 ? 32 : 16;  // planes per block
                 float *ebuf = reinterpret_cast<float *>(base + C::kEpiOff);
-                const int px = warp * 32 + lane;
                 const int x0 = (rr % tiles_x) * kTileX;
-                // 16 planes per round, the next round's TMEM read in flight
-                // while this one is staged and stored
-                constexpr int kRowBlocks = N / 16;
+                constexpr int kRowBlocks = N / kPB;
                 constexpr int kBlocks = TR * kRowBlocks;
-                uint32_t fbuf[2][16];
-                auto tmem_read16 = [&](int k, uint32_t (&vv)[16]) {
-                    tc::tmem_ld16(abase + (k / kRowBlocks) * N + (k % kRowBlocks) * 16, vv);
+                uint32_t fbuf[2][kPB];
+                auto tmem_read = [&](int k, uint32_t (&vv)[kPB]) {
+#pragma unroll
+                    for (int q = 0; q < kPB / 16; ++q)
+                        tc::tmem_ld16(abase + (k / kRowBlocks) * N + (k % kRowBlocks) * kPB + 16 * q,
+                                      *reinterpret_cast<uint32_t(*)[16]>(vv + 16 * q));
                 };
-                tmem_read16(0, fbuf[0]);
+                tmem_read(0, fbuf[0]);
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int kb = 0; kb < kBlocks; ++kb) {
-                    if (kb + 1 < kBlocks) tmem_read16(kb + 1, fbuf[(kb + 1) & 1]);
-                    const uint32_t (&v)[16] = fbuf[kb & 1];
-                    const int y = y0 + kb / kRowBlocks, j0 = (kb % kRowBlocks) * 16;
+                    if (kb + 1 < kBlocks) tmem_read(kb + 1, fbuf[(kb + 1) & 1]);
+                    const uint32_t (&v)[kPB] = fbuf[kb & 1];
+                    const int y = y0 + kb / kRowBlocks, j0 = (kb % kRowBlocks) * kPB;
                     if (j0 < a.cout) {  // padding columns are not stored
-                        float *buf = ebuf + (eblk & 1) * (16 * kTileX);
-                        // bias into registers before the barrier, whose memory
-                        // clobber would otherwise serialise these reads
-                        float bb[16];
+                        float *buf = ebuf + (warp * 2 + (eblk & 1)) * kPB * 32;
+                        if (lane == 0) tma_store_wait_read<1>();
+                        __syncwarp();
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) bb[e] = sbias[j0 + e];
-                        if (tid == 0) tma_store_wait_read<1>();
-                        named_bar_epilogue();
-#pragma unroll
-                        for (int e = 0; e < 16; ++e)
-                            buf[e * kTileX + px] = __uint_as_float(v[e]) + bb[e];
+                        for (int e = 0; e < kPB; ++e)
+                            buf[e * 32 + lane] = __uint_as_float(v[e]) + sbias[j0 + e];
                         tc::fence_proxy_async();
-                        named_bar_epilogue();
-                        if (tid == 0 && y < a.H) tma_store_planes(&omap, buf, x0, y, j0, b);
+                        __syncwarp();
+                        if (lane == 0 && y < a.H && x0 + warp * 32 < a.W)
+                            tma_store_planes(&omap, buf, x0 + warp * 32, y, j0, b);
                         ++eblk;
                     }
                     tc::tmem_wait_ld();
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             }
             release_acc();
         }
-        if (tid == 0 && eblk) tma_store_wait_all();
+        if (lane == 0 && eblk) tma_store_wait_all();
     }
 
     tc::tc_fence_before();
@@ -911,7 +913,7 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
         cuuint64_t strides[3] = {static_cast<cuuint64_t>(a.W) * 4ull,
                                  static_cast<cuuint64_t>(a.W) * a.H * 4ull,
                                  static_cast<cuuint64_t>(a.W) * a.H * a.cout * 4ull};
-        cuuint32_t box[4] = {static_cast<cuuint32_t>(kTileX), 1, 16, 1};
+        cuuint32_t box[4] = {32, 1, static_cast<cuuint32_t>(N >= 32 ? 32 : 16), 1};
         cuuint32_t estr[4] = {1, 1, 1, 1};
         if (enc && enc(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.outf, dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -945,7 +947,7 @@ int launch_variant(const ConvArgs &a, cudaStream_t stream) {
     }
     CUtensorMap umap;
     memset(&umap, 0, sizeof(umap));
-    if (b.tma_in == 2 && C::kUpFits && a.c1 % 16 == 0 && a.c1 > 0 && a.W % 2 == 0 &&
+    if (b.tma_in == 2 && C::kUpFits && a.epi_mode != kEpiF32Planar && a.c1 % 16 == 0 && a.c1 > 0 && a.W % 2 == 0 &&
         a.H % 2 == 0) {
         // the coarse source [B][H/2][W/2][c1] as 5-D (channel in chunk, x, y,
         // 16-channel chunk, image); box 16 x kUpW x kUpRows x 1 x 1 = one K chunk of
