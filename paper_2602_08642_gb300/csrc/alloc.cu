@@ -227,10 +227,17 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
     const long long gtid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     const long long n4 = N >> 2;
     const float4 *d4 = reinterpret_cast<const float4 *>(d);
-    // U independent vector loads in flight per thread and iteration; a warp
-    // whose 128 U values all lie in the accumulators' span (the common case)
-    // takes the short path, decided by a warp vote so that the re-basing code
-    // stays out of it
+    // U independent vector loads in flight per thread and iteration.  Chunk
+    // sums: when the 4U values of a thread are finite, non-negative, normal
+    // (or zero) and their exponents span at most 32 binades, the integer
+    //   S = sum of m_i 2^(e_i - e_min)  (m_i the 24-bit significand)
+    // is exact in 64 bits (below 4U 2^56), and the chunk is S 2^(e_min - 150),
+    // i.e. S at bit position e_min - 1 of the accumulator: one shift-and-add
+    // of 128 bits per chunk instead of one per value.  Other chunks (and the
+    // tail) take the per-value path.  After at most 32 chunk adds the 128-bit
+    // sum moves into the limbs, so it cannot overflow (each chunk add is below
+    // 2^122, each per-value add below 2^87).
+    int nadd = 0;
     for (long long q0 = gtid; q0 < n4; q0 += U * nthreads) {
         float4 v4[U];
 #pragma unroll
@@ -239,35 +246,42 @@ budget_sum_kernel(const float *__restrict__ d, long long N, AllocHeader *hdr, Bu
             v4[r] = q < n4 ? __ldg(d4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         const float *v = reinterpret_cast<const float *>(v4);
-        int wmin = 1 << 20, wmax = -(1 << 20);
+        uint32_t emin = 255u, emax = 0u;
         bool ok = true;
 #pragma unroll
         for (int r = 0; r < 4 * U; ++r) {
             const uint32_t bits = __float_as_uint(v[r]);
-            const uint32_t mag = bits & 0x7fffffffu;
-            ok &= mag < 0x7f800000u && bits == mag;  // finite, not negative
-            if (mag != 0u) {
-                const uint32_t e = mag >> 23;
-                const int w = (e ? static_cast<int>(e) - 1 : 0) >> 5;
-                wmin = min(wmin, w);
-                wmax = max(wmax, w);
-            }
+            const uint32_t e = bits >> 23;  // the sign bit makes e > 255
+            // finite, non-negative, and normal or +0
+            ok &= e < 255u && (e != 0u || bits == 0u);
+            emin = min(emin, bits ? e : 255u);
+            emax = max(emax, bits ? e : 0u);
         }
-        // an empty accumulator re-bases for free onto this chunk's windows
-        if (A.lo == 0ull && A.hi == 0ull && wmax >= 0) A.b = wmax > 0 ? wmax - 1 : 0;
-        ok &= wmin >= A.b && wmax <= A.b + 1;
-        if (__all_sync(__activemask(), ok)) {
+        if (ok && (emax < emin || emax - emin <= 32u)) {
+            if (emax >= emin) {  // not all zero
+                unsigned long long S = 0ull;
 #pragma unroll
-            for (int r = 0; r < 4 * U; ++r) {
-                const uint32_t mag = __float_as_uint(v[r]);
-                const uint32_t e = mag >> 23;
-                const unsigned long long m = (mag & 0x7fffffu) | (e ? 0x800000u : 0u);
-                const int sh = (e ? static_cast<int>(e) - 1 : 0) - 32 * A.b;
-                const unsigned long long vlo = m << (sh & 63);
-                const unsigned long long vhi = sh > 40 ? (m >> (64 - sh)) : 0ull;
-                const bool nz = mag != 0u;
-                A.lo += nz ? vlo : 0ull;
-                A.hi += (nz ? vhi : 0ull) + (A.lo < (nz ? vlo : 0ull) ? 1ull : 0ull);
+                for (int r = 0; r < 4 * U; ++r) {
+                    const uint32_t bits = __float_as_uint(v[r]);
+                    const uint32_t m = bits ? ((bits & 0x7fffffu) | 0x800000u) : 0u;
+                    const uint32_t sh = (bits >> 23) - emin;  // 0 .. 32 when m != 0
+                    const uint32_t lo = __funnelshift_lc(0u, m, sh);
+                    const uint32_t hi = __funnelshift_lc(m, 0u, sh);
+                    S += (static_cast<unsigned long long>(hi) << 32) | lo;
+                }
+                const int pos = static_cast<int>(emin) - 1;  // S 2^(pos - 149)
+                const bool empty = A.lo == 0ull && A.hi == 0ull;
+                if (!empty && (pos < 32 * A.b || pos - 32 * A.b > 63 || nadd >= 32)) {
+                    acc_flush(A, lim);
+                    nadd = 0;
+                }
+                if (A.lo == 0ull && A.hi == 0ull) A.b = pos >> 5;
+                const int sh = pos - 32 * A.b;  // 0 .. 63
+                const unsigned long long add_lo = S << sh;
+                const unsigned long long add_hi = sh ? (S >> (64 - sh)) : 0ull;
+                A.lo += add_lo;
+                A.hi += add_hi + (A.lo < add_lo ? 1ull : 0ull);
+                ++nadd;
             }
         } else {
 #pragma unroll

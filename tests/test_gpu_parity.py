@@ -209,6 +209,25 @@ def test_alloc_wide_dynamic_range_density(spp):
     check_alloc(fr, ref, "wide range")
 
 
+@pytest.mark.parametrize("e_lo,width", [(1, 33), (100, 32), (220, 33)])
+def test_alloc_exponent_bands(spp, e_lo, width):
+    """Densities whose exponents fill a band of `width` binades (plus 5 %
+    zeros), at the bottom of the normal range, in the middle and near the
+    top: the chunks of 8 values a thread sums in 64 bits at once span up to
+    32 binades (the exact-sum fast path) or 33 (the per-value path), both in
+    the same threads, several chunks per thread at 4096 x 2048."""
+    W, H = 4096, 2048
+    rng = np.random.default_rng(11 + e_lo)
+    e = rng.integers(e_lo, e_lo + width + 1, size=(H, W))
+    d = np.ldexp(1.0 + rng.random((H, W)), e - 127).astype(np.float32)
+    d[rng.random((H, W)) < 0.05] = 0.0
+    params = spp.make_params(0.25, frame=3)
+    fr = run_alloc(spp, d, W, H, params)
+    ref = oracle_alloc(d, params)
+    assert ref.S == math.fsum(d.astype(np.float64).ravel().tolist())
+    check_alloc(fr, ref, f"band {e_lo}+{width}")
+
+
 def test_alloc_phi_zero_and_one(spp):
     W, H = 256, 64
     d = inp.density_lognormal(W, H, seed=8)
