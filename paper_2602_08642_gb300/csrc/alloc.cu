@@ -1063,8 +1063,8 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     constexpr int kSumU = 2;
     const long long per_block = static_cast<long long>(kSumThreads) * 4 * kSumU;
     long long grid = (N + per_block - 1) / per_block;
-    // two blocks per SM: several chunks per thread at 1080p, and half as many
-    // limb atomics per block-sum as with eight (sample map 40.6 -> 38.5 us at
+    // two blocks per SM: several chunks per thread at 1080p, and a quarter of
+    // the blocks' limb atomics of eight per SM (sample map 40.6 -> 38.5 us at
     // 1080p, 93.9 -> 91.8 us at 4K, swept over 1, 2, 4 and 8 per SM)
     const long long max_grid = static_cast<long long>(sm_count()) * 2;
     if (grid > max_grid) grid = max_grid;
