@@ -1063,10 +1063,12 @@ int alloc_impl(const float *d, int W, int H, const spp_params *p, const Dither &
     constexpr int kSumU = 2;
     const long long per_block = static_cast<long long>(kSumThreads) * 4 * kSumU;
     long long grid = (N + per_block - 1) / per_block;
-    // two blocks per SM: several chunks per thread at 1080p, and a quarter of
-    // the blocks' limb atomics of eight per SM (sample map 40.6 -> 38.5 us at
-    // 1080p, 93.9 -> 91.8 us at 4K, swept over 1, 2, 4 and 8 per SM)
-    const long long max_grid = static_cast<long long>(sm_count()) * 2;
+    // up to eight blocks per SM.  Two per SM made the sample map alone faster
+    // (38.5 against 40.6 us at 1080p, L2 flushed before each call) but the
+    // 1080p frame slower (0.2093 against 0.2013 ms, three alternating runs on
+    // one GPU): inside the frame the longer blocks start behind the previous
+    // kernel's tail under programmatic dependent launch
+    const long long max_grid = static_cast<long long>(sm_count()) * 8;
     if (grid > max_grid) grid = max_grid;
     if (grid < 1) grid = 1;
     launch_dependent(budget_sum_kernel<kSumU>, dim3(static_cast<unsigned>(grid)),
