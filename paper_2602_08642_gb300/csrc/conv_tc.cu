@@ -35,6 +35,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "conv_src.cuh"
 #include "conv_tc.cuh"
@@ -48,7 +49,7 @@ namespace {
 
 constexpr int kTileX = 128;  // output pixels per row tile (MMA M)
 constexpr int kPitch = 130;  // staged halo pixels per row
-constexpr int kThreads = 288;
+constexpr int kThreads = 320;
 constexpr int kHeader = 384;  // barriers, TMEM slot, abort flag
 constexpr int kUpW = kTileX / 2 + 2;  // coarse pixels under a tile's halo (upsampling layers)
 constexpr int kSmemLimit = 227 * 1024;             // dynamic shared memory per CTA
@@ -84,7 +85,10 @@ struct Cfg {
     // a 16-byte pad per pixel: conflict-free 16-byte shared accesses)
     static constexpr int kCBs = N < 32 ? N : 32;
     static constexpr int kStageRow = 2 * kCBs + 16;
-    static constexpr int kStoreBytes = 4 * 32 * kStageRow;
+    // eight epilogue warps (two per TMEM sub-partition, each taking half of
+    // a tile's rows) when the layer's input comes by TMA and N <= 64, else four
+    static constexpr int kEpiWarps = N <= 64 ? 8 : 4;
+    static constexpr int kStoreBytes = kEpiWarps * 32 * kStageRow;
     // the FP32 planar staging buffers and the BF16 staging rows share one
     // region (a launch uses one of the two epilogues)
     static constexpr int kOutBytes = kEpiBytes > kStoreBytes ? kEpiBytes : kStoreBytes;
@@ -147,7 +151,6 @@ __device__ __forceinline__ int a_off(int row, int px, int kg) {
     return q * 32 + 16 * (kg ^ ((q >> 2) & 1));
 }
 
-__device__ __forceinline__ void named_bar_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // TMA load of an NHWC halo box [1 group][TR+2 rows][130 px][8 ch] (5-D map:
 // channel-in-group, x, y, group, image) into shared memory, completing on bar.
@@ -201,6 +204,10 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
     const int ntiles = a.B * per_img;
     const int kchunks = a.cin_pad / 16;
 
+    // the second set of epilogue warps: for a plain NHWC input (TMA halo, one
+    // issuing thread) the producer warps 4-7 take half of each tile's output
+    // rows and warp 9 issues the copies
+    const bool ep8 = C::kEpiWarps == 8 && a.tma_in == 1 && a.epi_mode != kEpiF32Planar;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             tc::mbar_init(&bars.full[s], a.tma_in == 1 ? 1 : 128);
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&bars.accf[i], 1);
-            tc::mbar_init(&bars.acce[i], 128);
+            tc::mbar_init(&bars.acce[i], ep8 ? 256 : 128);
         }
         tc::mbar_init(&bars.drain, 1);
         for (int i = 0; i < 2; ++i) {
@@ -242,9 +249,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         set_status(a.status, SPP_ERR_TIMEOUT);
     };
 
-    if (warp >= 4 && warp < 8) {
+    if (ep8 ? warp == 9 : (warp >= 4 && warp < 8)) {
         // ---------------------------------------------------------- producers
-        const int ptid = tid - 128;
+        const int ptid = ep8 ? tid - 288 : tid - 128;
         constexpr int kTasks = 2 * (TR + 2) * kPitch;  // 16-byte chunks per stage
         constexpr int kPer = (kTasks + 127) / 128;
         // this thread's tasks (the same in every stage): row << 10 | px << 1 | kg
@@ -564,11 +571,16 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp < 4 || (ep8 && warp < 8)) {
         // ----------------------------------------------------------- epilogue
+        // warp w reads TMEM lanes 32 (w % 4) ..; with eight epilogue warps,
+        // warps 0-3 take the first half of a tile's rows and 4-7 the second
+        const int sub = warp & 3;
+        const int row_lo = ep8 ? (warp >> 2) * (TR / 2) : 0;
+        const int row_hi = ep8 ? row_lo + TR / 2 : TR;
         uint32_t tl = 0;
         uint32_t eblk = 0;  // TMA-stored blocks (planar outputs)
-        const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+        const uint32_t lane_base = static_cast<uint32_t>(sub * 32) << 16;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
             const int acc = tl & 1;
             if (!tc::mbar_wait(&bars.accf[acc], (tl >> 1) & 1u, abort_flag)) {
@@ -577,7 +589,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             }
             tc::tc_fence_after();
             const int b = t / per_img, rr = t - b * per_img;
-            const int y0 = (rr / tiles_x) * TR, x = (rr % tiles_x) * kTileX + warp * 32 + lane;
+            const int y0 = (rr / tiles_x) * TR, x = (rr % tiles_x) * kTileX + sub * 32 + lane;
             const uint32_t abase = tmem + lane_base + acc * C::kAccCols + C::kRowOff * N;
             // hands the accumulator back to the MMA warp
             auto release_acc = [&]() {
@@ -620,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     __syncwarp();
                 };
 #pragma unroll 1
-                for (int r = 0; r < TR; r += 2) {
+                for (int r = row_lo; r < row_hi; r += 2) {
                     const int y = y0 + r;
 #pragma unroll 1
                     for (int j0 = 0; j0 < N; j0 += kCB) {
@@ -738,7 +750,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             constexpr int kCB = N < 32 ? N : 32;
             constexpr int kRowBlocks = N / kCB;
             constexpr int kBlocks = TR * kRowBlocks;
-            uint32_t vbuf[2][kCB];
             auto tmem_read = [&](int k, uint32_t (&vv)[kCB]) {
                 const int r = k / kRowBlocks, j0 = (k % kRowBlocks) * kCB;
 #pragma unroll
@@ -746,12 +757,18 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                     tc::tmem_ld16(abase + r * N + j0 + 16 * q,
                                   *reinterpret_cast<uint32_t(*)[16]>(vv + 16 * q));
             };
-            tmem_read(0, vbuf[0]);
+            // blocks [kb_lo, kb_lo + kCount) of the tile (kCount a constant, so
+            // that the double buffer stays in registers)
+            auto blocks = [&](auto count_c, int kb_lo) {
+            constexpr int kCount = decltype(count_c)::value;
+            uint32_t vbuf[2][kCB];
+            tmem_read(kb_lo, vbuf[0]);
             tc::tmem_wait_ld();
 #pragma unroll
-            for (int kb = 0; kb < kBlocks; ++kb) {
-                if (kb + 1 < kBlocks) tmem_read(kb + 1, vbuf[(kb + 1) & 1]);
-                const uint32_t (&v)[kCB] = vbuf[kb & 1];
+            for (int kk = 0; kk < kCount; ++kk) {
+                const int kb = kb_lo + kk;
+                if (kk + 1 < kCount) tmem_read(kb + 1, vbuf[(kk + 1) & 1]);
+                const uint32_t (&v)[kCB] = vbuf[kk & 1];
                 const int r = kb / kRowBlocks, j0 = (kb % kRowBlocks) * kCB;
                 const int y = y0 + r;
                 const bool inside = (x < a.W) && (y < a.H);
@@ -824,6 +841,11 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 }
                 tc::tmem_wait_ld();
             }
+            };
+            if (ep8)
+                blocks(std::integral_constant<int, kBlocks / 2>{}, row_lo * kRowBlocks);
+            else
+                blocks(std::integral_constant<int, kBlocks>{}, 0);
             release_acc();
         }
         if (lane == 0 && eblk) tma_store_wait_all();
