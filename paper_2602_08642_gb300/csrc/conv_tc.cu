@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
     // the second set of epilogue warps: for a plain NHWC input (TMA halo, one
     // issuing thread) the producer warps 4-7 take half of each tile's output
     // rows and warp 9 issues the copies
-    const bool ep8 = C::kEpiWarps == 8 && a.tma_in == 1 && a.epi_mode != kEpiF32Planar;
+    const bool ep8 = C::kEpiWarps == 8 && a.tma_in == 1;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
             tc::mbar_init(&bars.full[s], a.tma_in == 1 ? 1 : 128);
@@ -705,41 +705,56 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             if (RES && a.epi_mode == kEpiF32Planar && a.tma_out) {
                 // each epilogue warp stages kPB output planes of its 32 pixels of
                 // the row in its own buffer and stores them with one TMA tensor
-                // store (clipped at W and at cout); two buffers per warp
+                // store (clipped at W and at cout); two buffers per warp, one
+                // when eight warps share the staging area
                 constexpr int kPB = N >= 32 ? 32 : 16;  // planes per block
                 float *ebuf = reinterpret_cast<float *>(base + C::kEpiOff);
                 const int x0 = (rr % tiles_x) * kTileX;
                 constexpr int kRowBlocks = N / kPB;
                 constexpr int kBlocks = TR * kRowBlocks;
-                uint32_t fbuf[2][kPB];
                 auto tmem_read = [&](int k, uint32_t (&vv)[kPB]) {
 #pragma unroll
                     for (int q = 0; q < kPB / 16; ++q)
                         tc::tmem_ld16(abase + (k / kRowBlocks) * N + (k % kRowBlocks) * kPB + 16 * q,
                                       *reinterpret_cast<uint32_t(*)[16]>(vv + 16 * q));
                 };
-                tmem_read(0, fbuf[0]);
+                auto pblocks = [&](auto count_c, int kb_lo) {
+                constexpr int kCount = decltype(count_c)::value;
+                uint32_t fbuf[2][kPB];
+                tmem_read(kb_lo, fbuf[0]);
                 tc::tmem_wait_ld();
 #pragma unroll
-                for (int kb = 0; kb < kBlocks; ++kb) {
-                    if (kb + 1 < kBlocks) tmem_read(kb + 1, fbuf[(kb + 1) & 1]);
-                    const uint32_t (&v)[kPB] = fbuf[kb & 1];
+                for (int kk = 0; kk < kCount; ++kk) {
+                    const int kb = kb_lo + kk;
+                    if (kk + 1 < kCount) tmem_read(kb + 1, fbuf[(kk + 1) & 1]);
+                    const uint32_t (&v)[kPB] = fbuf[kk & 1];
                     const int y = y0 + kb / kRowBlocks, j0 = (kb % kRowBlocks) * kPB;
                     if (j0 < a.cout) {  // padding columns are not stored
-                        float *buf = ebuf + (warp * 2 + (eblk & 1)) * kPB * 32;
-                        if (lane == 0) tma_store_wait_read<1>();
+                        float *buf = ebuf + (ep8 ? warp : warp * 2 + static_cast<int>(eblk & 1)) *
+                                                kPB * 32;
+                        if (lane == 0) {
+                            if (ep8)
+                                tma_store_wait_read<0>();
+                            else
+                                tma_store_wait_read<1>();
+                        }
                         __syncwarp();
 #pragma unroll
                         for (int e = 0; e < kPB; ++e)
                             buf[e * 32 + lane] = __uint_as_float(v[e]) + sbias[j0 + e];
                         tc::fence_proxy_async();
                         __syncwarp();
-                        if (lane == 0 && y < a.H && x0 + warp * 32 < a.W)
-                            tma_store_planes(&omap, buf, x0 + warp * 32, y, j0, b);
+                        if (lane == 0 && y < a.H && x0 + sub * 32 < a.W)
+                            tma_store_planes(&omap, buf, x0 + sub * 32, y, j0, b);
                         ++eblk;
                     }
                     tc::tmem_wait_ld();
                 }
+                };
+                if (ep8)
+                    pblocks(std::integral_constant<int, kBlocks / 2>{}, row_lo * kRowBlocks);
+                else
+                    pblocks(std::integral_constant<int, kBlocks>{}, 0);
                 release_acc();
                 continue;
             }
