@@ -7,10 +7,13 @@
 // M=128 x N block of TMEM columns, double-buffered across tiles so the
 // epilogue of one tile overlaps the main loop of the next.
 //
-// Warp roles (288 threads):
+// Warp roles (320 threads):
 //   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM
 //              lanes 32w..32w+31 = pixels), bias / ReLU / mask, stores;
-//   warps 4-7  producers: per K chunk of 16 input channels they stage the
+//   warps 4-7  a second set of epilogue warps (the second half of each
+//              tile's rows, TMEM lanes 32 (w - 4)..) when the input arrives by
+//              TMA and N <= 64, with warp 9 issuing the copies; otherwise
+//              producers: per K chunk of 16 input channels they stage the
 //              (TR+2) x 130 pixel halo of the tile in shared memory as K-major
 //              rows of 32 bytes per pixel in the 32-byte swizzle ([row][pixel]
 //              [16 ch], a_off), with zero padding, fused 2x2 pooling, fused
