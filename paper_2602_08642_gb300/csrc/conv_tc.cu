@@ -138,7 +138,7 @@ struct Bars {
     uint64_t acce[2];   // accumulator drained by the epilogue (128 arrivals)
     uint64_t drain;     // abort path: all issued MMAs complete
     uint64_t upfull[2]; // coarse boxes of an upsampling layer landed (1 arrival + bytes)
-    uint64_t updone[2]; // coarse buffer expanded by every producer (128 arrivals)
+    uint64_t updone[2]; // coarse buffer expanded by every producer (160 arrivals)
     uint32_t tmem_base;
     int abort;
 };
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
     const bool ep8 = C::kEpiWarps == 8 && a.tma_in == 1;
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
-            tc::mbar_init(&bars.full[s], a.tma_in == 1 ? 1 : 128);
+            tc::mbar_init(&bars.full[s], a.tma_in == 1 ? 1 : a.tma_in == 3 ? 160 : 128);
             tc::mbar_init(&bars.wfull[s], 1);
             tc::mbar_init(&bars.empty[s], 1);
         }
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         tc::mbar_init(&bars.drain, 1);
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&bars.upfull[i], 1);
-            tc::mbar_init(&bars.updone[i], 128);
+            tc::mbar_init(&bars.updone[i], 160);
         }
         bars.abort = 0;
         tc::fence_mbar_init();
@@ -252,16 +252,21 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
         set_status(a.status, SPP_ERR_TIMEOUT);
     };
 
-    if (ep8 ? warp == 9 : (warp >= 4 && warp < 8)) {
+    // producers: warps 4-7, joined by warp 9 for an upsampling layer (whose
+    // expansion of the coarse boxes bounds it), or warp 9 alone (TMA-fed
+    // layers with eight epilogue warps)
+    const bool up5 = a.tma_in == 3;
+    if (ep8 ? warp == 9 : (warp >= 4 && warp < 8) || (up5 && warp == 9)) {
         // ---------------------------------------------------------- producers
-        const int ptid = ep8 ? tid - 288 : tid - 128;
+        const int ptid = ep8 ? tid - 288 : warp == 9 ? tid - 160 : tid - 128;
+        const int nprod = up5 ? 160 : 128;  // threads sharing the expansion tasks
         constexpr int kTasks = 2 * (TR + 2) * kPitch;  // 16-byte chunks per stage
         constexpr int kPer = (kTasks + 127) / 128;
         // this thread's tasks (the same in every stage): row << 10 | px << 1 | kg
         int tinfo[kPer];
 #pragma unroll
         for (int u = 0; u < kPer; ++u) {
-            const int j = u * 128 + ptid;
+            const int j = u * nprod + ptid;
             tinfo[u] = j < kTasks ? (((j >> 1) / kPitch) << 10) | (((j >> 1) % kPitch) << 1) | (j & 1)
                                   : -1;
         }
