@@ -727,37 +727,37 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                                       *reinterpret_cast<uint32_t(*)[16]>(vv + 16 * q));
                 };
                 auto pblocks = [&](auto count_c, int kb_lo) {
-                constexpr int kCount = decltype(count_c)::value;
-                uint32_t fbuf[2][kPB];
-                tmem_read(kb_lo, fbuf[0]);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int kk = 0; kk < kCount; ++kk) {
-                    const int kb = kb_lo + kk;
-                    if (kk + 1 < kCount) tmem_read(kb + 1, fbuf[(kk + 1) & 1]);
-                    const uint32_t (&v)[kPB] = fbuf[kk & 1];
-                    const int y = y0 + kb / kRowBlocks, j0 = (kb % kRowBlocks) * kPB;
-                    if (j0 < a.cout) {  // padding columns are not stored
-                        float *buf = ebuf + (ep8 ? warp : warp * 2 + static_cast<int>(eblk & 1)) *
-                                                kPB * 32;
-                        if (lane == 0) {
-                            if (ep8)
-                                tma_store_wait_read<0>();
-                            else
-                                tma_store_wait_read<1>();
-                        }
-                        __syncwarp();
-#pragma unroll
-                        for (int e = 0; e < kPB; ++e)
-                            buf[e * 32 + lane] = __uint_as_float(v[e]) + sbias[j0 + e];
-                        tc::fence_proxy_async();
-                        __syncwarp();
-                        if (lane == 0 && y < a.H && x0 + sub * 32 < a.W)
-                            tma_store_planes(&omap, buf, x0 + sub * 32, y, j0, b);
-                        ++eblk;
-                    }
+                    constexpr int kCount = decltype(count_c)::value;
+                    uint32_t fbuf[2][kPB];
+                    tmem_read(kb_lo, fbuf[0]);
                     tc::tmem_wait_ld();
-                }
+#pragma unroll
+                    for (int kk = 0; kk < kCount; ++kk) {
+                        const int kb = kb_lo + kk;
+                        if (kk + 1 < kCount) tmem_read(kb + 1, fbuf[(kk + 1) & 1]);
+                        const uint32_t (&v)[kPB] = fbuf[kk & 1];
+                        const int y = y0 + kb / kRowBlocks, j0 = (kb % kRowBlocks) * kPB;
+                        if (j0 < a.cout) {  // padding columns are not stored
+                            float *buf = ebuf + (ep8 ? warp : warp * 2 + static_cast<int>(eblk & 1)) *
+                                                    kPB * 32;
+                            if (lane == 0) {
+                                if (ep8)
+                                    tma_store_wait_read<0>();
+                                else
+                                    tma_store_wait_read<1>();
+                            }
+                            __syncwarp();
+#pragma unroll
+                            for (int e = 0; e < kPB; ++e)
+                                buf[e * 32 + lane] = __uint_as_float(v[e]) + sbias[j0 + e];
+                            tc::fence_proxy_async();
+                            __syncwarp();
+                            if (lane == 0 && y < a.H && x0 + sub * 32 < a.W)
+                                tma_store_planes(&omap, buf, x0 + sub * 32, y, j0, b);
+                            ++eblk;
+                        }
+                        tc::tmem_wait_ld();
+                    }
                 };
                 if (ep8)
                     pblocks(std::integral_constant<int, kBlocks / 2>{}, row_lo * kRowBlocks);
@@ -783,87 +783,87 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             // blocks [kb_lo, kb_lo + kCount) of the tile (kCount a constant, so
             // that the double buffer stays in registers)
             auto blocks = [&](auto count_c, int kb_lo) {
-            constexpr int kCount = decltype(count_c)::value;
-            uint32_t vbuf[2][kCB];
-            tmem_read(kb_lo, vbuf[0]);
-            tc::tmem_wait_ld();
+                constexpr int kCount = decltype(count_c)::value;
+                uint32_t vbuf[2][kCB];
+                tmem_read(kb_lo, vbuf[0]);
+                tc::tmem_wait_ld();
 #pragma unroll
-            for (int kk = 0; kk < kCount; ++kk) {
-                const int kb = kb_lo + kk;
-                if (kk + 1 < kCount) tmem_read(kb + 1, vbuf[(kk + 1) & 1]);
-                const uint32_t (&v)[kCB] = vbuf[kk & 1];
-                const int r = kb / kRowBlocks, j0 = (kb % kRowBlocks) * kCB;
-                const int y = y0 + r;
-                const bool inside = (x < a.W) && (y < a.H);
-                const size_t pix = (static_cast<size_t>(b) * a.H + y) * a.W + x;
-                if (a.epi_mode == kEpiF32Planar) {
-                    if (inside) {
-                        const size_t plane = static_cast<size_t>(a.H) * a.W;
-                        float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
-                                   static_cast<size_t>(y) * a.W + x;
+                for (int kk = 0; kk < kCount; ++kk) {
+                    const int kb = kb_lo + kk;
+                    if (kk + 1 < kCount) tmem_read(kb + 1, vbuf[(kk + 1) & 1]);
+                    const uint32_t (&v)[kCB] = vbuf[kk & 1];
+                    const int r = kb / kRowBlocks, j0 = (kb % kRowBlocks) * kCB;
+                    const int y = y0 + r;
+                    const bool inside = (x < a.W) && (y < a.H);
+                    const size_t pix = (static_cast<size_t>(b) * a.H + y) * a.W + x;
+                    if (a.epi_mode == kEpiF32Planar) {
+                        if (inside) {
+                            const size_t plane = static_cast<size_t>(a.H) * a.W;
+                            float *o = a.outf + static_cast<size_t>(b) * a.cout * plane +
+                                       static_cast<size_t>(y) * a.W + x;
 #pragma unroll
-                        for (int e = 0; e < kCB; ++e) {
-                            const int n = j0 + e;
-                            if (n < a.cout) __stcs(o + n * plane, __uint_as_float(v[e]) + sbias[n]);
-                        }
-                    }
-                } else {
-                    // BF16 values of this pixel's kCB channels into the warp's
-                    // staging row
-                    unsigned char *srow = base + C::kStoreOff + (warp * 32) * C::kStageRow;
-#pragma unroll
-                    for (int q = 0; q < kCB / 16; ++q) {
-                        const int j = j0 + 16 * q;
-                        float f[16];
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[16 * q + e]);
-                        if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
-#pragma unroll
-                            for (int e = 0; e < 16; ++e) f[e] += sbias[j + e];
-                            if (a.epi_mode == kEpiReluBF16) {
-#pragma unroll
-                                for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
+                            for (int e = 0; e < kCB; ++e) {
+                                const int n = j0 + e;
+                                if (n < a.cout) __stcs(o + n * plane, __uint_as_float(v[e]) + sbias[n]);
                             }
-                        } else if (a.epi_mode == kEpiMaskBF16) {
-                            const uint4 *m = reinterpret_cast<const uint4 *>(a.act + pix * N + j);
+                        }
+                    } else {
+                        // BF16 values of this pixel's kCB channels into the warp's
+                        // staging row
+                        unsigned char *srow = base + C::kStoreOff + (warp * 32) * C::kStageRow;
 #pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const uint4 qq = inside ? __ldg(m + h) : make_uint4(0, 0, 0, 0);
-                                const uint32_t *u = &qq.x;
+                        for (int q = 0; q < kCB / 16; ++q) {
+                            const int j = j0 + 16 * q;
+                            float f[16];
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    const float2 mv = unpack_bf16x2(u[k]);
-                                    f[8 * h + 2 * k] = mv.x > 0.f ? f[8 * h + 2 * k] : 0.f;
-                                    f[8 * h + 2 * k + 1] = mv.y > 0.f ? f[8 * h + 2 * k + 1] : 0.f;
+                            for (int e = 0; e < 16; ++e) f[e] = __uint_as_float(v[16 * q + e]);
+                            if (a.epi_mode == kEpiReluBF16 || a.epi_mode == kEpiBF16) {
+#pragma unroll
+                                for (int e = 0; e < 16; ++e) f[e] += sbias[j + e];
+                                if (a.epi_mode == kEpiReluBF16) {
+#pragma unroll
+                                    for (int e = 0; e < 16; ++e) f[e] = fmaxf(f[e], 0.f);
+                                }
+                            } else if (a.epi_mode == kEpiMaskBF16) {
+                                const uint4 *m = reinterpret_cast<const uint4 *>(a.act + pix * N + j);
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    const uint4 qq = inside ? __ldg(m + h) : make_uint4(0, 0, 0, 0);
+                                    const uint32_t *u = &qq.x;
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) {
+                                        const float2 mv = unpack_bf16x2(u[k]);
+                                        f[8 * h + 2 * k] = mv.x > 0.f ? f[8 * h + 2 * k] : 0.f;
+                                        f[8 * h + 2 * k + 1] = mv.y > 0.f ? f[8 * h + 2 * k + 1] : 0.f;
+                                    }
                                 }
                             }
+                            uint4 *d4 = reinterpret_cast<uint4 *>(srow + lane * C::kStageRow + 32 * q);
+                            d4[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
+                                               pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
+                            d4[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
+                                               pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
                         }
-                        uint4 *d4 = reinterpret_cast<uint4 *>(srow + lane * C::kStageRow + 32 * q);
-                        d4[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
-                                           pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
-                        d4[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
-                                           pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
-                    }
-                    __syncwarp();
-                    // the warp's 32 pixels x kCB channels as contiguous 16-byte
-                    // chunks: kCB / 8 chunks per pixel, one warp store per 32 chunks
-                    constexpr int kChunks = kCB / 8;
-                    const int xw = x - lane;  // the warp's first pixel
+                        __syncwarp();
+                        // the warp's 32 pixels x kCB channels as contiguous 16-byte
+                        // chunks: kCB / 8 chunks per pixel, one warp store per 32 chunks
+                        constexpr int kChunks = kCB / 8;
+                        const int xw = x - lane;  // the warp's first pixel
 #pragma unroll
-                    for (int i = 0; i < kChunks; ++i) {
-                        const int pp = i * (32 / kChunks) + lane / kChunks;
-                        const int ch = lane % kChunks;
-                        const uint4 val =
-                            *reinterpret_cast<const uint4 *>(srow + pp * C::kStageRow + 16 * ch);
-                        if (xw + pp < a.W && y < a.H) {
-                            const size_t q = (static_cast<size_t>(b) * a.H + y) * a.W + xw + pp;
-                            *reinterpret_cast<uint4 *>(a.out + q * N + j0 + 8 * ch) = val;
+                        for (int i = 0; i < kChunks; ++i) {
+                            const int pp = i * (32 / kChunks) + lane / kChunks;
+                            const int ch = lane % kChunks;
+                            const uint4 val =
+                                *reinterpret_cast<const uint4 *>(srow + pp * C::kStageRow + 16 * ch);
+                            if (xw + pp < a.W && y < a.H) {
+                                const size_t q = (static_cast<size_t>(b) * a.H + y) * a.W + xw + pp;
+                                *reinterpret_cast<uint4 *>(a.out + q * N + j0 + 8 * ch) = val;
+                            }
                         }
+                        __syncwarp();  // the staging row is rewritten by the next block
                     }
-                    __syncwarp();  // the staging row is rewritten by the next block
+                    tc::tmem_wait_ld();
                 }
-                tc::tmem_wait_ld();
-            }
             };
             if (ep8)
                 blocks(std::integral_constant<int, kBlocks / 2>{}, row_lo * kRowBlocks);
