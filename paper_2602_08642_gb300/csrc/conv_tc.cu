@@ -270,6 +270,17 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
             tinfo[u] = j < kTasks ? (((j >> 1) / kPitch) << 10) | (((j >> 1) % kPitch) << 1) | (j & 1)
                                   : -1;
         }
+        // upsampling layers: this thread's coarse pieces (the same in every
+        // chunk): coarse row << 10 | coarse column << 1 | 8-channel half
+        constexpr int kUpTasks = C::kUpRows * kUpW * 2;
+        constexpr int kUpPer = (kUpTasks + 127) / 128;
+        int uinfo[kUpPer];
+#pragma unroll
+        for (int k = 0; k < kUpPer; ++k) {
+            const int j = k * nprod + ptid;
+            uinfo[k] = j < kUpTasks ? (((j >> 1) / kUpW) << 10) | (((j >> 1) % kUpW) << 1) | (j & 1)
+                                    : -1;
+        }
         uint32_t it = 0;
         uint32_t issued = 0;  // weight copies issued (by ptid 0)
         bool ok = true;
@@ -378,18 +389,31 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                             break;
                         }
                         const unsigned char *ub = base + C::kUpOff + (u & 1) * C::kUpG;
-                        const int cy0 = (y0 - 1) >> 1, cx0 = (x0 >> 1) - 1;
+                        // each coarse piece (cr, cx) goes to the halo rows and
+                        // pixels that read it: rows 2 cr - p, 2 cr + 1 - p (p = 1
+                        // when y0 is even) and pixels 2 cx - 1, 2 cx (x0 is even),
+                        // those inside the halo.  W and H are even, so a halo
+                        // pixel outside the image reads a coarse cell outside the
+                        // coarse image, which the TMA box filled with zeros.
+                        const int par = (y0 - 1) & 1;
 #pragma unroll
-                        for (int k = 0; k < kPer; ++k) {
-                            if (tinfo[k] < 0) continue;
-                            const int row = tinfo[k] >> 10, px = (tinfo[k] >> 1) & 511,
-                                      kg = tinfo[k] & 1;
-                            const int y = y0 - 1 + row, x = x0 - 1 + px;
-                            uint4 v = make_uint4(0, 0, 0, 0);
-                            if (y >= 0 && y < a.H && x >= 0 && x < a.W)
-                                v = *reinterpret_cast<const uint4 *>(
-                                    ub + (((y >> 1) - cy0) * kUpW + ((x >> 1) - cx0)) * 32 + kg * 16);
-                            *reinterpret_cast<uint4 *>(As + a_off(row, px, kg)) = v;
+                        for (int k = 0; k < kUpPer; ++k) {
+                            if (uinfo[k] < 0) continue;
+                            const int cr = uinfo[k] >> 10, cx = (uinfo[k] >> 1) & 511,
+                                      kg = uinfo[k] & 1;
+                            const uint4 v = *reinterpret_cast<const uint4 *>(
+                                ub + (cr * kUpW + cx) * 32 + kg * 16);
+#pragma unroll
+                            for (int dr = 0; dr < 2; ++dr) {
+                                const int row = 2 * cr + dr - par;
+                                if (row < 0 || row > TR + 1) continue;
+#pragma unroll
+                                for (int dc = 0; dc < 2; ++dc) {
+                                    const int px = 2 * cx + dc - 1;
+                                    if (px < 0 || px >= kPitch) continue;
+                                    *reinterpret_cast<uint4 *>(As + a_off(row, px, kg)) = v;
+                                }
+                            }
                         }
                         tc::fence_proxy_async();
                         tc::mbar_arrive(&bars.full[s]);
