@@ -628,14 +628,6 @@ __global__ void __launch_bounds__(kThreads, 1) conv3x3_kernel(const ConvArgs a,
                 tc::tc_fence_before();
                 tc::mbar_arrive(&bars.acce[acc]);
             };
-            // BF16 NHWC store of 16 channels [j, j+16) of one pixel
-            auto store16 = [&](__nv_bfloat16 *dst, const float *f) {
-                uint4 *o = reinterpret_cast<uint4 *>(dst);
-                o[0] = make_uint4(pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]),
-                                  pack_bf16x2(f[4], f[5]), pack_bf16x2(f[6], f[7]));
-                o[1] = make_uint4(pack_bf16x2(f[8], f[9]), pack_bf16x2(f[10], f[11]),
-                                  pack_bf16x2(f[12], f[13]), pack_bf16x2(f[14], f[15]));
-            };
             if (TR % 2 == 0 && a.pool_out) {
                 // ReLU rows in pairs, plus the 2x2 average of their BF16 values
                 // (lanes x and x^1 hold horizontal neighbours), up to 32 columns
